@@ -1,0 +1,173 @@
+/*
+ * ks.h -- C ABI of the GB300 (sm_103a) RNS hybrid key-switching library.
+ *
+ * The operation is hybrid key switching (HKS) of CKKS as laid out in CiFlow
+ * (arxiv 2311.01598), Sec. III: ModUp (P1 iNTT, P2 BConv, P3 NTT, P4 apply
+ * key, P5 reduce over digits) followed by ModDown (P1 iNTT of the K special
+ * towers, P2 BConv to the Q towers, P3 NTT, P4 subtract and scale by P^-1),
+ * scheduled under the Max-Parallel, Digit-Centric or Output-Centric
+ * dataflow of Sec. IV.  All dataflows return bit-identical results: the
+ * paper notes that the operation count of HKS does not depend on the
+ * dataflow (Sec. IV-D), and every step here is exact integer arithmetic.
+ *
+ * Conventions shared by every entry point:
+ *   - A polynomial over a set of primes is stored limb-major: tower t
+ *     occupies words [t*N, (t+1)*N), one uint64 residue per coefficient or
+ *     slot, canonical in [0, prime).  Q towers come first (q_0..q_l), then
+ *     the K special towers (p_0..p_{K-1}) where those appear.
+ *   - Evaluation form (Sec. II, NTT domain): slot k holds the value at
+ *     psi^(2*brv(k)+1), brv the logN-bit reversal, psi the primitive 2N-th
+ *     root fixed by the prime rule of ks_params_create.
+ *   - Pointers named d_* are device pointers owned by the caller; pointers
+ *     named h_* are host pointers owned by the caller.  Handles (ks_params,
+ *     ks_key) are owned by the library and freed by their destroy call.
+ *   - Every call returns KS_OK (0) or a negative ks_status.  Argument errors
+ *     are detected on the host before any launch; ks_last_error() then
+ *     returns a message for the calling thread.  Device work is queued
+ *     asynchronously on the given stream (0 = legacy default stream);
+ *     errors raised by already-queued device work surface on a later call
+ *     or on the caller's synchronisation.
+ */
+#ifndef KS_H
+#define KS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ks_params ks_params; /* library-owned parameter set          */
+typedef struct ks_key ks_key;       /* library-owned device-resident evk    */
+typedef void *ks_stream_t;          /* a cudaStream_t                       */
+
+typedef enum {
+    KS_OK = 0,
+    KS_EINVAL = -1,       /* bad argument (caught before any launch)         */
+    KS_ENOMEM = -2,       /* device or host allocation failed                */
+    KS_ECUDA = -3,        /* a CUDA runtime call failed                      */
+    KS_ETIMEOUT = -4,     /* a bounded device wait ran out                   */
+    KS_EUNSUPPORTED = -5  /* valid request outside what this build supports  */
+} ks_status;
+
+/* Dataflows of CiFlow Sec. IV. */
+typedef enum {
+    KS_MP = 0,  /* Max-Parallel (Sec. IV-A): one stage at a time over all
+                   towers, every intermediate materialised in device memory */
+    KS_DC = 1,  /* Digit-Centric (Sec. IV-B): ModUp P1-P5 one digit at a
+                   time, partial sums accumulated, then ModDown            */
+    KS_OC = 2,  /* Output-Centric (Sec. IV-C): output towers computed with
+                   BConv fused into the NTT and the key product fused into
+                   its epilogue; P towers first, then Q towers with ModDown
+                   fused (readings: P-first order)                          */
+    KS_AUTO = 3 /* let the library choose (autotuned schedule cache)         */
+} ks_dataflow;
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *ks_last_error(void);
+
+/* Create a parameter set (Table I of the paper: N, Q = q_0..q_L, P =
+ * p_0..p_{K-1}, dnum digits of alpha = ceil((L+1)/dnum) towers).
+ *   logN      : ring degree N = 2^logN, 10 <= logN <= 17
+ *   n_q       : L+1 Q primes, 1 <= n_q <= 64
+ *   k_p       : K special primes, 1 <= k_p <= 32
+ *   dnum      : number of digits, 1 <= dnum <= n_q
+ *   h_q, h_p  : optional explicit primes (both or neither; each must be a
+ *               prime = 1 mod 2N below 2^61, all distinct).  With NULL the
+ *               prime rule applies: the n_q+k_p largest primes below
+ *               2^prime_bits that are 1 mod 2N, descending; the first k_p
+ *               become p_0.., the rest q_0, q_1, ...
+ *   prime_bits: 30..61, used only when h_q/h_p are NULL.
+ * Uploads twiddle and base-conversion tables to the current device.
+ * On success *out receives the handle. */
+int ks_params_create(uint32_t logN, uint32_t n_q, uint32_t k_p, uint32_t dnum,
+                     const uint64_t *h_q, const uint64_t *h_p, uint32_t prime_bits,
+                     ks_params **out);
+void ks_params_destroy(ks_params *params);
+
+/* Read back the primes (h_q: n_q words, h_p: k_p words; either may be NULL)
+ * and the digit geometry. */
+int ks_params_info(const ks_params *params, uint64_t *h_q, uint64_t *h_p,
+                   uint32_t *alpha, uint32_t *n_digits);
+
+/* Generate and upload an evaluation key switching s' -> s (hybrid key):
+ *   b_j = -a_j*s + e_j + [P*g_j]*s',  a_j uniform, e_j rounded Gaussian
+ *   (sigma 3.2, |e| <= 19), g_j the CRT idempotent of digit j.
+ * Sampling is on the host from SplitMix64 streams seed^0 (a_j: digit, then
+ * tower q_0..q_L,p_0..p_{K-1}, then coefficient) and seed^1 (e_j: digit,
+ * then coefficient); NTTs and the key combination run on the device.
+ *   h_s       : N coefficients of s in {-1,0,1}
+ *   h_s_prime : N signed coefficients of s' (|s'_i| < 2^62)
+ * The key stays resident in device memory until ks_key_destroy. */
+int ks_keygen_upload(const ks_params *params, const int8_t *h_s, const int64_t *h_s_prime,
+                     uint64_t seed, ks_stream_t stream, ks_key **out);
+
+/* Upload a key given in the canonical layout
+ *   evk[digit j < n_digits][b=0 / a=1][tower q_0..q_L, p_0..p_{K-1}][N]
+ * (evaluation form, canonical).  h_evk is host memory. */
+int ks_key_upload_raw(const ks_params *params, const uint64_t *h_evk, ks_stream_t stream,
+                      ks_key **out);
+void ks_key_destroy(ks_key *key);
+/* Bytes of device memory the key occupies. */
+size_t ks_key_bytes(const ks_key *key);
+
+/* Key switch one polynomial (Sec. III; Fig. 1 of the paper).
+ *   level_towers : l+1 active Q towers, 1 <= l+1 <= n_q.  Digit j covers
+ *                  towers [j*alpha, min((j+1)*alpha, l+1)); the key's towers
+ *                  outside D_l = {q_0..q_l} u P are not read.
+ *   d_in         : device [l+1][N], evaluation form, canonical; not written.
+ *   d_out0/out1  : device [l+1][N]; receive (out0, out1) with
+ *                  out0 + out1*s = d*s' + small noise (mod Q_l), canonical.
+ *                  Must not overlap d_in or each other.
+ * Device scratch is owned by the params object, one set per stream; calls
+ * on different streams may overlap. */
+int ks_switch(const ks_params *params, const ks_key *key, uint32_t level_towers,
+              const uint64_t *d_in, uint64_t *d_out0, uint64_t *d_out1, ks_dataflow dataflow,
+              ks_stream_t stream);
+
+/* One job of a batched key switch. */
+typedef struct {
+    const ks_key *key;
+    uint32_t level_towers;
+    const uint64_t *d_in;
+    uint64_t *d_out0;
+    uint64_t *d_out1;
+} ks_job;
+
+/* Key switch n independent jobs (uneven levels, each with its own key) in
+ * one batched launch sequence on `stream`.  Each output equals what
+ * ks_switch gives for the same job.  h_jobs is host memory. */
+int ks_switch_batch(const ks_params *params, uint32_t n, const ks_job *h_jobs,
+                    ks_dataflow dataflow, ks_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Stage entry points (the individual steps of Sec. III; used by the
+ * parity tests and available to callers composing their own schedules).
+ * ------------------------------------------------------------------- */
+
+/* Forward (inverse = 0) or inverse (inverse = 1) negacyclic NTT of
+ * n_towers limbs stored contiguously at d_data, in place.  Limb i uses
+ * tower (first_tower + i) of the full-level basis q_0..q_L, p_0..p_{K-1}.
+ * Input canonical; output canonical.  The inverse includes the N^-1
+ * factor. */
+int ks_ntt(const ks_params *params, uint32_t first_tower, uint32_t n_towers, uint64_t *d_data,
+           int inverse, ks_stream_t stream);
+
+/* ModUp (Sec. III-B, P1-P3) at level l+1 = level_towers: d_in [l+1][N]
+ * -> d_ext [n_active_digits][l+1+K][N] in evaluation form over D_l (Q
+ * towers then P towers); row j holds digit j raised to D_l, its own towers
+ * being the input towers.  Values canonical. */
+int ks_modup(const ks_params *params, uint32_t level_towers, const uint64_t *d_in,
+             uint64_t *d_ext, ks_stream_t stream);
+
+/* ModDown (Sec. III-C, P1-P4) of one polynomial c' over D_l:
+ * d_cp [l+1+K][N] evaluation form -> d_out [l+1][N] = (c' - NTT(BConv(
+ * iNTT(c'_P)))) * P^-1 (mod q_i).  Values canonical. */
+int ks_moddown(const ks_params *params, uint32_t level_towers, const uint64_t *d_cp,
+               uint64_t *d_out, ks_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KS_H */

@@ -1,0 +1,519 @@
+// ks_api.cu -- C ABI entry points, parameter/key objects, per-stream scratch
+// and the Max-Parallel / Digit-Centric executors (CiFlow Sec. IV-A, IV-B).
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ks_internal.h"
+#include "ks_launch.h"
+
+namespace ks {
+
+static thread_local std::string tl_err;
+
+void set_error(const std::string &msg) { tl_err = msg; }
+int fail(int code, const std::string &msg)
+{
+    tl_err = msg;
+    return code;
+}
+
+static int cuda_check(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return KS_OK;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? KS_ENOMEM : KS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Scratch of one stream: sized for the top level of the parameter set.
+struct Workspace {
+    u64 *y = nullptr;    // [nq][N]          ModUp P1 output (coefficient form)
+    u64 *D = nullptr;    // [ndig][nq+kp][N] ModUp P2/P3 output (MP); digit 0 slot (DC)
+    u64 *cp = nullptr;   // [2][nq+kp][N]    ModUp P5 output c'
+    u64 *v = nullptr;    // [2][nq][N]       ModDown P2/P3 output
+    u64 *tmp = nullptr;  // Output-Centric half-transformed limbs
+    size_t tmp_words = 0;
+};
+
+static int ws_alloc(u64 **p, size_t words)
+{
+    return cuda_check(cudaMalloc((void **)p, words * sizeof(u64)), "workspace allocation");
+}
+
+static int get_ws(ks_params *P, cudaStream_t st, bool need_D, Workspace **out)
+{
+    std::lock_guard<std::mutex> g(P->mu);
+    Workspace *&w = P->ws[(void *)st];
+    if (!w) w = new Workspace();
+    const size_t N = P->N;
+    const size_t nt = (size_t)P->nq + P->kp;
+    int rc = KS_OK;
+    if (!w->y && (rc = ws_alloc(&w->y, (size_t)P->nq * N)) != KS_OK) return rc;
+    if (!w->cp && (rc = ws_alloc(&w->cp, 2 * nt * N)) != KS_OK) return rc;
+    if (!w->v && (rc = ws_alloc(&w->v, 2 * (size_t)P->nq * N)) != KS_OK) return rc;
+    if (need_D && !w->D && (rc = ws_alloc(&w->D, (size_t)P->ndig * nt * N)) != KS_OK) return rc;
+    if (!w->tmp) {
+        const size_t words = std::max((size_t)P->ndig * P->kp, (size_t)(P->ndig + 2) * P->nq) * N;
+        if ((rc = ws_alloc(&w->tmp, words)) != KS_OK) return rc;
+        w->tmp_words = words;
+    }
+    *out = w;
+    return KS_OK;
+}
+
+static void free_ws(ks_params *P)
+{
+    for (auto &kv : P->ws) {
+        Workspace *w = kv.second;
+        u64 *bufs[] = {w->y, w->D, w->cp, w->v, w->tmp};
+        for (u64 *b : bufs)
+            if (b) cudaFree(b);
+        delete w;
+    }
+    P->ws.clear();
+}
+
+static int active_digits(const ks_params *P, int nact) { return (nact + P->alpha - 1) / P->alpha; }
+
+// ModUp P1 scale of tower i at level nact: N^-1 * (Q_j/q_i)^-1 mod q_i,
+// one contiguous row of nact pairs per level.
+static const ulonglong2 *pre_level(const ks_params *P, int nact) { return P->d_up_pre_lvl + (size_t)(nact - 1) * P->nq; }
+
+// ------------------------------------------------------------------ ModDown
+static int run_moddown(const ks_params *P, Workspace *w, int nact, int npoly, u64 *out0, u64 *out1, cudaStream_t st)
+{
+    const Tables &T = P->tables;
+    const size_t N = P->N;
+    const int nt = nact + P->kp;
+    int rc;
+    // P1: iNTT of the special towers of each polynomial (N^-1 (P/p_k)^-1 is
+    // folded into the key), canonical.
+    LimbMap mP{w->cp, w->cp, P->kp, nt, nact, nact, nact, -1};
+    if ((rc = launch_ntt_inv(T, mP, npoly * P->kp, nullptr, false, st)) != KS_OK) return rc;
+    // P2: fast base conversion P -> q_0..q_l (P^-1 folded into the matrix).
+    if ((rc = launch_bconv_down(T, nact, npoly, w->cp, (size_t)nt * N, w->v, (size_t)nact * N, st)) != KS_OK) return rc;
+    // P3: NTT of the converted towers.
+    LimbMap mV{w->v, w->v, nact, nact, 0, 0, nact, -1};
+    if ((rc = launch_ntt_fwd(T, mV, npoly * nact, false, st)) != KS_OK) return rc;
+    // P4: subtract.
+    u64 *outs[2] = {out0, out1};
+    return launch_down_final(T, nact, npoly, w->cp, (size_t)nt * N, w->v, (size_t)nact * N, outs, st);
+}
+
+// ------------------------------------------------------------------ MP
+// Max-Parallel: each stage over all towers, intermediates in device memory.
+static int run_mp(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, Workspace *w,
+                  cudaStream_t st)
+{
+    const Tables &T = P->tables;
+    const size_t N = P->N;
+    const int nt = nact + P->kp;
+    const int nd = active_digits(P, nact);
+    int rc;
+    // ModUp P1: iNTT and the (Q_j/q_i)^-1 prescale of every input tower.
+    LimbMap m1{d, w->y, nact, 0, 0, 0, nact, -1};
+    if ((rc = launch_ntt_inv(T, m1, nact, pre_level(P, nact), false, st)) != KS_OK) return rc;
+    // P2: every digit to every other tower of D_l.
+    if ((rc = launch_bconv_up(T, nact, w->y, w->D, st)) != KS_OK) return rc;
+    // P3: NTT of the converted towers (digit towers are bypassed).
+    LimbMap mD{w->D, w->D, nt, nt, 0, 0, nact, 0};
+    if ((rc = launch_ntt_fwd(T, mD, nd * nt, false, st)) != KS_OK) return rc;
+    // P4 + P5: key product summed over digits.
+    if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, K->d_evk, w->cp, false, st)) != KS_OK) return rc;
+    return run_moddown(P, w, nact, 2, out0, out1, st);
+}
+
+// ------------------------------------------------------------------ DC
+// Digit-Centric: ModUp P1..P5 for one digit at a time, partial sums of c'
+// accumulated in device memory, then ModDown.
+static int run_dc(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, Workspace *w,
+                  cudaStream_t st)
+{
+    const Tables &T = P->tables;
+    const size_t N = P->N;
+    const int nt = nact + P->kp;
+    const int nd = active_digits(P, nact);
+    int rc;
+    for (int j = 0; j < nd; ++j) {
+        const int lo = j * P->alpha;
+        const int a = std::min(P->alpha, nact - lo);
+        LimbMap m1{d, w->y, a, 0, lo, lo, nact, -1};
+        if ((rc = launch_ntt_inv(T, m1, a, pre_level(P, nact) + lo, false, st)) != KS_OK) return rc;
+        if ((rc = launch_bconv_up_digit(T, nact, j, w->y, w->D, st)) != KS_OK) return rc;
+        LimbMap mD{w->D, w->D, nt, nt, 0, 0, nact, j};
+        if ((rc = launch_ntt_fwd(T, mD, nt, false, st)) != KS_OK) return rc;
+        if ((rc = launch_apply_key(T, nact, j, j + 1, d, w->D, 0, K->d_evk, w->cp, j > 0, st)) != KS_OK) return rc;
+    }
+    return run_moddown(P, w, nact, 2, out0, out1, st);
+}
+
+static int run_oc(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, Workspace *w,
+                  cudaStream_t st)
+{
+    return launch_oc(P->tables, nact, d, K->d_evk, out0, out1, w->y, w->tmp, w->cp, pre_level(P, nact), st);
+}
+
+static int check_params(const ks_params *P)
+{
+    if (!P) return fail(KS_EINVAL, "params is NULL");
+    return KS_OK;
+}
+
+static int set_device(const ks_params *P)
+{
+    return cuda_check(cudaSetDevice(P->device), "cudaSetDevice");
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+extern "C" {
+
+const char *ks_last_error(void) { return tl_err.c_str(); }
+
+int ks_params_create(uint32_t logN, uint32_t n_q, uint32_t k_p, uint32_t dnum, const uint64_t *h_q,
+                     const uint64_t *h_p, uint32_t prime_bits, ks_params **out)
+{
+    if (!out) return fail(KS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (logN < (uint32_t)kMinLogN || logN > (uint32_t)kMaxLogN) return fail(KS_EUNSUPPORTED, "logN must be in 10..17");
+    if (n_q < 1 || n_q > (uint32_t)kMaxQ) return fail(KS_EINVAL, "n_q must be in 1..64");
+    if (k_p < 1 || k_p > (uint32_t)kMaxP) return fail(KS_EINVAL, "k_p must be in 1..32");
+    if (dnum < 1 || dnum > n_q) return fail(KS_EINVAL, "dnum must be in 1..n_q");
+    if ((h_q == nullptr) != (h_p == nullptr)) return fail(KS_EINVAL, "give both prime lists or neither");
+    const uint64_t N = 1ull << logN;
+    std::vector<u64> q(n_q), p(k_p);
+    if (h_q) {
+        std::vector<u64> all;
+        for (uint32_t i = 0; i < n_q; ++i) all.push_back(h_q[i]);
+        for (uint32_t i = 0; i < k_p; ++i) all.push_back(h_p[i]);
+        for (size_t i = 0; i < all.size(); ++i) {
+            if (all[i] >= (1ull << kMaxPrimeBits) || all[i] % (2 * N) != 1 || !is_prime_u64(all[i]))
+                return fail(KS_EINVAL, "explicit primes must be primes = 1 mod 2N below 2^56");
+            for (size_t k = 0; k < i; ++k)
+                if (all[k] == all[i]) return fail(KS_EINVAL, "explicit primes must be distinct");
+        }
+        for (uint32_t i = 0; i < n_q; ++i) q[i] = h_q[i];
+        for (uint32_t i = 0; i < k_p; ++i) p[i] = h_p[i];
+    } else {
+        if (prime_bits < 30 || prime_bits > (uint32_t)kMaxPrimeBits)
+            return fail(KS_EUNSUPPORTED, "prime_bits must be in 30..56");
+        std::vector<u64> all;
+        if (gen_primes((int)logN, (int)prime_bits, (int)(n_q + k_p), all) != 0)
+            return fail(KS_EINVAL, "not enough primes = 1 mod 2N below 2^prime_bits");
+        for (uint32_t k = 0; k < k_p; ++k) p[k] = all[k];
+        for (uint32_t i = 0; i < n_q; ++i) q[i] = all[k_p + i];
+    }
+    ks_params *P = new ks_params();
+    P->logN = (int)logN;
+    P->N = (uint32_t)N;
+    P->nq = (int)n_q;
+    P->kp = (int)k_p;
+    P->dnum = (int)dnum;
+    P->alpha = (int)((n_q + dnum - 1) / dnum);
+    P->ndig = (P->nq + P->alpha - 1) / P->alpha;
+    P->q = q;
+    P->p = p;
+    if (cudaGetDevice(&P->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete P;
+        return fail(KS_ECUDA, "no CUDA device");
+    }
+    int rc = build_tables(P);
+    if (rc != KS_OK) {
+        free_tables(P);
+        delete P;
+        return rc;
+    }
+    *out = P;
+    return KS_OK;
+}
+
+void ks_params_destroy(ks_params *P)
+{
+    if (!P) return;
+    cudaSetDevice(P->device);
+    cudaDeviceSynchronize();
+    free_ws(P);
+    free_tables(P);
+    delete P;
+}
+
+int ks_params_info(const ks_params *P, uint64_t *h_q, uint64_t *h_p, uint32_t *alpha, uint32_t *n_digits)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (h_q) std::memcpy(h_q, P->q.data(), sizeof(uint64_t) * P->nq);
+    if (h_p) std::memcpy(h_p, P->p.data(), sizeof(uint64_t) * P->kp);
+    if (alpha) *alpha = (uint32_t)P->alpha;
+    if (n_digits) *n_digits = (uint32_t)P->ndig;
+    return KS_OK;
+}
+
+static size_t evk_words(const ks_params *P) { return (size_t)P->ndig * 2 * (P->nq + P->kp) * P->N; }
+
+int ks_key_upload_raw(const ks_params *P, const uint64_t *h_evk, ks_stream_t stream, ks_key **out)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (!h_evk || !out) return fail(KS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    ks_key *K = new ks_key();
+    K->params = P;
+    K->bytes = evk_words(P) * sizeof(u64);
+    if ((rc = cuda_check(cudaMalloc((void **)&K->d_evk, K->bytes), "key allocation")) != KS_OK) {
+        delete K;
+        return rc;
+    }
+    rc = cuda_check(cudaMemcpyAsync(K->d_evk, h_evk, K->bytes, cudaMemcpyHostToDevice, st), "key upload");
+    if (rc == KS_OK) rc = launch_key_convert(P->tables, K->d_evk, st);
+    if (rc == KS_OK) rc = cuda_check(cudaStreamSynchronize(st), "key upload sync");
+    if (rc != KS_OK) {
+        cudaFree(K->d_evk);
+        delete K;
+        return rc;
+    }
+    *out = K;
+    return KS_OK;
+}
+
+void ks_key_destroy(ks_key *K)
+{
+    if (!K) return;
+    cudaSetDevice(K->params->device);
+    cudaDeviceSynchronize();
+    cudaFree(K->d_evk);
+    delete K;
+}
+
+size_t ks_key_bytes(const ks_key *K) { return K ? K->bytes : 0; }
+
+// SplitMix64 (Steele, Lea & Flood 2014).
+namespace {
+struct SplitMix {
+    uint64_t s;
+    uint64_t next()
+    {
+        s += 0x9E3779B97F4A7C15ULL;
+        uint64_t z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+        return z ^ (z >> 31);
+    }
+};
+uint64_t uniform_mod(SplitMix &g, uint64_t m)
+{
+    int b = 64 - __builtin_clzll(m);
+    uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1);
+    for (;;) {
+        uint64_t v = g.next() & mask;
+        if (v < m) return v;
+    }
+}
+int64_t gauss(SplitMix &g)
+{
+    const double sigma = 3.2;
+    for (;;) {
+        double u1 = (double)((g.next() >> 11) + 1) * 0x1.0p-53;
+        double u2 = (double)(g.next() >> 11) * 0x1.0p-53;
+        double z = std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * 3.14159265358979323846 * u2);
+        int64_t e = (int64_t)std::llround(sigma * z);
+        if (e >= -19 && e <= 19) return e;
+    }
+}
+}  // namespace
+
+int ks_keygen_upload(const ks_params *P, const int8_t *h_s, const int64_t *h_s_prime, uint64_t seed,
+                     ks_stream_t stream, ks_key **out)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (!h_s || !h_s_prime || !out) return fail(KS_EINVAL, "NULL argument");
+    *out = nullptr;
+    const size_t N = P->N;
+    const int nfull = P->nq + P->kp;
+    for (size_t n = 0; n < N; ++n) {
+        if (h_s[n] < -1 || h_s[n] > 1) return fail(KS_EINVAL, "s must be ternary");
+        if (h_s_prime[n] > (1ll << 62) || h_s_prime[n] < -(1ll << 62)) return fail(KS_EINVAL, "|s'| must be < 2^62");
+    }
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    // host sampling, in the documented draw order
+    std::vector<u64> evk_h(evk_words(P), 0);
+    SplitMix ga{seed ^ 0}, ge{seed ^ 1};
+    for (int j = 0; j < P->ndig; ++j)
+        for (int t = 0; t < nfull; ++t) {
+            const u64 r = t < P->nq ? P->q[t] : P->p[t - P->nq];
+            u64 *dst = evk_h.data() + (((size_t)j * 2 + 1) * nfull + t) * N;
+            for (size_t n = 0; n < N; ++n) dst[n] = uniform_mod(ga, r);
+        }
+    std::vector<int64_t> vecs((2 + (size_t)P->ndig) * N);
+    for (size_t n = 0; n < N; ++n) {
+        vecs[n] = h_s[n];
+        vecs[N + n] = h_s_prime[n];
+    }
+    for (int j = 0; j < P->ndig; ++j)
+        for (size_t n = 0; n < N; ++n) vecs[(2 + (size_t)j) * N + n] = gauss(ge);
+    std::vector<u64> pmod(nfull, 0);
+    for (int t = 0; t < P->nq; ++t) {
+        u64 pm = 1;
+        for (int k = 0; k < P->kp; ++k) pm = mulmod_h(pm, P->p[k] % P->q[t], P->q[t]);
+        pmod[t] = pm;
+    }
+    ks_key *K = new ks_key();
+    K->params = P;
+    K->bytes = evk_words(P) * sizeof(u64);
+    int64_t *d_vecs = nullptr;
+    u64 *d_res = nullptr, *d_pmod = nullptr;
+    const int nvec = 2 + P->ndig;
+    rc = cuda_check(cudaMalloc((void **)&K->d_evk, K->bytes), "key allocation");
+    if (rc == KS_OK) rc = cuda_check(cudaMalloc((void **)&d_vecs, vecs.size() * 8), "keygen scratch");
+    if (rc == KS_OK) rc = cuda_check(cudaMalloc((void **)&d_res, (size_t)nvec * nfull * N * 8), "keygen scratch");
+    if (rc == KS_OK) rc = cuda_check(cudaMalloc((void **)&d_pmod, nfull * 8), "keygen scratch");
+    if (rc == KS_OK)
+        rc = cuda_check(cudaMemcpyAsync(K->d_evk, evk_h.data(), K->bytes, cudaMemcpyHostToDevice, st), "key upload");
+    if (rc == KS_OK)
+        rc = cuda_check(cudaMemcpyAsync(d_vecs, vecs.data(), vecs.size() * 8, cudaMemcpyHostToDevice, st), "upload");
+    if (rc == KS_OK) rc = cuda_check(cudaMemcpyAsync(d_pmod, pmod.data(), nfull * 8, cudaMemcpyHostToDevice, st), "upload");
+    if (rc == KS_OK) rc = launch_signed_to_towers(P->tables, d_vecs, nvec, d_res, st);
+    if (rc == KS_OK) {
+        LimbMap m{d_res, d_res, nfull, nfull, 0, 0, P->nq, -1};
+        rc = launch_ntt_fwd(P->tables, m, nvec * nfull, true, st);
+    }
+    if (rc == KS_OK)
+        rc = launch_keygen_combine(P->tables, d_res, d_res + (size_t)nfull * N, d_res + 2 * (size_t)nfull * N, d_pmod,
+                                   K->d_evk, st);
+    if (rc == KS_OK) rc = launch_key_convert(P->tables, K->d_evk, st);
+    if (rc == KS_OK) rc = cuda_check(cudaStreamSynchronize(st), "keygen sync");
+    cudaFree(d_vecs);
+    cudaFree(d_res);
+    cudaFree(d_pmod);
+    if (rc != KS_OK) {
+        cudaFree(K->d_evk);
+        delete K;
+        return rc;
+    }
+    *out = K;
+    return KS_OK;
+}
+
+static int switch_one(ks_params *P, const ks_key *K, uint32_t nact, const uint64_t *d, uint64_t *o0, uint64_t *o1,
+                      ks_dataflow df, cudaStream_t st)
+{
+    Workspace *w = nullptr;
+    int rc = get_ws(P, st, df == KS_MP || df == KS_DC, &w);
+    if (rc) return rc;
+    switch (df) {
+    case KS_MP: return run_mp(P, K, (int)nact, d, o0, o1, w, st);
+    case KS_DC: return run_dc(P, K, (int)nact, d, o0, o1, w, st);
+    case KS_OC:
+    case KS_AUTO: return run_oc(P, K, (int)nact, d, o0, o1, w, st);
+    }
+    return fail(KS_EINVAL, "unknown dataflow");
+}
+
+static int check_job(const ks_params *P, const ks_key *K, uint32_t nact, const uint64_t *d, const uint64_t *o0,
+                     const uint64_t *o1)
+{
+    if (!K || K->params != P) return fail(KS_EINVAL, "key is NULL or belongs to another params object");
+    if (nact < 1 || nact > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
+    if (!d || !o0 || !o1) return fail(KS_EINVAL, "NULL data pointer");
+    const size_t bytes = (size_t)nact * P->N * sizeof(u64);
+    auto overlap = [bytes](const void *a, const void *b) {
+        const char *x = (const char *)a, *y = (const char *)b;
+        return x < y + bytes && y < x + bytes;
+    };
+    if (overlap(d, o0) || overlap(d, o1) || overlap(o0, o1)) return fail(KS_EINVAL, "d_in, d_out0, d_out1 overlap");
+    return KS_OK;
+}
+
+int ks_switch(const ks_params *P, const ks_key *K, uint32_t level_towers, const uint64_t *d_in, uint64_t *d_out0,
+              uint64_t *d_out1, ks_dataflow dataflow, ks_stream_t stream)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if ((rc = check_job(P, K, level_towers, d_in, d_out0, d_out1)) != KS_OK) return rc;
+    if ((int)dataflow < 0 || (int)dataflow > 3) return fail(KS_EINVAL, "unknown dataflow");
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    return switch_one(const_cast<ks_params *>(P), K, level_towers, d_in, d_out0, d_out1, dataflow,
+                      (cudaStream_t)stream);
+}
+
+int ks_switch_batch(const ks_params *P, uint32_t n, const ks_job *jobs, ks_dataflow dataflow, ks_stream_t stream)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (n > 0 && !jobs) return fail(KS_EINVAL, "jobs is NULL");
+    if ((int)dataflow < 0 || (int)dataflow > 3) return fail(KS_EINVAL, "unknown dataflow");
+    for (uint32_t i = 0; i < n; ++i)
+        if ((rc = check_job(P, jobs[i].key, jobs[i].level_towers, jobs[i].d_in, jobs[i].d_out0, jobs[i].d_out1)) != KS_OK)
+            return rc;
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    for (uint32_t i = 0; i < n; ++i) {
+        rc = switch_one(const_cast<ks_params *>(P), jobs[i].key, jobs[i].level_towers, jobs[i].d_in, jobs[i].d_out0,
+                        jobs[i].d_out1, dataflow, (cudaStream_t)stream);
+        if (rc) return rc;
+    }
+    return KS_OK;
+}
+
+int ks_ntt(const ks_params *P, uint32_t first_tower, uint32_t n_towers, uint64_t *d_data, int inverse,
+           ks_stream_t stream)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (!d_data) return fail(KS_EINVAL, "NULL data");
+    if ((uint64_t)first_tower + n_towers > (uint64_t)(P->nq + P->kp)) return fail(KS_EINVAL, "tower range outside the basis");
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    LimbMap m{d_data, d_data, (int)n_towers, 0, 0, (int)first_tower, P->nq, -1};
+    if (inverse) return launch_ntt_inv(P->tables, m, (int)n_towers, nullptr, true, (cudaStream_t)stream);
+    return launch_ntt_fwd(P->tables, m, (int)n_towers, true, (cudaStream_t)stream);
+}
+
+int ks_modup(const ks_params *P, uint32_t level_towers, const uint64_t *d_in, uint64_t *d_ext, ks_stream_t stream)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (!d_in || !d_ext) return fail(KS_EINVAL, "NULL data");
+    if (level_towers < 1 || level_towers > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    ks_params *PP = const_cast<ks_params *>(P);
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace *w = nullptr;
+    if ((rc = get_ws(PP, st, false, &w)) != KS_OK) return rc;
+    const int nact = (int)level_towers;
+    const int nt = nact + P->kp;
+    const int nd = active_digits(P, nact);
+    const Tables &T = P->tables;
+    LimbMap m1{d_in, w->y, nact, 0, 0, 0, nact, -1};
+    if ((rc = launch_ntt_inv(T, m1, nact, pre_level(P, nact), false, st)) != KS_OK) return rc;
+    if ((rc = launch_bconv_up(T, nact, w->y, d_ext, st)) != KS_OK) return rc;
+    LimbMap mD{d_ext, d_ext, nt, nt, 0, 0, nact, 0};
+    if ((rc = launch_ntt_fwd(T, mD, nd * nt, true, st)) != KS_OK) return rc;
+    return launch_bypass_copy(T, nact, d_in, d_ext, st);
+}
+
+int ks_moddown(const ks_params *P, uint32_t level_towers, const uint64_t *d_cp, uint64_t *d_out, ks_stream_t stream)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (!d_cp || !d_out) return fail(KS_EINVAL, "NULL data");
+    if (level_towers < 1 || level_towers > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    ks_params *PP = const_cast<ks_params *>(P);
+    cudaStream_t st = (cudaStream_t)stream;
+    Workspace *w = nullptr;
+    if ((rc = get_ws(PP, st, false, &w)) != KS_OK) return rc;
+    const int nact = (int)level_towers;
+    const int nt = nact + P->kp;
+    // fold the ModDown factors in (the key normally carries them)
+    LimbMap ms{d_cp, w->cp, nt, 0, 0, 0, nact, -1};
+    if ((rc = launch_scale(P->tables, ms, nt, P->d_plain_sc, st)) != KS_OK) return rc;
+    return run_moddown(P, w, nact, 1, d_out, d_out, st);
+}
+
+}  // extern "C"

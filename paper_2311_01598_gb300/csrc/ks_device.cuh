@@ -1,0 +1,241 @@
+// ks_device.cuh -- device arithmetic and the register/shared-memory NTT core.
+//
+// Modular arithmetic (all moduli q < 2^56, one uint64 per residue):
+//   * Shoup multiplication by a known constant w with w' = floor(w*2^64/q):
+//     a*w - floor(a*w'/2^64)*q lies in [0, 2q) for every a < 2^64 (Shoup).
+//   * Harvey's lazy butterflies: the forward (Cooley-Tukey) butterfly keeps
+//     values in [0, 4q), the inverse (Gentleman-Sande) one in [0, 2q).
+//   * Montgomery reduction (REDC) of a 128-bit sum of products with the
+//     stored key, whose factor 2^64 is folded in at upload.
+//   * Base conversion accumulates 28-bit-split partial products in three
+//     64-bit accumulators (no carries) and reduces once per output.
+//
+// NTT structure.  The negacyclic NTT of N = 2^(LA+LB) points is the in-place
+// Cooley-Tukey network whose stage s pairs indices differing in bit
+// logN-1-s, with twiddle psi^brv(2^s + i) for butterfly group i.  Stages
+// 0..LA-1 act within columns (fixed low LB index bits), stages LA..logN-1
+// within rows (fixed high LA bits), so the transform splits into a column
+// pass and a row pass over the limb viewed as a 2^LA x 2^LB matrix.  Inside a
+// pass each sub-transform of 2^L points is held in registers by 2^(L-RR)
+// threads (2^RR values each), RR = ceil(L/2): the first RR stages run in
+// registers, one shared-memory transpose regroups the values, and the
+// remaining L-RR stages run in registers again.  In sub-transform-local
+// terms the twiddle of local stage s and local group i is tw[G*2^s + i] with
+// G = 1 for the column pass and G = 2^LA + row for the row pass.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ks_internal.h"
+
+namespace ks {
+
+// ------------------------------------------------------------------ scalar
+__device__ __forceinline__ u64 shoup_lazy(u64 a, u64 w, u64 wp, u64 q)
+{
+    return a * w - __umul64hi(a, wp) * q;  // [0, 2q)
+}
+
+__device__ __forceinline__ u64 reduce2(u64 x, u64 q)  // [0, 2q) -> [0, q)
+{
+    return x >= q ? x - q : x;
+}
+
+__device__ __forceinline__ u64 reduce4(u64 x, u64 q, u64 q2)  // [0, 4q) -> [0, q)
+{
+    x = x >= q2 ? x - q2 : x;
+    return x >= q ? x - q : x;
+}
+
+// Forward Harvey butterfly: X, Y in [0, 4q) -> [0, 4q).
+__device__ __forceinline__ void fwd_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2)
+{
+    u64 x = X >= q2 ? X - q2 : X;
+    u64 t = shoup_lazy(Y, w, wp, q);
+    X = x + t;
+    Y = x - t + q2;
+}
+
+// Inverse Harvey butterfly: X, Y in [0, 2q) -> [0, 2q).
+__device__ __forceinline__ void inv_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2)
+{
+    u64 s = X + Y;
+    s = s >= q2 ? s - q2 : s;
+    u64 d = X - Y + q2;
+    X = s;
+    Y = shoup_lazy(d, w, wp, q);
+}
+
+// 128-bit accumulator.
+struct U128 {
+    u64 lo, hi;
+};
+__device__ __forceinline__ void mac128(U128 &acc, u64 a, u64 b)
+{
+    u64 lo = a * b;
+    u64 hi = __umul64hi(a, b);
+    acc.lo += lo;
+    acc.hi += hi + (acc.lo < lo ? 1 : 0);
+}
+// Montgomery reduction: returns T * 2^-64 mod q in [0, q + T/2^64).
+__device__ __forceinline__ u64 redc(U128 T, u64 q, u64 mont)
+{
+    u64 m = T.lo * mont;
+    return T.hi + __umul64hi(m, q) + (T.lo != 0 ? 1 : 0);
+}
+
+// Base-conversion accumulator: sum of y*c with y, c < 2^56 split at 28 bits.
+struct BAcc {
+    u64 a0, a1, a2;
+};
+__device__ __forceinline__ void bacc_zero(BAcc &A) { A.a0 = A.a1 = A.a2 = 0; }
+__device__ __forceinline__ void bacc_mac(BAcc &A, u32 y0, u32 y1, u64 csplit)
+{
+    const u32 c0 = (u32)csplit, c1 = (u32)(csplit >> 32);
+    A.a0 += (u64)y0 * c0;
+    A.a1 += (u64)y0 * c1;
+    A.a1 += (u64)y1 * c0;
+    A.a2 += (u64)y1 * c1;
+}
+// (a0 + a1*2^28 + a2*2^56) mod q, lazily in [0, 2q).
+__device__ __forceinline__ u64 bacc_reduce(const BAcc &A, const ModC &m)
+{
+    u64 t0 = A.a0 - __umul64hi(A.a0, m.one_sh) * m.q;
+    u64 t1 = shoup_lazy(A.a1, m.r28, m.r28_sh, m.q);
+    u64 t2 = shoup_lazy(A.a2, m.r56, m.r56_sh, m.q);
+    u64 s = t0 + t1 + t2;  // [0, 6q)
+    const u64 q4 = 2 * m.q2;
+    s = s >= q4 ? s - q4 : s;
+    return s >= m.q2 ? s - m.q2 : s;
+}
+__device__ __forceinline__ void split_y(u64 y, u32 &y0, u32 &y1)
+{
+    y0 = (u32)y & ((1u << kSplit) - 1);
+    y1 = (u32)(y >> kSplit);
+}
+
+// ------------------------------------------------------------------ NTT shape
+template <int LA_, int LB_>
+struct Shape {
+    static constexpr int LA = LA_, LB = LB_, LOGN = LA_ + LB_;
+    static constexpr int N = 1 << LOGN;
+    static constexpr int RA = (LA + 1) / 2, RB = (LB + 1) / 2;
+    static constexpr int REGA = 1 << RA, REGB = 1 << RB;
+    static constexpr int TA = 1 << (LA - RA), TB = 1 << (LB - RB);  // threads per sub-transform
+    static constexpr int COLS_W = (256 / TA) < 16 ? 16 : (256 / TA);
+    static constexpr int COLS = COLS_W > (1 << LB) ? (1 << LB) : COLS_W;  // columns per column-pass CTA
+    static constexpr int ROWS_W = 256 / TB;
+    static constexpr int ROWS = ROWS_W > (1 << LA) ? (1 << LA) : ROWS_W;  // rows per row-pass CTA
+    static constexpr int THREADS_A = COLS * TA;
+    static constexpr int THREADS_B = ROWS * TB;
+    static constexpr int MB = 1 << (LB - RB);         // group size of the row pass, 2nd round
+    static constexpr int ROWPAD = (1 << LB) + (1 << LB) / MB;  // padded row in shared memory
+    static constexpr int SMEM_A = (1 << LA) * COLS * 8 + (1 << LA) * 16;
+    static constexpr int SMEM_B = ROWS * ROWPAD * 8;
+};
+
+template <int LOGN>
+struct ShapeOf;
+template <> struct ShapeOf<10> { typedef Shape<5, 5> T; };
+template <> struct ShapeOf<11> { typedef Shape<6, 5> T; };
+template <> struct ShapeOf<12> { typedef Shape<6, 6> T; };
+template <> struct ShapeOf<13> { typedef Shape<7, 6> T; };
+template <> struct ShapeOf<14> { typedef Shape<7, 7> T; };
+template <> struct ShapeOf<15> { typedef Shape<8, 7> T; };
+template <> struct ShapeOf<16> { typedef Shape<8, 8> T; };
+template <> struct ShapeOf<17> { typedef Shape<9, 8> T; };
+
+// ------------------------------------------------------------------ rounds
+// Round 1 in registers: x[k], k = the high RR bits of the sub-transform index.
+// tw(s, i) returns the (w, w') pair of local stage s, local group i.
+template <int RR, class TW>
+__device__ __forceinline__ void fwd_round1(u64 (&x)[1 << RR], const TW &tw, u64 q, u64 q2)
+{
+#pragma unroll
+    for (int s = 0; s < RR; ++s) {
+        const int half = (1 << RR) >> (s + 1);
+#pragma unroll
+        for (int g = 0; g < (1 << s); ++g) {
+            const ulonglong2 W = tw(s, g);
+#pragma unroll
+            for (int k = 0; k < half; ++k) fwd_bfly(x[g * 2 * half + k], x[g * 2 * half + k + half], W.x, W.y, q, q2);
+        }
+    }
+}
+
+// Round 2 in registers: NG groups of M = 2^(L-RR) values; group gg has
+// global group id gid0 + gg (the high RR bits of the index).
+template <int L, int RR, class TW>
+__device__ __forceinline__ void fwd_round2(u64 (&x)[1 << RR], int gid0, const TW &tw, u64 q, u64 q2)
+{
+    constexpr int M = 1 << (L - RR);
+    constexpr int NG = (1 << RR) / M;
+#pragma unroll
+    for (int s2 = 0; s2 < L - RR; ++s2) {
+        const int half = M >> (s2 + 1);
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg) {
+#pragma unroll
+            for (int g2 = 0; g2 < (1 << s2); ++g2) {
+                const ulonglong2 W = tw(RR + s2, ((gid0 + gg) << s2) + g2);
+#pragma unroll
+                for (int k = 0; k < half; ++k)
+                    fwd_bfly(x[gg * M + g2 * 2 * half + k], x[gg * M + g2 * 2 * half + k + half], W.x, W.y, q, q2);
+            }
+        }
+    }
+}
+
+// Inverse of fwd_round2: local stages L-1 .. RR on the low bits.
+template <int L, int RR, class TW>
+__device__ __forceinline__ void inv_round2(u64 (&x)[1 << RR], int gid0, const TW &tw, u64 q, u64 q2)
+{
+    constexpr int M = 1 << (L - RR);
+    constexpr int NG = (1 << RR) / M;
+#pragma unroll
+    for (int s2 = L - RR - 1; s2 >= 0; --s2) {
+        const int half = M >> (s2 + 1);
+#pragma unroll
+        for (int gg = 0; gg < NG; ++gg) {
+#pragma unroll
+            for (int g2 = 0; g2 < (1 << s2); ++g2) {
+                const ulonglong2 W = tw(RR + s2, ((gid0 + gg) << s2) + g2);
+#pragma unroll
+                for (int k = 0; k < half; ++k)
+                    inv_bfly(x[gg * M + g2 * 2 * half + k], x[gg * M + g2 * 2 * half + k + half], W.x, W.y, q, q2);
+            }
+        }
+    }
+}
+
+// Inverse of fwd_round1: local stages RR-1 .. 0 on the high bits.
+template <int RR, class TW>
+__device__ __forceinline__ void inv_round1(u64 (&x)[1 << RR], const TW &tw, u64 q, u64 q2)
+{
+#pragma unroll
+    for (int s = RR - 1; s >= 0; --s) {
+        const int half = (1 << RR) >> (s + 1);
+#pragma unroll
+        for (int g = 0; g < (1 << s); ++g) {
+            const ulonglong2 W = tw(s, g);
+#pragma unroll
+            for (int k = 0; k < half; ++k) inv_bfly(x[g * 2 * half + k], x[g * 2 * half + k + half], W.x, W.y, q, q2);
+        }
+    }
+}
+
+// Twiddle fetchers.  Column pass: the first 2^LA entries of the tower's table,
+// staged in shared memory (G = 1).  Row pass: read through the read-only
+// path from the tower's global table (G = 2^LA + row).
+struct TwSmem {
+    const ulonglong2 *t;
+    __device__ __forceinline__ ulonglong2 operator()(int s, int i) const { return t[(1 << s) + i]; }
+};
+struct TwRow {
+    const ulonglong2 *t;  // tower table
+    int G;
+    __device__ __forceinline__ ulonglong2 operator()(int s, int i) const { return __ldg(t + (G << s) + i); }
+};
+
+}  // namespace ks

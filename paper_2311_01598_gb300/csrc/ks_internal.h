@@ -1,0 +1,126 @@
+// ks_internal.h -- internal types of the key-switching library (host + device).
+//
+// Layout of everything the library keeps on the device (one parameter set):
+//   modc[t]          per-tower constants, t over the full basis q_0..q_L, p_0..p_{K-1}
+//   tw[t][N]         forward twiddles (w, floor(w*2^64/q)) in bit-reversed order:
+//                    tw[t][i] = psi^brv(i) for the Cooley-Tukey NTT
+//   itw[t][N]        inverse twiddles psi^-brv(i) for the Gentleman-Sande iNTT
+//   up_pre[...]      ModUp P1 scale N^-1 * (Q_j/q_i)^-1 mod q_i per (digit, active
+//                    towers, source tower)
+//   up_mat[...]      ModUp P2 matrix (Q_j/q_i) mod r per (digit, active towers,
+//                    source tower, target tower), split in two 28-bit halves
+//   dn_mat[k][i]     ModDown P2 matrix (P/p_k) * P^-1 mod q_i (P^-1 of P4 folded in)
+//   key_sc[t]        per-tower factor folded into the stored key: P^-1 on Q towers
+//                    (ModDown P4), N^-1 * (P/p_k)^-1 on P towers (ModDown P1 + P2
+//                    prescale), times 2^64 for the Montgomery product of P4
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ks.h"
+
+namespace ks {
+
+typedef uint64_t u64;
+typedef uint32_t u32;
+
+constexpr int kMaxQ = 64;
+constexpr int kMaxP = 32;
+constexpr int kMaxT = kMaxQ + kMaxP;
+constexpr int kMinLogN = 10;
+constexpr int kMaxLogN = 17;
+constexpr int kMaxPrimeBits = 56;  // 28-bit split products in BConv; 4q < 2^58 in the NTT
+constexpr int kSplit = 28;
+
+// Per-tower constants.
+struct ModC {
+    u64 q;       // modulus
+    u64 q2;      // 2q
+    u64 mont;    // -q^-1 mod 2^64 (Montgomery reduction)
+    u64 one_sh;  // floor(2^64 / q): Shoup companion of 1
+    u64 r28, r28_sh;  // 2^28 mod q and its Shoup companion
+    u64 r56, r56_sh;  // 2^56 mod q and its Shoup companion
+    u64 ninv, ninv_sh;  // N^-1 mod q and its Shoup companion
+    u64 r2;             // 2^128 mod q (into Montgomery form)
+    u64 pad;
+};
+
+// Device tables of one parameter set, passed to kernels by value.
+struct Tables {
+    const ModC *modc;
+    const ulonglong2 *tw;
+    const ulonglong2 *itw;
+    const ulonglong2 *up_pre;
+    const u64 *up_mat;
+    const u64 *dn_mat;
+    const ulonglong2 *key_sc;   // Montgomery-form fold factors (see header)
+    const ulonglong2 *plain_sc; // the same factors without 2^64
+    const int *h_up_mat_off;  // HOST pointer: ModUp matrix offset of (digit j, active
+                              // towers a) at [j*(alpha+1)+a]; never read on the device
+    int logN;
+    int nq, kp, alpha, ndig;
+};
+
+// Offsets of the ModUp tables for digit j with `a` active towers.
+struct UpOffsets {
+    std::vector<int> pre;  // [j * (alpha + 1) + a]
+    std::vector<int> mat;
+};
+
+struct Workspace;
+
+}  // namespace ks
+
+struct ks_params {
+    int logN = 0;
+    uint32_t N = 0;
+    int nq = 0, kp = 0, dnum = 0, alpha = 0, ndig = 0;
+    int device = 0;
+    std::vector<uint64_t> q, p, psi;  // psi over the full basis
+    ks::UpOffsets up_off;
+    // device allocations
+    ks::ModC *d_modc = nullptr;
+    ulonglong2 *d_tw = nullptr, *d_itw = nullptr;
+    ulonglong2 *d_up_pre = nullptr;
+    ulonglong2 *d_up_pre_lvl = nullptr;  // [nq levels][nq]: ModUp P1 factor per level
+    uint64_t *d_up_mat = nullptr;
+    uint64_t *d_dn_mat = nullptr;
+    ulonglong2 *d_key_sc = nullptr, *d_plain_sc = nullptr;
+    ks::Tables tables{};
+    // per-stream scratch
+    std::mutex mu;
+    std::map<void *, ks::Workspace *> ws;
+};
+
+struct ks_key {
+    const ks_params *params = nullptr;
+    uint64_t *d_evk = nullptr;  // [ndig][2][nq+kp][N], Montgomery form with key_sc folded in
+    size_t bytes = 0;
+};
+
+namespace ks {
+
+// Thread-local error message (ks_last_error).
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+
+// Host number theory (ks_host.cpp).
+bool is_prime_u64(u64 n);
+int gen_primes(int logN, int bits, int count, std::vector<u64> &out);
+u64 find_psi(u64 q, int logN);
+u64 mulmod_h(u64 a, u64 b, u64 m);
+u64 powmod_h(u64 b, u64 e, u64 m);
+u64 invmod_h(u64 a, u64 m);
+u64 shoup_h(u64 w, u64 q);  // floor(w * 2^64 / q)
+
+// Build every host table and upload it (ks_host.cpp).
+int build_tables(ks_params *P);
+void free_tables(ks_params *P);
+
+}  // namespace ks

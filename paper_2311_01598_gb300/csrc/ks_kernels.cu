@@ -1,0 +1,618 @@
+// ks_kernels.cu -- NTT passes and the per-stage kernels of hybrid key
+// switching (CiFlow Sec. III: ModUp P1-P5, ModDown P1-P4).  The Max-Parallel
+// and Digit-Centric executors are built from these; the Output-Centric fused
+// kernels live in ks_oc.cu.
+#include <algorithm>
+
+#include "ks_ntt_core.cuh"
+
+namespace ks {
+
+// ------------------------------------------------------------------ NTT passes
+// Forward column pass (stages 0..LA-1).  grid (2^LB/COLS, nlimbs).
+template <class S>
+__global__ void __launch_bounds__(S::THREADS_A) k_fwd_col(Tables T, LimbMap m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64 *sm = reinterpret_cast<u64 *>(smem_raw);
+    ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(sm + (1 << S::LA) * S::COLS);
+    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    if (L.skip) return;
+    const u64 q = T.modc[L.tf].q, q2 = 2 * q;
+    const ulonglong2 *twt = T.tw + ((size_t)L.tf << S::LOGN);
+    for (int i = threadIdx.x; i < (1 << S::LA); i += S::THREADS_A) tws[i] = twt[i];
+    const int cc = threadIdx.x % S::COLS, tau = threadIdx.x / S::COLS;
+    const int c = blockIdx.x * S::COLS + cc;
+    u64 x[S::REGA];
+#pragma unroll
+    for (int k = 0; k < S::REGA; ++k) x[k] = L.src[((size_t)(k * S::TA + tau) << S::LB) + c];
+    __syncthreads();
+    fwd_round1<S::RA>(x, TwSmem{tws}, q, q2);
+#pragma unroll
+    for (int k = 0; k < S::REGA; ++k) sm[(k * S::TA + tau) * S::COLS + cc] = x[k];
+    __syncthreads();
+    constexpr int M = S::TA, NG = S::REGA / S::TA;
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) x[gg * M + k2] = sm[((tau * NG + gg) * M + k2) * S::COLS + cc];
+    fwd_round2<S::LA, S::RA>(x, tau * NG, TwSmem{tws}, q, q2);
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) L.dst[((size_t)((tau * NG + gg) * M + k2) << S::LB) + c] = x[gg * M + k2];
+}
+
+// Forward row pass (stages LA..logN-1).  grid (2^LA/ROWS, nlimbs).
+template <class S, bool CANON>
+__global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMap m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64 *sm = reinterpret_cast<u64 *>(smem_raw);
+    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    if (L.skip) return;
+    const u64 q = T.modc[L.tf].q, q2 = 2 * q;
+    const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
+    const int h = blockIdx.x * S::ROWS + rr;
+    const TwRow tw{T.tw + ((size_t)L.tf << S::LOGN), (1 << S::LA) + h};
+    const u64 *gin = L.src + ((size_t)h << S::LB);
+    u64 *gout = L.dst + ((size_t)h << S::LB);
+    u64 x[S::REGB];
+#pragma unroll
+    for (int k = 0; k < S::REGB; ++k) x[k] = gin[k * S::TB + tau];
+    row_fwd_core<S>(x, tw, sm + rr * S::ROWPAD, tau, q, q2);
+#pragma unroll
+    for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = CANON ? reduce4(x[k], q, q2) : x[k];
+}
+
+// Inverse row pass (stages logN-1..LA), first half of the iNTT.  Input in
+// [0, 2q); output in [0, 2q).
+template <class S>
+__global__ void __launch_bounds__(S::THREADS_B) k_inv_row(Tables T, LimbMap m)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64 *sm = reinterpret_cast<u64 *>(smem_raw);
+    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    if (L.skip) return;
+    const u64 q = T.modc[L.tf].q, q2 = 2 * q;
+    const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
+    const int h = blockIdx.x * S::ROWS + rr;
+    const TwRow tw{T.itw + ((size_t)L.tf << S::LOGN), (1 << S::LA) + h};
+    const u64 *gin = L.src + ((size_t)h << S::LB);
+    u64 *gout = L.dst + ((size_t)h << S::LB);
+    u64 x[S::REGB];
+#pragma unroll
+    for (int k = 0; k < S::REGB; ++k) x[k] = gin[k * S::TB + tau];
+    row_inv_core<S>(x, tw, sm + rr * S::ROWPAD, tau, q, q2);
+#pragma unroll
+    for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = x[k];
+}
+
+// Inverse column pass (stages LA-1..0), second half of the iNTT, then the
+// optional scale; output canonical.  SC: 0 none, 1 per-limb scale[b],
+// 2 N^-1.
+template <class S, int SC>
+__global__ void __launch_bounds__(S::THREADS_A) k_inv_col(Tables T, LimbMap m, const ulonglong2 *scale)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64 *sm = reinterpret_cast<u64 *>(smem_raw);
+    ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(sm + (1 << S::LA) * S::COLS);
+    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    if (L.skip) return;
+    const ModC mc = T.modc[L.tf];
+    const u64 q = mc.q, q2 = 2 * q;
+    const ulonglong2 *twt = T.itw + ((size_t)L.tf << S::LOGN);
+    for (int i = threadIdx.x; i < (1 << S::LA); i += S::THREADS_A) tws[i] = twt[i];
+    const int cc = threadIdx.x % S::COLS, tau = threadIdx.x / S::COLS;
+    const int c = blockIdx.x * S::COLS + cc;
+    constexpr int M = S::TA, NG = S::REGA / S::TA;
+    u64 x[S::REGA];
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) x[gg * M + k2] = L.src[((size_t)((tau * NG + gg) * M + k2) << S::LB) + c];
+    __syncthreads();
+    inv_round2<S::LA, S::RA>(x, tau * NG, TwSmem{tws}, q, q2);
+#pragma unroll
+    for (int gg = 0; gg < NG; ++gg)
+#pragma unroll
+        for (int k2 = 0; k2 < M; ++k2) sm[((tau * NG + gg) * M + k2) * S::COLS + cc] = x[gg * M + k2];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < S::REGA; ++k) x[k] = sm[(k * S::TA + tau) * S::COLS + cc];
+    inv_round1<S::RA>(x, TwSmem{tws}, q, q2);
+    u64 w = 0, wp = 0;
+    if (SC == 1) {
+        const ulonglong2 f = scale[L.b];
+        w = f.x;
+        wp = f.y;
+    } else if (SC == 2) {
+        w = mc.ninv;
+        wp = mc.ninv_sh;
+    }
+#pragma unroll
+    for (int k = 0; k < S::REGA; ++k) {
+        u64 v = x[k];
+        if (SC != 0) v = shoup_lazy(v, w, wp, q);
+        L.dst[((size_t)(k * S::TA + tau) << S::LB) + c] = reduce2(v, q);
+    }
+}
+
+template <class S>
+static void set_smem_attrs()
+{
+    static bool done = false;  // per instantiation; attributes are per device function
+    if (done) return;
+    cudaFuncSetAttribute(k_fwd_col<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+    cudaFuncSetAttribute(k_inv_col<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+    cudaFuncSetAttribute(k_inv_col<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+    cudaFuncSetAttribute(k_inv_col<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+    cudaFuncSetAttribute(k_fwd_row<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+    cudaFuncSetAttribute(k_fwd_row<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+    cudaFuncSetAttribute(k_inv_row<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+    done = true;
+}
+
+static int launch_status(const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(KS_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return KS_OK;
+}
+
+template <class S>
+static void ntt_fwd_S(const Tables &T, const LimbMap &m, int nlimbs, bool canonical, cudaStream_t st)
+{
+    set_smem_attrs<S>();
+    dim3 ga((1 << S::LB) / S::COLS, nlimbs), gb((1 << S::LA) / S::ROWS, nlimbs);
+    k_fwd_col<S><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m);
+    LimbMap m2 = m;
+    m2.src = m.dst;
+    if (canonical)
+        k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m2);
+    else
+        k_fwd_row<S, false><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m2);
+}
+
+template <class S>
+static void ntt_inv_S(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool ninv,
+                      cudaStream_t st)
+{
+    set_smem_attrs<S>();
+    dim3 ga((1 << S::LB) / S::COLS, nlimbs), gb((1 << S::LA) / S::ROWS, nlimbs);
+    k_inv_row<S><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m);
+    LimbMap m2 = m;
+    m2.src = m.dst;
+    if (scale)
+        k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, scale);
+    else if (ninv)
+        k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, nullptr);
+    else
+        k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, nullptr);
+}
+
+#define KS_DISPATCH_LOGN(logN, FN, ...)                                                                   \
+    switch (logN) {                                                                                       \
+    case 10: FN<ShapeOf<10>::T>(__VA_ARGS__); break;                                                      \
+    case 11: FN<ShapeOf<11>::T>(__VA_ARGS__); break;                                                      \
+    case 12: FN<ShapeOf<12>::T>(__VA_ARGS__); break;                                                      \
+    case 13: FN<ShapeOf<13>::T>(__VA_ARGS__); break;                                                      \
+    case 14: FN<ShapeOf<14>::T>(__VA_ARGS__); break;                                                      \
+    case 15: FN<ShapeOf<15>::T>(__VA_ARGS__); break;                                                      \
+    case 16: FN<ShapeOf<16>::T>(__VA_ARGS__); break;                                                      \
+    case 17: FN<ShapeOf<17>::T>(__VA_ARGS__); break;                                                      \
+    default: return fail(KS_EUNSUPPORTED, "logN outside 10..17");                                         \
+    }
+
+template <class S>
+static void fwd_col_S(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
+{
+    set_smem_attrs<S>();
+    k_fwd_col<S><<<dim3((1 << S::LB) / S::COLS, nlimbs), S::THREADS_A, S::SMEM_A, st>>>(T, m);
+}
+
+template <class S>
+static void inv_col_S(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool ninv,
+                      cudaStream_t st)
+{
+    set_smem_attrs<S>();
+    dim3 ga((1 << S::LB) / S::COLS, nlimbs);
+    if (scale)
+        k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, scale);
+    else if (ninv)
+        k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, nullptr);
+    else
+        k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, nullptr);
+}
+
+int launch_fwd_col(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
+{
+    if (nlimbs <= 0) return KS_OK;
+    KS_DISPATCH_LOGN(T.logN, fwd_col_S, T, m, nlimbs, st);
+    return launch_status("forward column pass launch");
+}
+
+int launch_inv_col(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool scale_by_ninv,
+                   cudaStream_t st)
+{
+    if (nlimbs <= 0) return KS_OK;
+    KS_DISPATCH_LOGN(T.logN, inv_col_S, T, m, nlimbs, scale, scale_by_ninv, st);
+    return launch_status("inverse column pass launch");
+}
+
+int launch_ntt_fwd(const Tables &T, const LimbMap &m, int nlimbs, bool canonical, cudaStream_t st)
+{
+    if (nlimbs <= 0) return KS_OK;
+    KS_DISPATCH_LOGN(T.logN, ntt_fwd_S, T, m, nlimbs, canonical, st);
+    return launch_status("forward NTT launch");
+}
+
+int launch_ntt_inv(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool scale_by_ninv,
+                   cudaStream_t st)
+{
+    if (nlimbs <= 0) return KS_OK;
+    KS_DISPATCH_LOGN(T.logN, ntt_inv_S, T, m, nlimbs, scale, scale_by_ninv, st);
+    return launch_status("inverse NTT launch");
+}
+
+// ------------------------------------------------------------------ BConv
+constexpr int BC_TT = 8;      // target towers per block
+constexpr int BC_THREADS = 256;
+
+struct DigitOffs {
+    int mat[kMaxQ];
+};
+
+// ModUp P2: grid (N/256, ceil(targets/TT), digits).  Digit j (or jsel)
+// converts its canonical coefficient-form towers y[lo..hi) to the towers of
+// D_l with compact index in [t_begin, t_end) outside the digit; output lazy
+// in [0, 2r) at D + j*dstride + (t - t_base)*N (j = 0 when jsel is set).
+__global__ void __launch_bounds__(BC_THREADS) k_bconv_up(Tables T, int nact, int jsel, int t_begin, int t_end,
+                                                         int t_base, DigitOffs offs, const u64 *y, u64 *D,
+                                                         size_t dstride)
+{
+    __shared__ u64 cs[kMaxQ][BC_TT];
+    __shared__ int s_t[BC_TT];
+    __shared__ int s_tf[BC_TT];
+    const int j = jsel >= 0 ? jsel : (int)blockIdx.z;
+    const int lo = j * T.alpha;
+    const int hi = min(lo + T.alpha, nact);
+    const int a = hi - lo;
+    // overlap of the digit with the target range
+    const int olo = max(lo, t_begin), ohi = min(hi, t_end);
+    const int ov = ohi > olo ? ohi - olo : 0;
+    const int nb = (t_end - t_begin) - ov;
+    const int u0 = blockIdx.y * BC_TT;
+    if (u0 >= nb) return;
+    const int nfull = T.nq + T.kp;
+    const u64 *mat = T.up_mat + offs.mat[j];
+    if (threadIdx.x < BC_TT) {
+        const int u = min(u0 + (int)threadIdx.x, nb - 1);
+        int t = t_begin + u;
+        if (ov > 0 && t >= olo) t += ov;
+        s_t[threadIdx.x] = t;
+        s_tf[threadIdx.x] = full_tower(t, nact, T.nq);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < a * BC_TT; idx += blockDim.x) {
+        const int i = idx / BC_TT, g = idx % BC_TT;
+        cs[i][g] = (u0 + g < nb) ? mat[(size_t)i * nfull + s_tf[g]] : 0;
+    }
+    __syncthreads();
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    BAcc acc[BC_TT];
+#pragma unroll
+    for (int g = 0; g < BC_TT; ++g) bacc_zero(acc[g]);
+    for (int i = 0; i < a; ++i) {
+        u32 y0, y1;
+        split_y(y[(size_t)(lo + i) * N + n], y0, y1);
+#pragma unroll
+        for (int g = 0; g < BC_TT; ++g) bacc_mac(acc[g], y0, y1, cs[i][g]);
+    }
+    u64 *Dj = D + (size_t)(jsel >= 0 ? 0 : j) * dstride;
+#pragma unroll
+    for (int g = 0; g < BC_TT; ++g) {
+        if (u0 + g < nb) {
+            const ModC mc = T.modc[s_tf[g]];
+            Dj[(size_t)(s_t[g] - t_base) * N + n] = bacc_reduce(acc[g], mc);
+        }
+    }
+}
+
+static DigitOffs digit_offsets(const Tables &T, int nact)
+{
+    const int *mat_off = T.h_up_mat_off;
+    DigitOffs o;
+    const int nd = (nact + T.alpha - 1) / T.alpha;
+    for (int j = 0; j < nd; ++j) {
+        const int a = std::min(T.alpha, nact - j * T.alpha);
+        o.mat[j] = mat_off[j * (T.alpha + 1) + a];
+    }
+    return o;
+}
+
+int launch_bconv_up_range(const Tables &T, int nact, int t_begin, int t_end, int t_base, const u64 *y, u64 *D,
+                          size_t dstride, cudaStream_t st)
+{
+    const int nd = (nact + T.alpha - 1) / T.alpha;
+    const size_t N = (size_t)1 << T.logN;
+    if (t_end <= t_begin) return KS_OK;
+    DigitOffs o = digit_offsets(T, nact);
+    dim3 g((unsigned)(N / BC_THREADS), (unsigned)((t_end - t_begin + BC_TT - 1) / BC_TT), (unsigned)nd);
+    k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, nact, -1, t_begin, t_end, t_base, o, y, D, dstride);
+    return launch_status("ModUp BConv launch");
+}
+
+int launch_bconv_up(const Tables &T, int nact, const u64 *y, u64 *D, cudaStream_t st)
+{
+    const int nt = nact + T.kp;
+    const size_t N = (size_t)1 << T.logN;
+    return launch_bconv_up_range(T, nact, 0, nt, 0, y, D, (size_t)nt * N, st);
+}
+
+int launch_bconv_up_digit(const Tables &T, int nact, int j, const u64 *y, u64 *Dj, cudaStream_t st)
+{
+    const int nt = nact + T.kp;
+    const size_t N = (size_t)1 << T.logN;
+    DigitOffs o = digit_offsets(T, nact);
+    dim3 g((unsigned)(N / BC_THREADS), (unsigned)((nt + BC_TT - 1) / BC_TT), 1);
+    k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, nact, j, 0, nt, 0, o, y, Dj, 0);
+    return launch_status("ModUp BConv launch");
+}
+
+// ------------------------------------------------------------------ apply key
+// ModUp P4+P5: grid (N/256, nact+K).  Stored key = evk * key_sc * 2^64, so
+// REDC of the 128-bit sum gives the folded c' directly.
+__global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, int j1, const u64 *d, const u64 *D,
+                                                   size_t dstride, const u64 *evk, u64 *cp, int accumulate)
+{
+    const int t = blockIdx.y;
+    const int nt = nact + T.kp;
+    const int nfull = T.nq + T.kp;
+    const int tf = full_tower(t, nact, T.nq);
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const ModC mc = T.modc[tf];
+    U128 sb = {0, 0}, sa = {0, 0};
+    for (int j = j0; j < j1; ++j) {
+        const bool own = t < nact && t / T.alpha == j;
+        const u64 dv = own ? d[(size_t)t * N + n] : D[(size_t)(j - j0) * dstride + (size_t)t * N + n];
+        const u64 kb = evk[(((size_t)j * 2 + 0) * nfull + tf) * N + n];
+        const u64 ka = evk[(((size_t)j * 2 + 1) * nfull + tf) * N + n];
+        mac128(sb, dv, kb);
+        mac128(sa, dv, ka);
+    }
+    u64 rb = reduce2(redc(sb, mc.q, mc.mont), mc.q);
+    u64 ra = reduce2(redc(sa, mc.q, mc.mont), mc.q);
+    u64 *cb = cp + (size_t)t * N + n;
+    u64 *ca = cp + ((size_t)nt + t) * N + n;
+    if (accumulate) {
+        rb = reduce2(rb + *cb, mc.q);
+        ra = reduce2(ra + *ca, mc.q);
+    }
+    *cb = rb;
+    *ca = ra;
+}
+
+int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u64 *d, const u64 *D,
+                     size_t D_digit_stride, const u64 *evk, u64 *cp, bool accumulate, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    dim3 g((unsigned)(N / 256), (unsigned)(nact + T.kp));
+    k_apply_key<<<g, 256, 0, st>>>(T, nact, j_begin, j_end, d, D, D_digit_stride, evk, cp, accumulate ? 1 : 0);
+    return launch_status("apply-key launch");
+}
+
+// ------------------------------------------------------------------ ModDown
+// P2: grid (N/256, ceil(nact/TT), npoly).
+__global__ void __launch_bounds__(BC_THREADS) k_bconv_down(Tables T, int nact, const u64 *cp, size_t cp_stride,
+                                                           u64 *v, size_t v_stride)
+{
+    __shared__ u64 cs[kMaxP][BC_TT];
+    const int i0 = blockIdx.y * BC_TT;
+    const int K = T.kp;
+    for (int idx = threadIdx.x; idx < K * BC_TT; idx += blockDim.x) {
+        const int k = idx / BC_TT, g = idx % BC_TT;
+        cs[k][g] = (i0 + g < nact) ? T.dn_mat[(size_t)k * T.nq + i0 + g] : 0;
+    }
+    __syncthreads();
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 *w = cp + (size_t)blockIdx.z * cp_stride + (size_t)nact * N;
+    BAcc acc[BC_TT];
+#pragma unroll
+    for (int g = 0; g < BC_TT; ++g) bacc_zero(acc[g]);
+    for (int k = 0; k < K; ++k) {
+        u32 y0, y1;
+        split_y(w[(size_t)k * N + n], y0, y1);
+#pragma unroll
+        for (int g = 0; g < BC_TT; ++g) bacc_mac(acc[g], y0, y1, cs[k][g]);
+    }
+    u64 *vo = v + (size_t)blockIdx.z * v_stride;
+#pragma unroll
+    for (int g = 0; g < BC_TT; ++g)
+        if (i0 + g < nact) vo[(size_t)(i0 + g) * N + n] = bacc_reduce(acc[g], T.modc[i0 + g]);
+}
+
+int launch_bconv_down(const Tables &T, int nact, int npoly, const u64 *cp, size_t cp_stride, u64 *v,
+                      size_t v_stride, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    dim3 g((unsigned)(N / BC_THREADS), (unsigned)((nact + BC_TT - 1) / BC_TT), (unsigned)npoly);
+    k_bconv_down<<<g, BC_THREADS, 0, st>>>(T, nact, cp, cp_stride, v, v_stride);
+    return launch_status("ModDown BConv launch");
+}
+
+struct OutPtrs {
+    u64 *p[2];
+};
+
+// P4: out = cp - v mod q (cp canonical, v lazy in [0, 4q)).
+__global__ void __launch_bounds__(256) k_down_final(Tables T, const u64 *cp, size_t cp_stride, const u64 *v,
+                                                    size_t v_stride, OutPtrs outs)
+{
+    const int i = blockIdx.y, x = blockIdx.z;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 q = T.modc[i].q, q2 = 2 * q;
+    u64 r = cp[x * cp_stride + (size_t)i * N + n] + 2 * q2 - v[x * v_stride + (size_t)i * N + n];
+    r = r >= 2 * q2 ? r - 2 * q2 : r;
+    outs.p[x][(size_t)i * N + n] = reduce4(r, q, q2);
+}
+
+int launch_down_final(const Tables &T, int nact, int npoly, const u64 *cp, size_t cp_stride, const u64 *v,
+                      size_t v_stride, u64 *const *outs, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    OutPtrs o;
+    o.p[0] = outs[0];
+    o.p[1] = npoly > 1 ? outs[1] : outs[0];
+    dim3 g((unsigned)(N / 256), (unsigned)nact, (unsigned)npoly);
+    k_down_final<<<g, 256, 0, st>>>(T, cp, cp_stride, v, v_stride, o);
+    return launch_status("ModDown final launch");
+}
+
+// ------------------------------------------------------------------ helpers
+// grid (N/256, nlimbs)
+__global__ void k_scale(Tables T, LimbMap m, const ulonglong2 *fac)
+{
+    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, T.logN);
+    if (L.skip) return;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 q = T.modc[L.tf].q;
+    const ulonglong2 f = fac[L.tf];
+    L.dst[n] = reduce2(shoup_lazy(L.src[n], f.x, f.y, q), q);
+}
+
+int launch_scale(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *factors_full, cudaStream_t st)
+{
+    if (nlimbs <= 0) return KS_OK;
+    const size_t N = (size_t)1 << T.logN;
+    k_scale<<<dim3((unsigned)(N / 256), nlimbs), 256, 0, st>>>(T, m, factors_full);
+    return launch_status("scale launch");
+}
+
+__global__ void k_canon(Tables T, LimbMap m)
+{
+    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, T.logN);
+    if (L.skip) return;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 q = T.modc[L.tf].q;
+    L.dst[n] = reduce4(L.src[n], q, 2 * q);
+}
+
+int launch_canon(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
+{
+    if (nlimbs <= 0) return KS_OK;
+    const size_t N = (size_t)1 << T.logN;
+    k_canon<<<dim3((unsigned)(N / 256), nlimbs), 256, 0, st>>>(T, m);
+    return launch_status("canonicalise launch");
+}
+
+// grid (N/256, nact, nd): D[j][t] = d[t] for t in digit j.
+__global__ void k_bypass_copy(Tables T, int nact, const u64 *d, u64 *D)
+{
+    const int t = blockIdx.y, j = blockIdx.z;
+    if (t / T.alpha != j) return;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nt = nact + T.kp;
+    D[((size_t)j * nt + t) * N + n] = d[(size_t)t * N + n];
+}
+
+int launch_bypass_copy(const Tables &T, int nact, const u64 *d, u64 *D, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    const int nd = (nact + T.alpha - 1) / T.alpha;
+    k_bypass_copy<<<dim3((unsigned)(N / 256), nact, nd), 256, 0, st>>>(T, nact, d, D);
+    return launch_status("bypass copy launch");
+}
+
+// ------------------------------------------------------------------ keys
+// evk [ndig][2][nfull][N] canonical -> * key_sc[t] (Montgomery factor folded).
+__global__ void k_key_convert(Tables T, u64 *evk)
+{
+    const int nfull = T.nq + T.kp;
+    const int limb = blockIdx.y;
+    const int tf = limb % nfull;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 q = T.modc[tf].q;
+    const ulonglong2 f = T.key_sc[tf];
+    u64 *p = evk + (size_t)limb * N + n;
+    *p = reduce2(shoup_lazy(*p, f.x, f.y, q), q);
+}
+
+int launch_key_convert(const Tables &T, u64 *evk, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    const int limbs = T.ndig * 2 * (T.nq + T.kp);
+    k_key_convert<<<dim3((unsigned)(N / 256), limbs), 256, 0, st>>>(T, evk);
+    return launch_status("key conversion launch");
+}
+
+// a*b mod q for arbitrary a, b < q (two Montgomery reductions).
+__device__ __forceinline__ u64 mulmod_dev(u64 a, u64 b, const ModC &m)
+{
+    U128 t = {0, 0};
+    mac128(t, a, b);
+    u64 r = reduce2(redc(t, m.q, m.mont), m.q);  // a*b*2^-64
+    U128 t2 = {0, 0};
+    mac128(t2, r, m.r2);
+    return reduce2(redc(t2, m.q, m.mont), m.q);  // * 2^128 * 2^-64
+}
+
+// grid (N/256, nfull, ndig)
+__global__ void k_keygen_combine(Tables T, const u64 *s_hat, const u64 *sp_hat, const u64 *e_hat, const u64 *pmod,
+                                 u64 *evk)
+{
+    const int tf = blockIdx.y, j = blockIdx.z;
+    const int nfull = T.nq + T.kp;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const ModC mc = T.modc[tf];
+    const u64 q = mc.q;
+    const u64 a = evk[(((size_t)j * 2 + 1) * nfull + tf) * N + n];
+    const u64 sh = s_hat[(size_t)tf * N + n];
+    const u64 sph = sp_hat[(size_t)tf * N + n];
+    const u64 eh = e_hat[((size_t)j * nfull + tf) * N + n];
+    u64 b = eh + q - mulmod_dev(a, sh, mc);
+    b = reduce2(b, q);
+    const bool in_digit = tf < T.nq && tf / T.alpha == j;
+    if (in_digit) b = reduce2(b + mulmod_dev(pmod[tf], sph, mc), q);
+    evk[(((size_t)j * 2 + 0) * nfull + tf) * N + n] = b;
+}
+
+int launch_keygen_combine(const Tables &T, const u64 *s_hat, const u64 *sp_hat, const u64 *e_hat, const u64 *pmod,
+                          u64 *evk, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    k_keygen_combine<<<dim3((unsigned)(N / 256), T.nq + T.kp, T.ndig), 256, 0, st>>>(T, s_hat, sp_hat, e_hat, pmod,
+                                                                                     evk);
+    return launch_status("keygen combine launch");
+}
+
+// grid (N/256, nfull, nvec): out[v][t][n] = in[v][n] mod r_t (signed input).
+__global__ void k_signed_to_towers(Tables T, const int64_t *in, u64 *out)
+{
+    const int tf = blockIdx.y, vi = blockIdx.z;
+    const int nfull = T.nq + T.kp;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 q = T.modc[tf].q;
+    const int64_t v = in[(size_t)vi * N + n];
+    const u64 mag = v < 0 ? (u64)(-(v + 1)) + 1 : (u64)v;
+    u64 r = mag % q;
+    if (v < 0 && r != 0) r = q - r;
+    out[((size_t)vi * nfull + tf) * N + n] = r;
+}
+
+int launch_signed_to_towers(const Tables &T, const int64_t *v, int nvec, u64 *out, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    k_signed_to_towers<<<dim3((unsigned)(N / 256), T.nq + T.kp, nvec), 256, 0, st>>>(T, v, out);
+    return launch_status("signed residue launch");
+}
+
+}  // namespace ks

@@ -1,0 +1,220 @@
+"""Thin ctypes binding of the C ABI in include/ks.h.
+
+Argument marshalling only: every step of key switching runs in the CUDA
+library.  Device buffers are torch tensors (dtype int64 holding the uint64
+bit patterns); streams are torch CUDA streams.  If the library has not been
+built, ``lib()`` raises -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+KS_OK, KS_EINVAL, KS_ENOMEM, KS_ECUDA, KS_ETIMEOUT, KS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+MP, DC, OC, AUTO = 0, 1, 2, 3
+DATAFLOWS = {"MP": MP, "DC": DC, "OC": OC, "AUTO": AUTO}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class KSError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"ks error {code}: {msg}")
+        self.code = code
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_void_p), ("level_towers", ctypes.c_uint32),
+                ("d_in", ctypes.c_void_p), ("d_out0", ctypes.c_void_p), ("d_out1", ctypes.c_void_p)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library missing at {path}: run paper_2311_01598_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        vp, u32, u64, ci = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+        pvp = ctypes.POINTER(ctypes.c_void_p)
+        L.ks_last_error.restype = ctypes.c_char_p
+        L.ks_params_create.argtypes = [u32, u32, u32, u32, vp, vp, u32, pvp]
+        L.ks_params_destroy.argtypes = [vp]
+        L.ks_params_destroy.restype = None
+        L.ks_params_info.argtypes = [vp, vp, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+        L.ks_keygen_upload.argtypes = [vp, vp, vp, u64, vp, pvp]
+        L.ks_key_upload_raw.argtypes = [vp, vp, vp, pvp]
+        L.ks_key_destroy.argtypes = [vp]
+        L.ks_key_destroy.restype = None
+        L.ks_key_bytes.argtypes = [vp]
+        L.ks_key_bytes.restype = ctypes.c_size_t
+        L.ks_switch.argtypes = [vp, vp, u32, vp, vp, vp, ci, vp]
+        L.ks_switch_batch.argtypes = [vp, u32, ctypes.POINTER(Job), ci, vp]
+        L.ks_ntt.argtypes = [vp, u32, u32, vp, ci, vp]
+        L.ks_modup.argtypes = [vp, u32, vp, vp, vp]
+        L.ks_moddown.argtypes = [vp, u32, vp, vp, vp]
+        for name in ("ks_params_create", "ks_params_info", "ks_keygen_upload", "ks_key_upload_raw", "ks_switch",
+                     "ks_switch_batch", "ks_ntt", "ks_modup", "ks_moddown"):
+            getattr(L, name).restype = ci
+        _lib = L
+        return L
+
+
+def exported_symbols() -> list[str]:
+    """Names declared in include/ks.h that the library must export."""
+    import re
+    hdr = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "ks.h")
+    with open(hdr) as f:
+        text = f.read()
+    return sorted(set(re.findall(r"\b(ks_[a-z_0-9]+)\s*\(", text)))
+
+
+def check(rc: int) -> None:
+    if rc != KS_OK:
+        raise KSError(rc, lib().ks_last_error().decode())
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous(), "tensor must be contiguous"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Key:
+    def __init__(self, params: "Params", handle: int):
+        self.params = params
+        self.handle = handle
+
+    @property
+    def nbytes(self) -> int:
+        return int(lib().ks_key_bytes(self.handle))
+
+    def close(self) -> None:
+        if self.handle:
+            lib().ks_key_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Params:
+    """A parameter set (N = 2^logN, nq = L+1 Q primes, kp = K P primes, dnum)."""
+
+    def __init__(self, logN: int, nq: int, kp: int, dnum: int, prime_bits: int = 54, q=None, p=None):
+        L = lib()
+        h = ctypes.c_void_p()
+        qa = pa = None
+        if q is not None:
+            qa = np.ascontiguousarray(q, dtype=np.uint64)
+            pa = np.ascontiguousarray(p, dtype=np.uint64)
+        check(L.ks_params_create(logN, nq, kp, dnum, _ptr(qa), _ptr(pa), prime_bits, ctypes.byref(h)))
+        self.handle = h.value
+        self.logN, self.N, self.nq, self.kp, self.dnum = logN, 1 << logN, nq, kp, dnum
+        qo = np.zeros(nq, dtype=np.uint64)
+        po = np.zeros(kp, dtype=np.uint64)
+        alpha, ndig = ctypes.c_uint32(), ctypes.c_uint32()
+        check(L.ks_params_info(self.handle, _ptr(qo), _ptr(po), ctypes.byref(alpha), ctypes.byref(ndig)))
+        self.q = [int(x) for x in qo]
+        self.p = [int(x) for x in po]
+        self.alpha, self.ndig = alpha.value, ndig.value
+
+    def close(self) -> None:
+        if self.handle:
+            lib().ks_params_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def active_digits(self, nact: int) -> int:
+        return (nact + self.alpha - 1) // self.alpha
+
+    # -- keys ---------------------------------------------------------------
+    def keygen(self, s, s_prime, seed: int, stream=None) -> Key:
+        s = np.ascontiguousarray(s, dtype=np.int8)
+        sp = np.ascontiguousarray(s_prime, dtype=np.int64)
+        h = ctypes.c_void_p()
+        check(lib().ks_keygen_upload(self.handle, _ptr(s), _ptr(sp), seed & (2**64 - 1), _stream_handle(stream),
+                                     ctypes.byref(h)))
+        return Key(self, h.value)
+
+    def upload_key(self, evk: np.ndarray, stream=None) -> Key:
+        evk = np.ascontiguousarray(evk, dtype=np.uint64)
+        assert evk.shape == (self.ndig, 2, self.nq + self.kp, self.N)
+        h = ctypes.c_void_p()
+        check(lib().ks_key_upload_raw(self.handle, _ptr(evk), _stream_handle(stream), ctypes.byref(h)))
+        return Key(self, h.value)
+
+    # -- key switching --------------------------------------------------------
+    def switch(self, key: Key, nact: int, d, out0, out1, dataflow=OC, stream=None) -> None:
+        df = DATAFLOWS[dataflow] if isinstance(dataflow, str) else dataflow
+        check(lib().ks_switch(self.handle, key.handle, nact, _ptr(d), _ptr(out0), _ptr(out1), df,
+                              _stream_handle(stream)))
+
+    def switch_batch(self, jobs, dataflow=OC, stream=None) -> None:
+        """jobs: iterable of (key, nact, d, out0, out1)."""
+        df = DATAFLOWS[dataflow] if isinstance(dataflow, str) else dataflow
+        jobs = list(jobs)
+        arr = (Job * max(1, len(jobs)))()
+        for i, (key, nact, d, o0, o1) in enumerate(jobs):
+            arr[i] = Job(key.handle, nact, _ptr(d).value, _ptr(o0).value, _ptr(o1).value)
+        check(lib().ks_switch_batch(self.handle, len(jobs), arr, df, _stream_handle(stream)))
+
+    # -- stages ----------------------------------------------------------------
+    def ntt(self, first_tower: int, data, inverse: bool = False, stream=None) -> None:
+        n = data.shape[0]
+        check(lib().ks_ntt(self.handle, first_tower, n, _ptr(data), 1 if inverse else 0, _stream_handle(stream)))
+
+    def modup(self, nact: int, d, ext, stream=None) -> None:
+        check(lib().ks_modup(self.handle, nact, _ptr(d), _ptr(ext), _stream_handle(stream)))
+
+    def moddown(self, nact: int, cp, out, stream=None) -> None:
+        check(lib().ks_moddown(self.handle, nact, _ptr(cp), _ptr(out), _stream_handle(stream)))
+
+
+# -- torch helpers (device memory only) ------------------------------------------
+def to_device(a: np.ndarray, device="cuda"):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)
+
+
+def to_host(t) -> np.ndarray:
+    return t.cpu().numpy().view(np.uint64)
+
+
+def empty(shape, device="cuda"):
+    import torch
+    return torch.empty(shape, dtype=torch.int64, device=device)
