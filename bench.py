@@ -1,0 +1,403 @@
+"""Benchmark: hybrid key switching at N=2^16, L+1=24 Q primes, K=8 P primes,
+dnum=3 (alpha=8), 54-bit primes -- the Output-Centric batched path, with the
+plain single-ciphertext Max-Parallel path beside it.
+
+One step = one ks_switch_batch call over B ciphertexts at the top level, each
+with its own Galois key (B distinct 96 MiB keys, so no key is reused within a
+step and every key switch streams its whole key).  Inputs and keys together
+exceed the 126 MB L2 (B=16: 192 MiB inputs, 1.5 GiB keys), so no L2 flush is
+needed between steps.
+
+Prints ONE JSON line (rank 0).  `value` is key-switches/s over the timed
+region on device-resident inputs; `e2e` is the same metric through
+ks_switch_batch_host (pinned host buffers, both copies inside the timed
+region); `roofline` describes the kernel with the largest share of device
+time, timed live with CUDA events on its launch stream.
+
+--impl reference times the CPU oracle (oracle/, plain C, OpenMP over towers)
+on this host's cores on the same workload and prints the same line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "key-switches/s at N=2^16 L+1=24 dnum=3, OC batched vs MP plain; % HBM roofline"
+UNIT = "key-switches/s"
+LOGN, NQ, KP, DNUM, BITS = 16, 24, 8, 3, 54
+N = 1 << LOGN
+LIMB = N * 8
+# algorithmic bytes of one key switch at the top level: input + key + both outputs
+ALG_BYTES_PER_KS = NQ * LIMB + DNUM * 2 * (NQ + KP) * LIMB + 2 * NQ * LIMB
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), float(m.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+# ------------------------------------------------------------------ workload model
+def algorithmic_work(nact=NQ):
+    """Per key switch at level nact: modular multiplications of every stage
+    (butterflies count one each) and bytes per kernel class.  Used for the
+    roofline of the dominant kernel."""
+    nt = nact + KP
+    alpha = (NQ + DNUM - 1) // DNUM
+    nd = (nact + alpha - 1) // alpha
+    a_last = nact - (nd - 1) * alpha
+    bfly = (N // 2) * LOGN
+    ntt = {
+        "modup_intt": nact,
+        "modup_ntt": sum(nt - min(alpha, nact - j * alpha) for j in range(nd)),
+        "moddown_intt": 2 * KP,
+        "moddown_ntt": 2 * nact,
+    }
+    n_ntt = sum(ntt.values())
+    bconv_up = sum(min(alpha, nact - j * alpha) * (nt - min(alpha, nact - j * alpha)) for j in range(nd)) * N
+    bconv_down = 2 * KP * nact * N
+    key_mac = 2 * nd * nt * N
+    return {"ntt": n_ntt, "butterflies": n_ntt * bfly, "bconv_macs": bconv_up + bconv_down, "key_macs": key_mac,
+            "modmul": n_ntt * bfly + bconv_up + bconv_down + key_mac + nact * N, "a_last": a_last}
+
+
+def class_work(nact=NQ):
+    """Algorithmic work of the Output-Centric schedule per key switch, per
+    kernel class: (modular multiplications, bytes that must cross the
+    kernel's boundary).  A butterfly counts one modmul; each base-conversion
+    or key multiply-accumulate one; bytes are each limb read or written once
+    by the kernel (1 limb = N words of 8 bytes)."""
+    alpha = (NQ + DNUM - 1) // DNUM
+    nd = (nact + alpha - 1) // alpha
+    al = [min(alpha, nact - j * alpha) for j in range(nd)]
+    K, half = KP, N // 2
+    LA = {16: 8, 17: 9}.get(LOGN, (LOGN + 1) // 2)
+    LB = LOGN - LA
+    q_modup = sum(nact - a for a in al)          # ModUp limbs produced for Q towers
+    w = {}
+    w["ntt_inv_row"] = (nact * half * LB, 2 * nact * LIMB)
+    w["ntt_inv_col"] = ((nact + 2 * K) * half * LA + nact * N, 2 * (nact + 2 * K) * LIMB)
+    fc = nd * K + q_modup + 2 * nact
+    w["ntt_fwd_col"] = (fc * half * LA, 2 * fc * LIMB)
+    w["bconv_up"] = (sum(a * (K + nact - a) for a in al) * N, (2 * nact + nd * K + q_modup) * LIMB)
+    w["bconv_down"] = (2 * K * nact * N, (2 * K + 2 * nact) * LIMB)
+    w["oc_row_p"] = ((nd * K + 2 * K) * half * LB + 2 * nd * K * N, (nd * K + 2 * nd * K + 2 * K) * LIMB)
+    w["oc_row_q"] = ((q_modup + 2 * nact) * half * LB + 2 * nd * nact * N,
+                     (q_modup + 2 * nact + nact + 2 * nd * nact + 2 * nact) * LIMB)
+    return w
+
+
+def workload_config(B, dataflow, world):
+    return {"workload": f"hybrid key switch N=2^16 L+1=24 K=8 dnum=3 alpha=8 54-bit primes, {B} "
+                        f"ciphertexts/step each with its own Galois key, {dataflow} batched",
+            "batch_per_gpu": B, "dataflow": dataflow, "parallelism": f"replicas x{world}",
+            "l2": "inputs+keys per step exceed L2 (no flush)"}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(seconds: float = 10.0, min_reps: int = 2):
+    """The oracle, as it stands, on this host's cores: key switches per
+    second on the same parameter set (bounded sample of whole key switches)."""
+    import numpy as np
+    from oracle import oracle as orc
+    from paper_2311_01598_gb300 import inputs
+    C = orc.Ctx(LOGN, NQ, KP, DNUM, bits=BITS)
+    s = inputs.ternary_secret(N, inputs.SEED_BASE + 1)
+    sp = inputs.galois_secret(s, inputs.galois_elements(N, 1, inputs.SEED_BASE + 2)[0])
+    evk = C.keygen(s, sp, seed=inputs.SEED_BASE + 3)
+    d = inputs.uniform_towers(C.q, N, seed=inputs.SEED_BASE + 4)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        C.keyswitch(NQ, d, evk)
+        reps += 1
+        el = time.perf_counter() - t0
+        if reps >= min_reps and el >= seconds:
+            break
+    del np
+    return reps / el, reps, el, orc.get_threads()
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--dataflow", default="OC", choices=["MP", "DC", "OC"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2311_01598_gb300 import build as kbuild
+    if rank == 0 and not os.path.exists(kbuild.LIB):
+        kbuild.build()
+    if dist is not None:
+        dist.barrier()
+    from paper_2311_01598_gb300 import inputs, ks
+
+    P = ks.Params(LOGN, NQ, KP, DNUM, prime_bits=BITS)
+    B = args.batch
+    s = inputs.ternary_secret(N, inputs.SEED_BASE + 1 + rank)
+    gals = inputs.galois_elements(N, B, seed=inputs.SEED_BASE + 2)
+    keys = [P.keygen(s, inputs.galois_secret(s, g), seed=inputs.SEED_BASE + 100 + i) for i, g in enumerate(gals)]
+    d = [ks.to_device(inputs.uniform_towers(P.q, N, seed=inputs.SEED_BASE + 1000 * (rank + 1) + i))
+         for i in range(B)]
+    o0 = [ks.empty((NQ, N)) for _ in range(B)]
+    o1 = [ks.empty((NQ, N)) for _ in range(B)]
+    jobs = [(keys[i], NQ, d[i], o0[i], o1[i]) for i in range(B)]
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1))
+
+    step = lambda: P.switch_batch(jobs, args.dataflow, stream)  # noqa: E731
+
+    # ---- headline: device-resident inputs, clocks sampled during the region
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    l0 = ks.kernel_launches()
+    ms = timed(step, args.steps, 0)
+    launches = ks.kernel_launches() - l0
+    clocks = sampler.stop()
+    ms_per_step = ms / args.steps
+    value = world * B * args.steps / (ms / 1e3)
+
+    # ---- per-kernel device time of the same workload (CUDA events per launch)
+    ks.profile_enable(True)
+    ms_prof = timed(step, args.steps, 0)
+    ks.profile_enable(False)
+    prof = ks.profile_collect()
+    top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+
+    # ---- the plain single-ciphertext paths beside it
+    singles = {}
+    for df in ("MP", "DC", "OC"):
+        f = lambda df=df: P.switch(keys[0], NQ, d[0], o0[0], o1[0], df, stream)  # noqa: E731
+        t = timed(f, args.steps, 3)
+        singles[df] = world * args.steps / (t / 1e3)
+
+    # ---- end to end through the host-buffer entry point
+    hin = [torch.empty((NQ, N), dtype=torch.int64, pin_memory=True) for _ in range(B)]
+    for i in range(B):
+        hin[i].copy_(d[i].cpu())
+    h0 = [torch.empty((NQ, N), dtype=torch.int64, pin_memory=True) for _ in range(B)]
+    h1 = [torch.empty((NQ, N), dtype=torch.int64, pin_memory=True) for _ in range(B)]
+    hjobs = [(keys[i], NQ, hin[i], h0[i], h1[i]) for i in range(B)]
+    e2e_step = lambda: P.switch_batch_host(hjobs, args.dataflow, stream)  # noqa: E731
+    ms_e2e = timed(e2e_step, args.steps, 3)
+    torch.cuda.synchronize()
+    e2e_ok = all(torch.equal(h0[i], o0[i].cpu()) and torch.equal(h1[i], o1[i].cpu()) for i in range(B))
+    e2e_value = world * B * args.steps / (ms_e2e / 1e3)
+
+    hbm_gbs, sm_max_mhz, peak_src = peaks()
+    hbm_achieved = value / world * ALG_BYTES_PER_KS / 1e9
+    work = algorithmic_work()
+
+    roofline = None
+    if top is not None:
+        name, (cnt, tot_ms) = top
+        model = class_work().get(name) if args.dataflow == "OC" else None
+        # integer-multiply peak: 152 SMs x 64 IMAD lanes/clk x max SM clock,
+        # 10 32-bit multiplies per 64-bit Shoup/Montgomery modular product
+        alu_peak = 152 * 64 * sm_max_mhz * 1e6 / 10 / 1e9
+        roofline = {"bound": "alu", "kernel": name, "unit": "Gmodmul/s", "peak": round(alu_peak, 2),
+                    "peak_basis": f"152 SMs x 64 int-mul lanes/clk x {sm_max_mhz:.0f} MHz / 10 per modmul",
+                    "traffic": None, "launches_per_step": cnt / args.steps,
+                    "per_launch_ms": round(tot_ms / cnt, 4), "share_of_step": round(tot_ms / ms_prof, 4)}
+        if model is not None:
+            mm_ks, by_ks = model
+            secs_per_ks = tot_ms / 1e3 / (args.steps * B)
+            achieved = mm_ks / secs_per_ks / 1e9
+            roofline.update({"achieved": round(achieved, 2), "frac": round(achieved / alu_peak, 4),
+                             "algorithmic_modmul_per_launch": int(mm_ks * B * args.steps / cnt),
+                             "algorithmic_bytes_per_launch": int(by_ks * B * args.steps / cnt),
+                             "hbm_frac_of_kernel": round(by_ks / secs_per_ks / 1e9 / hbm_gbs, 4)})
+        else:
+            roofline.update({"achieved": None, "frac": None})
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, reps, el, cores = oracle_rate()
+        cpu = {"value": round(rate, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{reps} whole key switches at N=2^16 L+1=24 K=8 dnum=3 ({el:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": workload_config(B, args.dataflow, world),
+            "mp_plain": {"value": round(singles["MP"], 2), "unit": UNIT, "note": "single ciphertext per call"},
+            "single_ciphertext": {k: round(v, 2) for k, v in singles.items()},
+            "oc_batched_over_mp_plain": round(value / singles["MP"], 3),
+            "hbm_roofline": {"achieved": round(hbm_achieved, 1), "peak": hbm_gbs, "unit": "GB/s",
+                             "frac": round(hbm_achieved / hbm_gbs, 4), "basis": f"{peak_src} copy bandwidth",
+                             "algorithmic_bytes_per_ks": ALG_BYTES_PER_KS},
+            "roofline": roofline,
+            "kernels": {k: {"launches": c, "ms": round(t, 3)} for k, (c, t) in sorted(prof.items(),
+                                                                                     key=lambda kv: -kv[1][1])},
+            "work_per_ks": work,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": B * NQ * LIMB,
+                    "d2h_bytes_per_step": 2 * B * NQ * LIMB, "outputs_match_device_path": e2e_ok},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on this host's cores, same metric."""
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    orc.build()
+    # each step: one whole key switch of the workload (bounded sample)
+    import numpy as np
+    from paper_2311_01598_gb300 import inputs
+    C = orc.Ctx(LOGN, NQ, KP, DNUM, bits=BITS)
+    s = inputs.ternary_secret(N, inputs.SEED_BASE + 1)
+    sp = inputs.galois_secret(s, inputs.galois_elements(N, 1, inputs.SEED_BASE + 2)[0])
+    evk = C.keygen(s, sp, seed=inputs.SEED_BASE + 3)
+    d = inputs.uniform_towers(C.q, N, seed=inputs.SEED_BASE + 4)
+    for _ in range(min(args.warmup, 1)):
+        C.keyswitch(NQ, d, evk)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        C.keyswitch(NQ, d, evk)
+    el = time.perf_counter() - t0
+    value = args.steps / el
+    del np
+    line = {
+        "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 2), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic", "impl": "reference",
+        "config": workload_config(args.batch, args.dataflow, world),
+        "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+                         "sample": f"each step one whole key switch of the workload ({args.steps} steps), "
+                                   f"CPU oracle (plain C, OpenMP over towers)"},
+        "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

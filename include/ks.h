@@ -8,7 +8,8 @@
  * scheduled under the Max-Parallel, Digit-Centric or Output-Centric
  * dataflow of Sec. IV.  All dataflows return bit-identical results: the
  * paper notes that the operation count of HKS does not depend on the
- * dataflow (Sec. IV-D), and every step here is exact integer arithmetic.
+ * dataflow (Sec. IV, arithmetic-intensity comparison with Table II), and
+ * every step here is exact integer arithmetic.
  *
  * Conventions shared by every entry point:
  *   - A polynomial over a set of primes is stored limb-major: tower t
@@ -57,10 +58,10 @@ typedef enum {
                    towers, every intermediate materialised in device memory */
     KS_DC = 1,  /* Digit-Centric (Sec. IV-B): ModUp P1-P5 one digit at a
                    time, partial sums accumulated, then ModDown            */
-    KS_OC = 2,  /* Output-Centric (Sec. IV-C): output towers computed with
-                   BConv fused into the NTT and the key product fused into
-                   its epilogue; P towers first, then Q towers with ModDown
-                   fused (readings: P-first order)                          */
+    KS_OC = 2,  /* Output-Centric (Sec. IV-C): BConv only to the towers of
+                   the section being produced, the key product and P5
+                   reduce fused into the NTT row pass; the special towers
+                   first, then the Q towers with ModDown fused in           */
     KS_AUTO = 3 /* let the library choose (autotuned schedule cache)         */
 } ks_dataflow;
 
@@ -74,11 +75,11 @@ const char *ks_last_error(void);
  *   k_p       : K special primes, 1 <= k_p <= 32
  *   dnum      : number of digits, 1 <= dnum <= n_q
  *   h_q, h_p  : optional explicit primes (both or neither; each must be a
- *               prime = 1 mod 2N below 2^61, all distinct).  With NULL the
+ *               prime = 1 mod 2N below 2^56, all distinct).  With NULL the
  *               prime rule applies: the n_q+k_p largest primes below
  *               2^prime_bits that are 1 mod 2N, descending; the first k_p
  *               become p_0.., the rest q_0, q_1, ...
- *   prime_bits: 30..61, used only when h_q/h_p are NULL.
+ *   prime_bits: 30..56, used only when h_q/h_p are NULL.
  * Uploads twiddle and base-conversion tables to the current device.
  * On success *out receives the handle. */
 int ks_params_create(uint32_t logN, uint32_t n_q, uint32_t k_p, uint32_t dnum,
@@ -166,6 +167,40 @@ int ks_modup(const ks_params *params, uint32_t level_towers, const uint64_t *d_i
  * iNTT(c'_P)))) * P^-1 (mod q_i).  Values canonical. */
 int ks_moddown(const ks_params *params, uint32_t level_towers, const uint64_t *d_cp,
                uint64_t *d_out, ks_stream_t stream);
+
+/* One job of a batched key switch whose data live in HOST memory. */
+typedef struct {
+    const ks_key *key;
+    uint32_t level_towers;
+    const uint64_t *h_in;  /* host [l+1][N] evaluation form                    */
+    uint64_t *h_out0;      /* host [l+1][N]                                    */
+    uint64_t *h_out1;      /* host [l+1][N]                                    */
+} ks_host_job;
+
+/* End-to-end batched key switch from host memory: for every job, copy the
+ * input to the device, key switch (as ks_switch), copy both outputs back.
+ * Copies run on two library-owned streams and overlap the key switch of
+ * the neighbouring jobs (double-buffered device staging owned by the
+ * params object); everything is ordered before work later queued on
+ * `stream`.  Host buffers should be page-locked for the copies to overlap.
+ * Returns after queueing; synchronise `stream` before reading outputs. */
+int ks_switch_batch_host(const ks_params *params, uint32_t n, const ks_host_job *h_jobs,
+                         ks_dataflow dataflow, ks_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Measurement hooks (used by the benchmark; cheap when disabled).
+ * ------------------------------------------------------------------- */
+
+/* Number of kernels this library has launched since it was loaded. */
+uint64_t ks_kernel_launches(void);
+
+/* When on, every kernel launch is bracketed by CUDA events on its stream. */
+void ks_profile_enable(int on);
+
+/* Synchronise the recorded events and return, per kernel name, the number of
+ * launches and their summed device time (ms) since the last collect; then
+ * clear.  names: max x 48 chars.  *n_out receives the number of names. */
+int ks_profile_collect(uint32_t max, char *names, double *total_ms, uint32_t *counts, uint32_t *n_out);
 
 #ifdef __cplusplus
 }

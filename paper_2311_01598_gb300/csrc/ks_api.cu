@@ -1,5 +1,6 @@
 // ks_api.cu -- C ABI entry points, parameter/key objects, per-stream scratch
 // and the Max-Parallel / Digit-Centric executors (CiFlow Sec. IV-A, IV-B).
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -17,6 +18,47 @@ int fail(int code, const std::string &msg)
 {
     tl_err = msg;
     return code;
+}
+
+// ------------------------------------------------------------------ launches
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<bool> g_prof{false};
+struct ProfRec {
+    const char *name;
+    cudaEvent_t e0, e1;
+};
+static std::mutex g_prof_mu;
+static std::vector<ProfRec> g_recs;
+static std::vector<cudaEvent_t> g_ev_pool;
+
+static cudaEvent_t pool_event()
+{
+    if (!g_ev_pool.empty()) {
+        cudaEvent_t e = g_ev_pool.back();
+        g_ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+LaunchScope::LaunchScope(cudaStream_t st, const char *name) : st_(st)
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (!g_prof.load(std::memory_order_relaxed)) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    ProfRec r{name, pool_event(), pool_event()};
+    cudaEventRecord(r.e0, st);
+    rec_ = (long)g_recs.size();
+    g_recs.push_back(r);
+}
+
+LaunchScope::~LaunchScope()
+{
+    if (rec_ < 0) return;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    cudaEventRecord(g_recs[rec_].e1, st_);
 }
 
 static int cuda_check(cudaError_t e, const char *what)
@@ -62,8 +104,53 @@ static int get_ws(ks_params *P, cudaStream_t st, bool need_D, Workspace **out)
     return KS_OK;
 }
 
+// Double-buffered device staging of the host-memory batch path.
+struct HostStage {
+    u64 *din[2] = {nullptr, nullptr}, *dout0[2] = {nullptr, nullptr}, *dout1[2] = {nullptr, nullptr};
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaEvent_t h2d[2] = {}, comp[2] = {}, d2h[2] = {};
+};
+
+static int get_stage(ks_params *P, HostStage **out)
+{
+    if (!P->stage) {
+        HostStage *h = new HostStage();
+        const size_t words = (size_t)P->nq * P->N;
+        int rc = KS_OK;
+        for (int i = 0; i < 2 && rc == KS_OK; ++i) {
+            if ((rc = ws_alloc(&h->din[i], words)) != KS_OK) break;
+            if ((rc = ws_alloc(&h->dout0[i], words)) != KS_OK) break;
+            if ((rc = ws_alloc(&h->dout1[i], words)) != KS_OK) break;
+            rc = cuda_check(cudaEventCreateWithFlags(&h->h2d[i], cudaEventDisableTiming), "event");
+            if (rc == KS_OK) rc = cuda_check(cudaEventCreateWithFlags(&h->comp[i], cudaEventDisableTiming), "event");
+            if (rc == KS_OK) rc = cuda_check(cudaEventCreateWithFlags(&h->d2h[i], cudaEventDisableTiming), "event");
+        }
+        if (rc == KS_OK) rc = cuda_check(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking), "stream");
+        if (rc == KS_OK) rc = cuda_check(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking), "stream");
+        P->stage = h;  // partially built stages are released by free_ws
+        if (rc != KS_OK) return rc;
+    }
+    *out = P->stage;
+    return KS_OK;
+}
+
 static void free_ws(ks_params *P)
 {
+    if (P->stage) {
+        HostStage *h = P->stage;
+        for (int i = 0; i < 2; ++i) {
+            u64 *bufs[] = {h->din[i], h->dout0[i], h->dout1[i]};
+            for (u64 *b : bufs)
+                if (b) cudaFree(b);
+            cudaEvent_t evs[] = {h->h2d[i], h->comp[i], h->d2h[i]};
+            for (cudaEvent_t e : evs)
+                if (e) cudaEventDestroy(e);
+        }
+        if (h->s_in) cudaStreamDestroy(h->s_in);
+        if (h->s_out) cudaStreamDestroy(h->s_out);
+        delete h;
+        P->stage = nullptr;
+    }
     for (auto &kv : P->ws) {
         Workspace *w = kv.second;
         u64 *bufs[] = {w->y, w->D, w->cp, w->v, w->tmp};
@@ -459,6 +546,93 @@ int ks_switch_batch(const ks_params *P, uint32_t n, const ks_job *jobs, ks_dataf
         if (rc) return rc;
     }
     return KS_OK;
+}
+
+int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs, ks_dataflow dataflow,
+                         ks_stream_t stream)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (n > 0 && !jobs) return fail(KS_EINVAL, "jobs is NULL");
+    if ((int)dataflow < 0 || (int)dataflow > 3) return fail(KS_EINVAL, "unknown dataflow");
+    for (uint32_t i = 0; i < n; ++i) {
+        const ks_host_job &j = jobs[i];
+        if (!j.key || j.key->params != P) return fail(KS_EINVAL, "key is NULL or belongs to another params object");
+        if (j.level_towers < 1 || j.level_towers > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
+        if (!j.h_in || !j.h_out0 || !j.h_out1) return fail(KS_EINVAL, "NULL host pointer");
+    }
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    ks_params *PP = const_cast<ks_params *>(P);
+    std::lock_guard<std::mutex> g(PP->host_mu);
+    HostStage *h = nullptr;
+    if ((rc = get_stage(PP, &h)) != KS_OK) return rc;
+    cudaStream_t cs = (cudaStream_t)stream;
+    for (uint32_t i = 0; i < n; ++i) {
+        const ks_host_job &j = jobs[i];
+        const int s = (int)(i & 1);
+        const size_t bytes = (size_t)j.level_towers * P->N * sizeof(u64);
+        // copy in once the key switch that last read this slot has finished
+        rc = cuda_check(cudaStreamWaitEvent(h->s_in, h->comp[s], 0), "wait");
+        if (rc == KS_OK) rc = cuda_check(cudaMemcpyAsync(h->din[s], j.h_in, bytes, cudaMemcpyHostToDevice, h->s_in), "H2D copy");
+        if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->h2d[s], h->s_in), "record");
+        // compute once the input is in and the slot's previous outputs are out
+        if (rc == KS_OK) rc = cuda_check(cudaStreamWaitEvent(cs, h->h2d[s], 0), "wait");
+        if (rc == KS_OK) rc = cuda_check(cudaStreamWaitEvent(cs, h->d2h[s], 0), "wait");
+        if (rc == KS_OK) rc = switch_one(PP, j.key, j.level_towers, h->din[s], h->dout0[s], h->dout1[s], dataflow, cs);
+        if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->comp[s], cs), "record");
+        // copy out
+        if (rc == KS_OK) rc = cuda_check(cudaStreamWaitEvent(h->s_out, h->comp[s], 0), "wait");
+        if (rc == KS_OK) rc = cuda_check(cudaMemcpyAsync(j.h_out0, h->dout0[s], bytes, cudaMemcpyDeviceToHost, h->s_out), "D2H copy");
+        if (rc == KS_OK) rc = cuda_check(cudaMemcpyAsync(j.h_out1, h->dout1[s], bytes, cudaMemcpyDeviceToHost, h->s_out), "D2H copy");
+        if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->d2h[s], h->s_out), "record");
+        if (rc) return rc;
+    }
+    // later work on the caller's stream is ordered after every copy-out
+    for (int s = 0; s < 2; ++s)
+        if ((rc = cuda_check(cudaStreamWaitEvent(cs, h->d2h[s], 0), "wait")) != KS_OK) return rc;
+    return KS_OK;
+}
+
+uint64_t ks_kernel_launches(void) { return g_launches.load(); }
+
+void ks_profile_enable(int on) { g_prof.store(on != 0); }
+
+int ks_profile_collect(uint32_t max, char *names, double *total_ms, uint32_t *counts, uint32_t *n_out)
+{
+    if (!n_out || (max > 0 && (!names || !total_ms || !counts))) return fail(KS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    std::vector<std::string> keys;
+    std::vector<double> ms;
+    std::vector<uint32_t> cnt;
+    int rc = KS_OK;
+    for (ProfRec &r : g_recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.e1) != cudaSuccess || cudaEventElapsedTime(&t, r.e0, r.e1) != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(KS_ECUDA, "profiling event query failed");
+        }
+        size_t k = 0;
+        while (k < keys.size() && keys[k] != r.name) ++k;
+        if (k == keys.size()) {
+            keys.push_back(r.name);
+            ms.push_back(0.0);
+            cnt.push_back(0);
+        }
+        ms[k] += t;
+        cnt[k] += 1;
+        g_ev_pool.push_back(r.e0);
+        g_ev_pool.push_back(r.e1);
+    }
+    g_recs.clear();
+    const uint32_t m = (uint32_t)std::min<size_t>(keys.size(), max);
+    for (uint32_t i = 0; i < m; ++i) {
+        std::strncpy(names + (size_t)i * 48, keys[i].c_str(), 47);
+        names[(size_t)i * 48 + 47] = 0;
+        total_ms[i] = ms[i];
+        counts[i] = cnt[i];
+    }
+    *n_out = (uint32_t)keys.size();
+    return rc;
 }
 
 int ks_ntt(const ks_params *P, uint32_t first_tower, uint32_t n_towers, uint64_t *d_data, int inverse,

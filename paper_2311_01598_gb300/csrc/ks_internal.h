@@ -74,6 +74,7 @@ struct UpOffsets {
 };
 
 struct Workspace;
+struct HostStage;
 
 }  // namespace ks
 
@@ -96,6 +97,9 @@ struct ks_params {
     // per-stream scratch
     std::mutex mu;
     std::map<void *, ks::Workspace *> ws;
+    // double-buffered device staging of ks_switch_batch_host
+    std::mutex host_mu;
+    ks::HostStage *stage = nullptr;
 };
 
 struct ks_key {
@@ -105,6 +109,26 @@ struct ks_key {
 };
 
 namespace ks {
+
+// Every kernel launch of the library runs inside a LaunchScope: the scope
+// counts the launch and, while profiling is on, brackets it with CUDA events
+// recorded on the launch stream (ks_profile_collect sums them per name).
+class LaunchScope {
+  public:
+    LaunchScope(cudaStream_t st, const char *name);
+    ~LaunchScope();
+    LaunchScope(const LaunchScope &) = delete;
+    LaunchScope &operator=(const LaunchScope &) = delete;
+
+  private:
+    cudaStream_t st_;
+    long rec_ = -1;
+};
+#define KS_LAUNCH(st, name, ...)              \
+    do {                                      \
+        ::ks::LaunchScope ks_scope_(st, name); \
+        __VA_ARGS__;                          \
+    } while (0)
 
 // Thread-local error message (ks_last_error).
 void set_error(const std::string &msg);

@@ -165,13 +165,13 @@ static void ntt_fwd_S(const Tables &T, const LimbMap &m, int nlimbs, bool canoni
 {
     set_smem_attrs<S>();
     dim3 ga((1 << S::LB) / S::COLS, nlimbs), gb((1 << S::LA) / S::ROWS, nlimbs);
-    k_fwd_col<S><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m);
+    KS_LAUNCH(st, "ntt_fwd_col", k_fwd_col<S><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
     LimbMap m2 = m;
     m2.src = m.dst;
     if (canonical)
-        k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m2);
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m2));
     else
-        k_fwd_row<S, false><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m2);
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, false><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m2));
 }
 
 template <class S>
@@ -180,15 +180,15 @@ static void ntt_inv_S(const Tables &T, const LimbMap &m, int nlimbs, const ulong
 {
     set_smem_attrs<S>();
     dim3 ga((1 << S::LB) / S::COLS, nlimbs), gb((1 << S::LA) / S::ROWS, nlimbs);
-    k_inv_row<S><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m);
+    KS_LAUNCH(st, "ntt_inv_row", k_inv_row<S><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
     LimbMap m2 = m;
     m2.src = m.dst;
     if (scale)
-        k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, scale);
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, scale));
     else if (ninv)
-        k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, nullptr);
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, nullptr));
     else
-        k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, nullptr);
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, nullptr));
 }
 
 #define KS_DISPATCH_LOGN(logN, FN, ...)                                                                   \
@@ -208,7 +208,7 @@ template <class S>
 static void fwd_col_S(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
 {
     set_smem_attrs<S>();
-    k_fwd_col<S><<<dim3((1 << S::LB) / S::COLS, nlimbs), S::THREADS_A, S::SMEM_A, st>>>(T, m);
+    KS_LAUNCH(st, "ntt_fwd_col", k_fwd_col<S><<<dim3((1 << S::LB) / S::COLS, nlimbs), S::THREADS_A, S::SMEM_A, st>>>(T, m));
 }
 
 template <class S>
@@ -218,11 +218,11 @@ static void inv_col_S(const Tables &T, const LimbMap &m, int nlimbs, const ulong
     set_smem_attrs<S>();
     dim3 ga((1 << S::LB) / S::COLS, nlimbs);
     if (scale)
-        k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, scale);
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, scale));
     else if (ninv)
-        k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, nullptr);
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, nullptr));
     else
-        k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, nullptr);
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, nullptr));
 }
 
 int launch_fwd_col(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
@@ -340,7 +340,7 @@ int launch_bconv_up_range(const Tables &T, int nact, int t_begin, int t_end, int
     if (t_end <= t_begin) return KS_OK;
     DigitOffs o = digit_offsets(T, nact);
     dim3 g((unsigned)(N / BC_THREADS), (unsigned)((t_end - t_begin + BC_TT - 1) / BC_TT), (unsigned)nd);
-    k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, nact, -1, t_begin, t_end, t_base, o, y, D, dstride);
+    KS_LAUNCH(st, "bconv_up", k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, nact, -1, t_begin, t_end, t_base, o, y, D, dstride));
     return launch_status("ModUp BConv launch");
 }
 
@@ -357,7 +357,7 @@ int launch_bconv_up_digit(const Tables &T, int nact, int j, const u64 *y, u64 *D
     const size_t N = (size_t)1 << T.logN;
     DigitOffs o = digit_offsets(T, nact);
     dim3 g((unsigned)(N / BC_THREADS), (unsigned)((nt + BC_TT - 1) / BC_TT), 1);
-    k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, nact, j, 0, nt, 0, o, y, Dj, 0);
+    KS_LAUNCH(st, "bconv_up", k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, nact, j, 0, nt, 0, o, y, Dj, 0));
     return launch_status("ModUp BConv launch");
 }
 
@@ -400,7 +400,8 @@ int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u6
 {
     const size_t N = (size_t)1 << T.logN;
     dim3 g((unsigned)(N / 256), (unsigned)(nact + T.kp));
-    k_apply_key<<<g, 256, 0, st>>>(T, nact, j_begin, j_end, d, D, D_digit_stride, evk, cp, accumulate ? 1 : 0);
+    KS_LAUNCH(st, "apply_key",
+              k_apply_key<<<g, 256, 0, st>>>(T, nact, j_begin, j_end, d, D, D_digit_stride, evk, cp, accumulate ? 1 : 0));
     return launch_status("apply-key launch");
 }
 
@@ -440,7 +441,7 @@ int launch_bconv_down(const Tables &T, int nact, int npoly, const u64 *cp, size_
 {
     const size_t N = (size_t)1 << T.logN;
     dim3 g((unsigned)(N / BC_THREADS), (unsigned)((nact + BC_TT - 1) / BC_TT), (unsigned)npoly);
-    k_bconv_down<<<g, BC_THREADS, 0, st>>>(T, nact, cp, cp_stride, v, v_stride);
+    KS_LAUNCH(st, "bconv_down", k_bconv_down<<<g, BC_THREADS, 0, st>>>(T, nact, cp, cp_stride, v, v_stride));
     return launch_status("ModDown BConv launch");
 }
 
@@ -469,7 +470,7 @@ int launch_down_final(const Tables &T, int nact, int npoly, const u64 *cp, size_
     o.p[0] = outs[0];
     o.p[1] = npoly > 1 ? outs[1] : outs[0];
     dim3 g((unsigned)(N / 256), (unsigned)nact, (unsigned)npoly);
-    k_down_final<<<g, 256, 0, st>>>(T, cp, cp_stride, v, v_stride, o);
+    KS_LAUNCH(st, "down_final", k_down_final<<<g, 256, 0, st>>>(T, cp, cp_stride, v, v_stride, o));
     return launch_status("ModDown final launch");
 }
 
@@ -489,7 +490,7 @@ int launch_scale(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2
 {
     if (nlimbs <= 0) return KS_OK;
     const size_t N = (size_t)1 << T.logN;
-    k_scale<<<dim3((unsigned)(N / 256), nlimbs), 256, 0, st>>>(T, m, factors_full);
+    KS_LAUNCH(st, "scale", k_scale<<<dim3((unsigned)(N / 256), nlimbs), 256, 0, st>>>(T, m, factors_full));
     return launch_status("scale launch");
 }
 
@@ -506,7 +507,7 @@ int launch_canon(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
 {
     if (nlimbs <= 0) return KS_OK;
     const size_t N = (size_t)1 << T.logN;
-    k_canon<<<dim3((unsigned)(N / 256), nlimbs), 256, 0, st>>>(T, m);
+    KS_LAUNCH(st, "canon", k_canon<<<dim3((unsigned)(N / 256), nlimbs), 256, 0, st>>>(T, m));
     return launch_status("canonicalise launch");
 }
 
@@ -525,7 +526,7 @@ int launch_bypass_copy(const Tables &T, int nact, const u64 *d, u64 *D, cudaStre
 {
     const size_t N = (size_t)1 << T.logN;
     const int nd = (nact + T.alpha - 1) / T.alpha;
-    k_bypass_copy<<<dim3((unsigned)(N / 256), nact, nd), 256, 0, st>>>(T, nact, d, D);
+    KS_LAUNCH(st, "bypass_copy", k_bypass_copy<<<dim3((unsigned)(N / 256), nact, nd), 256, 0, st>>>(T, nact, d, D));
     return launch_status("bypass copy launch");
 }
 
@@ -548,7 +549,7 @@ int launch_key_convert(const Tables &T, u64 *evk, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
     const int limbs = T.ndig * 2 * (T.nq + T.kp);
-    k_key_convert<<<dim3((unsigned)(N / 256), limbs), 256, 0, st>>>(T, evk);
+    KS_LAUNCH(st, "key_convert", k_key_convert<<<dim3((unsigned)(N / 256), limbs), 256, 0, st>>>(T, evk));
     return launch_status("key conversion launch");
 }
 
@@ -588,8 +589,8 @@ int launch_keygen_combine(const Tables &T, const u64 *s_hat, const u64 *sp_hat, 
                           u64 *evk, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
-    k_keygen_combine<<<dim3((unsigned)(N / 256), T.nq + T.kp, T.ndig), 256, 0, st>>>(T, s_hat, sp_hat, e_hat, pmod,
-                                                                                     evk);
+    KS_LAUNCH(st, "keygen_combine", k_keygen_combine<<<dim3((unsigned)(N / 256), T.nq + T.kp, T.ndig), 256, 0, st>>>(
+                                          T, s_hat, sp_hat, e_hat, pmod, evk));
     return launch_status("keygen combine launch");
 }
 
@@ -611,7 +612,7 @@ __global__ void k_signed_to_towers(Tables T, const int64_t *in, u64 *out)
 int launch_signed_to_towers(const Tables &T, const int64_t *v, int nvec, u64 *out, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
-    k_signed_to_towers<<<dim3((unsigned)(N / 256), T.nq + T.kp, nvec), 256, 0, st>>>(T, v, out);
+    KS_LAUNCH(st, "signed_to_towers", k_signed_to_towers<<<dim3((unsigned)(N / 256), T.nq + T.kp, nvec), 256, 0, st>>>(T, v, out));
     return launch_status("signed residue launch");
 }
 

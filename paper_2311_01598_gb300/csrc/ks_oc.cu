@@ -152,10 +152,13 @@ static void oc_rows_S(const Tables &T, int nact, int nd, const u64 *tmp1, const 
         attr = true;
     }
     if (p_section)
-        k_oc_rowP<S><<<dim3((1 << S::LA) / S::ROWS, T.kp), S::THREADS_B, S::SMEM_B, st>>>(T, nact, nd, tmp1, evk, cp);
+        KS_LAUNCH(st, "oc_row_p",
+                  k_oc_rowP<S><<<dim3((1 << S::LA) / S::ROWS, T.kp), S::THREADS_B, S::SMEM_B, st>>>(T, nact, nd, tmp1,
+                                                                                                  evk, cp));
     else
-        k_oc_rowQ<S><<<dim3((1 << S::LA) / S::ROWS, nact), S::THREADS_B, S::SMEM_B, st>>>(T, nact, nd, tmp2, d, evk,
-                                                                                          out0, out1);
+        KS_LAUNCH(st, "oc_row_q",
+                  k_oc_rowQ<S><<<dim3((1 << S::LA) / S::ROWS, nact), S::THREADS_B, S::SMEM_B, st>>>(
+                      T, nact, nd, tmp2, d, evk, out0, out1));
 }
 
 static int oc_rows(const Tables &T, int nact, int nd, const u64 *tmp1, const u64 *tmp2, const u64 *d,

@@ -29,6 +29,11 @@ class KSError(RuntimeError):
         self.code = code
 
 
+class HostJob(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_void_p), ("level_towers", ctypes.c_uint32),
+                ("h_in", ctypes.c_void_p), ("h_out0", ctypes.c_void_p), ("h_out1", ctypes.c_void_p)]
+
+
 class Job(ctypes.Structure):
     _fields_ = [("key", ctypes.c_void_p), ("level_towers", ctypes.c_uint32),
                 ("d_in", ctypes.c_void_p), ("d_out0", ctypes.c_void_p), ("d_out1", ctypes.c_void_p)]
@@ -66,8 +71,16 @@ def lib():
         L.ks_ntt.argtypes = [vp, u32, u32, vp, ci, vp]
         L.ks_modup.argtypes = [vp, u32, vp, vp, vp]
         L.ks_moddown.argtypes = [vp, u32, vp, vp, vp]
+        L.ks_switch_batch_host.argtypes = [vp, u32, ctypes.POINTER(HostJob), ci, vp]
+        L.ks_kernel_launches.argtypes = []
+        L.ks_kernel_launches.restype = ctypes.c_uint64
+        L.ks_profile_enable.argtypes = [ci]
+        L.ks_profile_enable.restype = None
+        L.ks_profile_collect.argtypes = [u32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(u32), ctypes.POINTER(u32)]
         for name in ("ks_params_create", "ks_params_info", "ks_keygen_upload", "ks_key_upload_raw", "ks_switch",
-                     "ks_switch_batch", "ks_ntt", "ks_modup", "ks_moddown"):
+                     "ks_switch_batch", "ks_ntt", "ks_modup", "ks_moddown", "ks_switch_batch_host",
+                     "ks_profile_collect"):
             getattr(L, name).restype = ci
         _lib = L
         return L
@@ -193,6 +206,16 @@ class Params:
             arr[i] = Job(key.handle, nact, _ptr(d).value, _ptr(o0).value, _ptr(o1).value)
         check(lib().ks_switch_batch(self.handle, len(jobs), arr, df, _stream_handle(stream)))
 
+    def switch_batch_host(self, jobs, dataflow=OC, stream=None) -> None:
+        """jobs: iterable of (key, nact, h_in, h_out0, h_out1) with host
+        buffers (pinned torch tensors or numpy arrays)."""
+        df = DATAFLOWS[dataflow] if isinstance(dataflow, str) else dataflow
+        jobs = list(jobs)
+        arr = (HostJob * max(1, len(jobs)))()
+        for i, (key, nact, hi, h0, h1) in enumerate(jobs):
+            arr[i] = HostJob(key.handle, nact, _ptr(hi).value, _ptr(h0).value, _ptr(h1).value)
+        check(lib().ks_switch_batch_host(self.handle, len(jobs), arr, df, _stream_handle(stream)))
+
     # -- stages ----------------------------------------------------------------
     def ntt(self, first_tower: int, data, inverse: bool = False, stream=None) -> None:
         n = data.shape[0]
@@ -203,6 +226,29 @@ class Params:
 
     def moddown(self, nact: int, cp, out, stream=None) -> None:
         check(lib().ks_moddown(self.handle, nact, _ptr(cp), _ptr(out), _stream_handle(stream)))
+
+
+# -- measurement hooks ---------------------------------------------------------------
+def kernel_launches() -> int:
+    return int(lib().ks_kernel_launches())
+
+
+def profile_enable(on: bool = True) -> None:
+    lib().ks_profile_enable(1 if on else 0)
+
+
+def profile_collect(max_names: int = 64) -> dict:
+    """{kernel name: (launches, total ms)} since the last collect."""
+    names = ctypes.create_string_buffer(48 * max_names)
+    ms = (ctypes.c_double * max_names)()
+    cnt = (ctypes.c_uint32 * max_names)()
+    n = ctypes.c_uint32()
+    check(lib().ks_profile_collect(max_names, names, ms, cnt, ctypes.byref(n)))
+    out = {}
+    for i in range(min(n.value, max_names)):
+        nm = names.raw[48 * i:48 * i + 48].split(b"\0", 1)[0].decode()
+        out[nm] = (int(cnt[i]), float(ms[i]))
+    return out
 
 
 # -- torch helpers (device memory only) ------------------------------------------

@@ -1,0 +1,46 @@
+"""Profiling driver: run a few key switches through the C ABI and exit.
+
+Used under ncu (the launch list and single-kernel captures under profiles/):
+    python -m paper_2311_01598_gb300.profile_ks --dataflow OC,MP
+    python -m paper_2311_01598_gb300.profile_ks --dataflow OC --batch 16
+Key generation runs first (a few launches), then one key switch per
+dataflow listed (or one batched call per dataflow with --batch B > 1).
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import inputs, ks
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dataflow", default="OC")
+    ap.add_argument("--logN", type=int, default=16)
+    ap.add_argument("--nq", type=int, default=24)
+    ap.add_argument("--kp", type=int, default=8)
+    ap.add_argument("--dnum", type=int, default=3)
+    ap.add_argument("--level", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=1)
+    a = ap.parse_args()
+    P = ks.Params(a.logN, a.nq, a.kp, a.dnum)
+    nact = a.level or a.nq
+    s = inputs.ternary_secret(P.N, 1)
+    key = P.keygen(s, inputs.galois_secret(s, 5), 7)
+    jobs = []
+    for i in range(a.batch):
+        d = ks.to_device(inputs.uniform_towers(P.q[:nact], P.N, 3 + i))
+        jobs.append((key, nact, d, ks.empty((nact, P.N)), ks.empty((nact, P.N))))
+    for df in a.dataflow.split(","):
+        if a.batch == 1:
+            P.switch(key, nact, jobs[0][2], jobs[0][3], jobs[0][4], df)
+        else:
+            P.switch_batch(jobs, df)
+    torch.cuda.synchronize()
+    print("ok launches", ks.kernel_launches())
+
+
+if __name__ == "__main__":
+    main()
