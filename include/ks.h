@@ -142,6 +142,28 @@ typedef struct {
 int ks_switch_batch(const ks_params *params, uint32_t n, const ks_job *h_jobs,
                     ks_dataflow dataflow, ks_stream_t stream);
 
+/* Key switch without allocating (the paper has no counterpart; this is a
+ * deployment aid).  For callers that cannot allocate device memory while
+ * running -- e.g. a server whose device memory is wholly owned by its own
+ * pool allocator, or a loop that cannot afford cudaMalloc's device-wide
+ * synchronisation.  Same inputs, outputs and result as ks_switch with
+ * KS_OC, but the scratch is one static device array of
+ * ks_switch_noalloc_max_words() words (32 MiB), reserved on every GPU that
+ * loads the library until the process exits.
+ *   - Requests needing more scratch (n_words grows with N, the level and K)
+ *     fail with KS_EINVAL and a message giving both sizes; nothing runs.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ *   - All calls share the one array: calls that may overlap on the GPU (on
+ *     different streams without ordering between them) race and must not be
+ *     issued.  Nothing in the array needs to start at zero. */
+int ks_switch_noalloc(const ks_params *params, const ks_key *key, uint32_t level_towers,
+                      const uint64_t *d_in, uint64_t *d_out0, uint64_t *d_out1, ks_stream_t stream);
+/* Words of the static scratch array of ks_switch_noalloc. */
+size_t ks_switch_noalloc_max_words(void);
+
 /* ---------------------------------------------------------------------
  * Stage entry points (the individual steps of Sec. III; used by the
  * parity tests and available to callers composing their own schedules).

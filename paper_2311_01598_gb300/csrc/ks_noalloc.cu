@@ -1,0 +1,103 @@
+// ks_noalloc.cu -- key switch that allocates nothing.
+//
+// Some callers cannot allocate device memory once they are running: a
+// serving process whose device memory is entirely reserved by its own pool
+// allocator (a third-party cudaMalloc would fail or fragment the pool), or a
+// latency-critical loop where cudaMalloc/cudaFree would synchronise the
+// device and stall every other stream.  ks_switch allocates its scratch on
+// first use per stream, so it does not suit them.  ks_switch_noalloc runs
+// the same Output-Centric key switch with its scratch in one file-scope
+// device array of fixed size, reserved when the library's device code is
+// loaded and held by every GPU that loads it until the process exits.
+#include <map>
+#include <mutex>
+
+#include "ks_internal.h"
+#include "ks_launch.h"
+
+namespace ks {
+
+// 4 Mi words = 32 MiB of scratch.
+constexpr size_t kNoAllocScratchWords = (size_t)4 << 20;
+
+static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchWords];
+
+// Device address of the scratch array, looked up once per device.  In host
+// code the array's name is only a host-side stand-in; its device address
+// must come from cudaGetSymbolAddress, called with the device current.
+static std::mutex g_noalloc_mu;
+static std::map<int, u64 *> g_noalloc_addr;
+
+static int noalloc_scratch(int device, u64 **out)
+{
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    auto it = g_noalloc_addr.find(device);
+    if (it != g_noalloc_addr.end()) {
+        *out = it->second;
+        return KS_OK;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, std::string("cudaGetSymbolAddress of the no-allocation scratch failed: ") +
+                                  cudaGetErrorString(e));
+    }
+    g_noalloc_addr[device] = (u64 *)p;
+    *out = (u64 *)p;
+    return KS_OK;
+}
+
+// Scratch words the Output-Centric schedule needs at level nact: y (nact
+// limbs), the section temporaries (max(nd*K, (nd+2)*nact) limbs) and c'
+// (2*(nact+K) limbs).
+static size_t noalloc_words(const ks_params *P, int nact)
+{
+    const size_t nd = (size_t)(nact + P->alpha - 1) / P->alpha;
+    const size_t tmp = std::max(nd * P->kp, (nd + 2) * (size_t)nact);
+    return ((size_t)nact + tmp + 2 * ((size_t)nact + P->kp)) * P->N;
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+extern "C" size_t ks_switch_noalloc_max_words(void) { return kNoAllocScratchWords; }
+
+extern "C" int ks_switch_noalloc(const ks_params *P, const ks_key *K, uint32_t level_towers, const uint64_t *d_in,
+                                 uint64_t *d_out0, uint64_t *d_out1, ks_stream_t stream)
+{
+    if (!P) return fail(KS_EINVAL, "params is NULL");
+    if (!K || K->params != P) return fail(KS_EINVAL, "key is NULL or belongs to another params object");
+    if (level_towers < 1 || level_towers > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
+    if (!d_in || !d_out0 || !d_out1) return fail(KS_EINVAL, "NULL data pointer");
+    const size_t bytes = (size_t)level_towers * P->N * sizeof(u64);
+    auto overlap = [bytes](const void *a, const void *b) {
+        const char *x = (const char *)a, *y = (const char *)b;
+        return x < y + bytes && y < x + bytes;
+    };
+    if (overlap(d_in, d_out0) || overlap(d_in, d_out1) || overlap(d_out0, d_out1))
+        return fail(KS_EINVAL, "d_in, d_out0, d_out1 overlap");
+    const int nact = (int)level_towers;
+    const size_t need = noalloc_words(P, nact);
+    if (need > kNoAllocScratchWords)
+        return fail(KS_EINVAL, "ks_switch_noalloc: this parameter set and level need " + std::to_string(need) +
+                                   " scratch words, the static buffer holds " +
+                                   std::to_string(kNoAllocScratchWords) + " (32 MiB); use ks_switch");
+    if (cudaSetDevice(P->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "cudaSetDevice failed");
+    }
+    u64 *base = nullptr;
+    int rc = noalloc_scratch(P->device, &base);
+    if (rc != KS_OK) return rc;
+    // Every scratch word the schedule reads is written earlier in the same
+    // call, so nothing needs clearing between calls.
+    const size_t N = P->N;
+    const int nd = (nact + P->alpha - 1) / P->alpha;
+    u64 *y = base;
+    u64 *tmp = y + (size_t)nact * N;
+    u64 *cp = tmp + std::max((size_t)nd * P->kp, (size_t)(nd + 2) * nact) * N;
+    const ulonglong2 *pre = P->d_up_pre_lvl + (size_t)(nact - 1) * P->nq;
+    return launch_oc(P->tables, nact, d_in, K->d_evk, d_out0, d_out1, y, tmp, cp, pre, (cudaStream_t)stream);
+}

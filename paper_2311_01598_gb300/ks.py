@@ -72,6 +72,10 @@ def lib():
         L.ks_modup.argtypes = [vp, u32, vp, vp, vp]
         L.ks_moddown.argtypes = [vp, u32, vp, vp, vp]
         L.ks_switch_batch_host.argtypes = [vp, u32, ctypes.POINTER(HostJob), ci, vp]
+        L.ks_switch_noalloc.argtypes = [vp, vp, u32, vp, vp, vp, vp]
+        L.ks_switch_noalloc.restype = ci
+        L.ks_switch_noalloc_max_words.argtypes = []
+        L.ks_switch_noalloc_max_words.restype = ctypes.c_size_t
         L.ks_kernel_launches.argtypes = []
         L.ks_kernel_launches.restype = ctypes.c_uint64
         L.ks_profile_enable.argtypes = [ci]
@@ -196,6 +200,12 @@ class Params:
         df = DATAFLOWS[dataflow] if isinstance(dataflow, str) else dataflow
         check(lib().ks_switch(self.handle, key.handle, nact, _ptr(d), _ptr(out0), _ptr(out1), df,
                               _stream_handle(stream)))
+
+    def switch_noalloc(self, key: Key, nact: int, d, out0, out1, stream=None) -> None:
+        """ks_switch_noalloc: Output-Centric key switch using the library's
+        static scratch array instead of allocated scratch."""
+        check(lib().ks_switch_noalloc(self.handle, key.handle, nact, _ptr(d), _ptr(out0), _ptr(out1),
+                                      _stream_handle(stream)))
 
     def switch_batch(self, jobs, dataflow=OC, stream=None) -> None:
         """jobs: iterable of (key, nact, d, out0, out1)."""
