@@ -284,6 +284,14 @@ def main():
     prof = ks.profile_collect()
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
 
+    # ---- both Output-Centric variants on the same batch (schedule comparison)
+    variants = {}
+    for vname, v in (("fused", 0), ("split", 1)):
+        sc = ks.Schedule(2, v, 64, 0)
+        f = lambda sc=sc: P.switch_batch_sched(jobs, sc, stream)  # noqa: E731
+        t = timed(f, max(3, args.steps // 2), 2)
+        variants[vname] = round(world * B * max(3, args.steps // 2) / (t / 1e3), 2)
+
     # ---- the plain single-ciphertext paths beside it
     singles = {}
     for df in ("MP", "DC", "OC"):
@@ -345,6 +353,8 @@ def main():
             "mp_plain": {"value": round(singles["MP"], 2), "unit": UNIT, "note": "single ciphertext per call"},
             "single_ciphertext": {k: round(v, 2) for k, v in singles.items()},
             "oc_batched_over_mp_plain": round(value / singles["MP"], 3),
+            "oc_variants": variants,
+            "schedule": list(P.default_schedule().as_tuple()),
             "hbm_roofline": {"achieved": round(hbm_achieved, 1), "peak": hbm_gbs, "unit": "GB/s",
                              "frac": round(hbm_achieved / hbm_gbs, 4), "basis": f"{peak_src} copy bandwidth",
                              "algorithmic_bytes_per_ks": ALG_BYTES_PER_KS},

@@ -190,6 +190,27 @@ int ks_modup(const ks_params *params, uint32_t level_towers, const uint64_t *d_i
 int ks_moddown(const ks_params *params, uint32_t level_towers, const uint64_t *d_cp,
                uint64_t *d_out, ks_stream_t stream);
 
+/* A schedule: how a batch is executed.  All schedules give identical
+ * results; they differ in speed only. */
+typedef struct {
+    int32_t dataflow;    /* KS_MP, KS_DC or KS_OC                                  */
+    int32_t oc_variant;  /* KS_OC: 0 = fused row kernels (row pass, key product,
+                            ModDown step in one kernel per row block), 1 = split
+                            (plain row pass, then a streaming combine kernel)     */
+    int32_t chunk;       /* KS_OC: jobs per batched launch group, 1..64           */
+    int32_t order;       /* 0 = jobs in the given order, 1 = grouped by level
+                            (descending), 2 = grouped by key                     */
+} ks_schedule;
+
+/* Batched key switch with an explicit schedule (see ks_schedule). */
+int ks_switch_batch_sched(const ks_params *params, uint32_t n, const ks_job *h_jobs,
+                          const ks_schedule *schedule, ks_stream_t stream);
+
+/* The schedule KS_OC and KS_AUTO use when no tuned entry applies
+ * (initially: Output-Centric, split variant, chunk 64, given order). */
+int ks_get_default_schedule(const ks_params *params, ks_schedule *out);
+int ks_set_default_schedule(ks_params *params, const ks_schedule *schedule);
+
 /* One job of a batched key switch whose data live in HOST memory. */
 typedef struct {
     const ks_key *key;
@@ -199,13 +220,14 @@ typedef struct {
     uint64_t *h_out1;      /* host [l+1][N]                                    */
 } ks_host_job;
 
-/* End-to-end batched key switch from host memory: for every job, copy the
- * input to the device, key switch (as ks_switch), copy both outputs back.
- * Copies run on two library-owned streams and overlap the key switch of
- * the neighbouring jobs (double-buffered device staging owned by the
- * params object); everything is ordered before work later queued on
- * `stream`.  Host buffers should be page-locked for the copies to overlap.
- * Returns after queueing; synchronise `stream` before reading outputs. */
+/* End-to-end batched key switch from host memory: copy the inputs to the
+ * device, key switch (results as ks_switch gives them), copy both outputs
+ * back.  Jobs run in chunks of 4 (batched launches under KS_OC/KS_AUTO); the
+ * copies of the next and previous chunk run on two library-owned streams
+ * while a chunk computes (double-buffered device staging owned by the params
+ * object), and everything is ordered before work later queued on `stream`.
+ * Host buffers should be page-locked for the copies to overlap.  Returns
+ * after queueing; synchronise `stream` before reading outputs. */
 int ks_switch_batch_host(const ks_params *params, uint32_t n, const ks_host_job *h_jobs,
                          ks_dataflow dataflow, ks_stream_t stream);
 

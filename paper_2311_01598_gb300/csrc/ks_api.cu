@@ -1,5 +1,6 @@
 // ks_api.cu -- C ABI entry points, parameter/key objects, per-stream scratch
 // and the Max-Parallel / Digit-Centric executors (CiFlow Sec. IV-A, IV-B).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -74,8 +75,9 @@ struct Workspace {
     u64 *D = nullptr;    // [ndig][nq+kp][N] ModUp P2/P3 output (MP); digit 0 slot (DC)
     u64 *cp = nullptr;   // [2][nq+kp][N]    ModUp P5 output c'
     u64 *v = nullptr;    // [2][nq][N]       ModDown P2/P3 output
-    u64 *tmp = nullptr;  // Output-Centric half-transformed limbs
-    size_t tmp_words = 0;
+    u64 *oc = nullptr;   // Output-Centric scratch of one job at the top level
+    u64 *batch = nullptr;  // Output-Centric scratch of a batch
+    size_t batch_words = 0;
 };
 
 static int ws_alloc(u64 **p, size_t words)
@@ -95,18 +97,18 @@ static int get_ws(ks_params *P, cudaStream_t st, bool need_D, Workspace **out)
     if (!w->cp && (rc = ws_alloc(&w->cp, 2 * nt * N)) != KS_OK) return rc;
     if (!w->v && (rc = ws_alloc(&w->v, 2 * (size_t)P->nq * N)) != KS_OK) return rc;
     if (need_D && !w->D && (rc = ws_alloc(&w->D, (size_t)P->ndig * nt * N)) != KS_OK) return rc;
-    if (!w->tmp) {
-        const size_t words = std::max((size_t)P->ndig * P->kp, (size_t)(P->ndig + 2) * P->nq) * N;
-        if ((rc = ws_alloc(&w->tmp, words)) != KS_OK) return rc;
-        w->tmp_words = words;
-    }
+    if (!w->oc && (rc = ws_alloc(&w->oc, oc_scratch_words(P->tables, P->nq))) != KS_OK) return rc;
     *out = w;
     return KS_OK;
 }
 
-// Double-buffered device staging of the host-memory batch path.
+// Double-buffered device staging of the host-memory batch path: jobs run in
+// chunks of kHostChunk; chunk c computes while chunk c+1 is copied in and
+// chunk c-1 is copied out.
+constexpr int kHostChunk = 4;
 struct HostStage {
     u64 *din[2] = {nullptr, nullptr}, *dout0[2] = {nullptr, nullptr}, *dout1[2] = {nullptr, nullptr};
+    u64 *scratch = nullptr;  // Output-Centric scratch of one chunk
     cudaStream_t s_in = nullptr, s_out = nullptr;
     cudaEvent_t h2d[2] = {}, comp[2] = {}, d2h[2] = {};
 };
@@ -115,7 +117,8 @@ static int get_stage(ks_params *P, HostStage **out)
 {
     if (!P->stage) {
         HostStage *h = new HostStage();
-        const size_t words = (size_t)P->nq * P->N;
+        P->stage = h;  // partially built stages are released by free_ws
+        const size_t words = (size_t)kHostChunk * P->nq * P->N;
         int rc = KS_OK;
         for (int i = 0; i < 2 && rc == KS_OK; ++i) {
             if ((rc = ws_alloc(&h->din[i], words)) != KS_OK) break;
@@ -125,9 +128,9 @@ static int get_stage(ks_params *P, HostStage **out)
             if (rc == KS_OK) rc = cuda_check(cudaEventCreateWithFlags(&h->comp[i], cudaEventDisableTiming), "event");
             if (rc == KS_OK) rc = cuda_check(cudaEventCreateWithFlags(&h->d2h[i], cudaEventDisableTiming), "event");
         }
+        if (rc == KS_OK) rc = ws_alloc(&h->scratch, (size_t)kHostChunk * oc_scratch_words(P->tables, P->nq));
         if (rc == KS_OK) rc = cuda_check(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking), "stream");
         if (rc == KS_OK) rc = cuda_check(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking), "stream");
-        P->stage = h;  // partially built stages are released by free_ws
         if (rc != KS_OK) return rc;
     }
     *out = P->stage;
@@ -138,6 +141,7 @@ static void free_ws(ks_params *P)
 {
     if (P->stage) {
         HostStage *h = P->stage;
+        if (h->scratch) cudaFree(h->scratch);
         for (int i = 0; i < 2; ++i) {
             u64 *bufs[] = {h->din[i], h->dout0[i], h->dout1[i]};
             for (u64 *b : bufs)
@@ -153,7 +157,7 @@ static void free_ws(ks_params *P)
     }
     for (auto &kv : P->ws) {
         Workspace *w = kv.second;
-        u64 *bufs[] = {w->y, w->D, w->cp, w->v, w->tmp};
+        u64 *bufs[] = {w->y, w->D, w->cp, w->v, w->oc, w->batch};
         for (u64 *b : bufs)
             if (b) cudaFree(b);
         delete w;
@@ -176,13 +180,16 @@ static int run_moddown(const ks_params *P, Workspace *w, int nact, int npoly, u6
     int rc;
     // P1: iNTT of the special towers of each polynomial (N^-1 (P/p_k)^-1 is
     // folded into the key), canonical.
-    LimbMap mP{w->cp, w->cp, P->kp, nt, nact, nact, nact, -1};
-    if ((rc = launch_ntt_inv(T, mP, npoly * P->kp, nullptr, false, st)) != KS_OK) return rc;
+    LimbMap mP{w->cp, w->cp, nullptr, P->kp, nt, nact, nact, nact, -1};
+    if ((rc = launch_ntt_inv(T, one_map(mP, npoly * P->kp), false, st)) != KS_OK) return rc;
     // P2: fast base conversion P -> q_0..q_l (P^-1 folded into the matrix).
-    if ((rc = launch_bconv_down(T, nact, npoly, w->cp, (size_t)nt * N, w->v, (size_t)nact * N, st)) != KS_OK) return rc;
+    BDnJobs bd;
+    bd.n = 0;
+    add_bdn(bd, BDnJob{w->cp, (size_t)nt * N, w->v, (size_t)nact * N, nact, npoly});
+    if ((rc = launch_bconv_down(T, bd, st)) != KS_OK) return rc;
     // P3: NTT of the converted towers.
-    LimbMap mV{w->v, w->v, nact, nact, 0, 0, nact, -1};
-    if ((rc = launch_ntt_fwd(T, mV, npoly * nact, false, st)) != KS_OK) return rc;
+    LimbMap mV{w->v, w->v, nullptr, nact, nact, 0, 0, nact, -1};
+    if ((rc = launch_ntt_fwd(T, one_map(mV, npoly * nact), false, st)) != KS_OK) return rc;
     // P4: subtract.
     u64 *outs[2] = {out0, out1};
     return launch_down_final(T, nact, npoly, w->cp, (size_t)nt * N, w->v, (size_t)nact * N, outs, st);
@@ -199,13 +206,16 @@ static int run_mp(const ks_params *P, const ks_key *K, int nact, const u64 *d, u
     const int nd = active_digits(P, nact);
     int rc;
     // ModUp P1: iNTT and the (Q_j/q_i)^-1 prescale of every input tower.
-    LimbMap m1{d, w->y, nact, 0, 0, 0, nact, -1};
-    if ((rc = launch_ntt_inv(T, m1, nact, pre_level(P, nact), false, st)) != KS_OK) return rc;
+    LimbMap m1{d, w->y, pre_level(P, nact), nact, 0, 0, 0, nact, -1};
+    if ((rc = launch_ntt_inv(T, one_map(m1, nact), false, st)) != KS_OK) return rc;
     // P2: every digit to every other tower of D_l.
-    if ((rc = launch_bconv_up(T, nact, w->y, w->D, st)) != KS_OK) return rc;
+    BUpJobs bu;
+    bu.n = 0;
+    add_bup(bu, T, BUpJob{w->y, w->D, (size_t)nt * N, nact, 0, nt, 0, -1});
+    if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;
     // P3: NTT of the converted towers (digit towers are bypassed).
-    LimbMap mD{w->D, w->D, nt, nt, 0, 0, nact, 0};
-    if ((rc = launch_ntt_fwd(T, mD, nd * nt, false, st)) != KS_OK) return rc;
+    LimbMap mD{w->D, w->D, nullptr, nt, nt, 0, 0, nact, 0};
+    if ((rc = launch_ntt_fwd(T, one_map(mD, nd * nt), false, st)) != KS_OK) return rc;
     // P4 + P5: key product summed over digits.
     if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, K->d_evk, w->cp, false, st)) != KS_OK) return rc;
     return run_moddown(P, w, nact, 2, out0, out1, st);
@@ -218,27 +228,49 @@ static int run_dc(const ks_params *P, const ks_key *K, int nact, const u64 *d, u
                   cudaStream_t st)
 {
     const Tables &T = P->tables;
-    const size_t N = P->N;
     const int nt = nact + P->kp;
     const int nd = active_digits(P, nact);
     int rc;
     for (int j = 0; j < nd; ++j) {
         const int lo = j * P->alpha;
         const int a = std::min(P->alpha, nact - lo);
-        LimbMap m1{d, w->y, a, 0, lo, lo, nact, -1};
-        if ((rc = launch_ntt_inv(T, m1, a, pre_level(P, nact) + lo, false, st)) != KS_OK) return rc;
-        if ((rc = launch_bconv_up_digit(T, nact, j, w->y, w->D, st)) != KS_OK) return rc;
-        LimbMap mD{w->D, w->D, nt, nt, 0, 0, nact, j};
-        if ((rc = launch_ntt_fwd(T, mD, nt, false, st)) != KS_OK) return rc;
+        LimbMap m1{d, w->y, pre_level(P, nact) + lo, a, 0, lo, lo, nact, -1};
+        if ((rc = launch_ntt_inv(T, one_map(m1, a), false, st)) != KS_OK) return rc;
+        BUpJobs bu;
+        bu.n = 0;
+        add_bup(bu, T, BUpJob{w->y, w->D, 0, nact, 0, nt, 0, j});
+        if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;
+        LimbMap mD{w->D, w->D, nullptr, nt, nt, 0, 0, nact, j};
+        if ((rc = launch_ntt_fwd(T, one_map(mD, nt), false, st)) != KS_OK) return rc;
         if ((rc = launch_apply_key(T, nact, j, j + 1, d, w->D, 0, K->d_evk, w->cp, j > 0, st)) != KS_OK) return rc;
     }
     return run_moddown(P, w, nact, 2, out0, out1, st);
 }
 
+// ------------------------------------------------------------------ OC
+static OcJob oc_job(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, u64 *scratch)
+{
+    const size_t N = P->N;
+    const int nd = active_digits(P, nact);
+    OcJob J;
+    J.d = d;
+    J.out0 = out0;
+    J.out1 = out1;
+    J.evk = K->d_evk;
+    J.y = scratch;
+    J.tmp = J.y + (size_t)nact * N;
+    J.cp = J.tmp + std::max((size_t)nd * P->kp, (size_t)(nd + 2) * nact) * N;
+    J.pre = pre_level(P, nact);
+    J.nact = nact;
+    J.nd = nd;
+    return J;
+}
+
 static int run_oc(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, Workspace *w,
                   cudaStream_t st)
 {
-    return launch_oc(P->tables, nact, d, K->d_evk, out0, out1, w->y, w->tmp, w->cp, pre_level(P, nact), st);
+    OcJob J = oc_job(P, K, nact, d, out0, out1, w->oc);
+    return launch_oc(P->tables, 1, &J, P->sched.oc_variant, st);
 }
 
 static int check_params(const ks_params *P)
@@ -468,8 +500,8 @@ int ks_keygen_upload(const ks_params *P, const int8_t *h_s, const int64_t *h_s_p
     if (rc == KS_OK) rc = cuda_check(cudaMemcpyAsync(d_pmod, pmod.data(), nfull * 8, cudaMemcpyHostToDevice, st), "upload");
     if (rc == KS_OK) rc = launch_signed_to_towers(P->tables, d_vecs, nvec, d_res, st);
     if (rc == KS_OK) {
-        LimbMap m{d_res, d_res, nfull, nfull, 0, 0, P->nq, -1};
-        rc = launch_ntt_fwd(P->tables, m, nvec * nfull, true, st);
+        LimbMap m{d_res, d_res, nullptr, nfull, nfull, 0, 0, P->nq, -1};
+        rc = launch_ntt_fwd(P->tables, one_map(m, nvec * nfull), true, st);
     }
     if (rc == KS_OK)
         rc = launch_keygen_combine(P->tables, d_res, d_res + (size_t)nfull * N, d_res + 2 * (size_t)nfull * N, d_pmod,
@@ -492,8 +524,10 @@ static int switch_one(ks_params *P, const ks_key *K, uint32_t nact, const uint64
                       ks_dataflow df, cudaStream_t st)
 {
     Workspace *w = nullptr;
-    int rc = get_ws(P, st, df == KS_MP || df == KS_DC, &w);
+    const ks_dataflow eff = df == KS_AUTO ? (ks_dataflow)P->sched.dataflow : df;
+    int rc = get_ws(P, st, eff == KS_MP || eff == KS_DC, &w);
     if (rc) return rc;
+    if (df == KS_AUTO) df = (ks_dataflow)P->sched.dataflow;
     switch (df) {
     case KS_MP: return run_mp(P, K, (int)nact, d, o0, o1, w, st);
     case KS_DC: return run_dc(P, K, (int)nact, d, o0, o1, w, st);
@@ -530,21 +564,118 @@ int ks_switch(const ks_params *P, const ks_key *K, uint32_t level_towers, const 
                       (cudaStream_t)stream);
 }
 
-int ks_switch_batch(const ks_params *P, uint32_t n, const ks_job *jobs, ks_dataflow dataflow, ks_stream_t stream)
+static int check_schedule(const ks_schedule *sc)
+{
+    if (!sc) return fail(KS_EINVAL, "schedule is NULL");
+    if (sc->dataflow < KS_MP || sc->dataflow > KS_OC) return fail(KS_EINVAL, "schedule dataflow must be MP, DC or OC");
+    if (sc->oc_variant < 0 || sc->oc_variant > 1) return fail(KS_EINVAL, "schedule oc_variant must be 0 or 1");
+    if (sc->chunk < 1 || sc->chunk > kMaxBatch) return fail(KS_EINVAL, "schedule chunk must be in 1..64");
+    if (sc->order < 0 || sc->order > 2) return fail(KS_EINVAL, "schedule order must be 0, 1 or 2");
+    return KS_OK;
+}
+
+// Run a validated batch under a schedule.
+static int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st)
+{
+    int rc;
+    std::vector<uint32_t> idx(n);
+    for (uint32_t i = 0; i < n; ++i) idx[i] = i;
+    if (sc.order == 1)
+        std::stable_sort(idx.begin(), idx.end(),
+                         [&](uint32_t a, uint32_t b) { return jobs[a].level_towers > jobs[b].level_towers; });
+    else if (sc.order == 2)
+        std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return jobs[a].key < jobs[b].key; });
+    if (sc.dataflow == KS_MP || sc.dataflow == KS_DC) {
+        for (uint32_t i : idx) {
+            const ks_job &j = jobs[i];
+            rc = switch_one(P, j.key, j.level_towers, j.d_in, j.d_out0, j.d_out1, (ks_dataflow)sc.dataflow, st);
+            if (rc) return rc;
+        }
+        return KS_OK;
+    }
+    // Output-Centric: every stage launch covers a group of sc.chunk jobs, each
+    // with its own scratch.
+    Workspace *w = nullptr;
+    if ((rc = get_ws(P, st, false, &w)) != KS_OK) return rc;
+    size_t words = 0;
+    for (uint32_t i = 0; i < n; ++i) words += oc_scratch_words(P->tables, (int)jobs[i].level_towers);
+    {
+        std::lock_guard<std::mutex> g(P->mu);
+        if (w->batch_words < words) {
+            if (w->batch) {
+                // the old buffer may still be in use by queued work on this stream
+                cudaStreamSynchronize(st);
+                cudaFree(w->batch);
+                w->batch = nullptr;
+                w->batch_words = 0;
+            }
+            if ((rc = ws_alloc(&w->batch, words)) != KS_OK) return rc;
+            w->batch_words = words;
+        }
+    }
+    std::vector<OcJob> oj(n);
+    size_t off = 0;
+    for (uint32_t k = 0; k < n; ++k) {
+        const ks_job &j = jobs[idx[k]];
+        const int nact = (int)j.level_towers;
+        oj[k] = oc_job(P, j.key, nact, j.d_in, j.d_out0, j.d_out1, w->batch + off);
+        off += oc_scratch_words(P->tables, nact);
+    }
+    for (uint32_t i0 = 0; i0 < n; i0 += (uint32_t)sc.chunk) {
+        const int m = (int)std::min<uint32_t>((uint32_t)sc.chunk, n - i0);
+        if ((rc = launch_oc(P->tables, m, oj.data() + i0, sc.oc_variant, st)) != KS_OK) return rc;
+    }
+    return KS_OK;
+}
+
+static int check_batch(const ks_params *P, uint32_t n, const ks_job *jobs)
 {
     int rc = check_params(P);
     if (rc) return rc;
     if (n > 0 && !jobs) return fail(KS_EINVAL, "jobs is NULL");
-    if ((int)dataflow < 0 || (int)dataflow > 3) return fail(KS_EINVAL, "unknown dataflow");
     for (uint32_t i = 0; i < n; ++i)
         if ((rc = check_job(P, jobs[i].key, jobs[i].level_towers, jobs[i].d_in, jobs[i].d_out0, jobs[i].d_out1)) != KS_OK)
             return rc;
+    return KS_OK;
+}
+
+int ks_switch_batch(const ks_params *P, uint32_t n, const ks_job *jobs, ks_dataflow dataflow, ks_stream_t stream)
+{
+    int rc = check_batch(P, n, jobs);
+    if (rc) return rc;
+    if ((int)dataflow < 0 || (int)dataflow > 3) return fail(KS_EINVAL, "unknown dataflow");
     if ((rc = set_device(P)) != KS_OK) return rc;
-    for (uint32_t i = 0; i < n; ++i) {
-        rc = switch_one(const_cast<ks_params *>(P), jobs[i].key, jobs[i].level_towers, jobs[i].d_in, jobs[i].d_out0,
-                        jobs[i].d_out1, dataflow, (cudaStream_t)stream);
-        if (rc) return rc;
-    }
+    ks_schedule sc = P->sched;
+    if (dataflow == KS_MP || dataflow == KS_DC) sc.dataflow = dataflow;
+    if (dataflow == KS_OC) sc.dataflow = KS_OC;
+    return run_batch(const_cast<ks_params *>(P), n, jobs, sc, (cudaStream_t)stream);
+}
+
+int ks_switch_batch_sched(const ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule *schedule,
+                          ks_stream_t stream)
+{
+    int rc = check_batch(P, n, jobs);
+    if (rc) return rc;
+    if ((rc = check_schedule(schedule)) != KS_OK) return rc;
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    return run_batch(const_cast<ks_params *>(P), n, jobs, *schedule, (cudaStream_t)stream);
+}
+
+int ks_get_default_schedule(const ks_params *P, ks_schedule *out)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (!out) return fail(KS_EINVAL, "out is NULL");
+    *out = P->sched;
+    return KS_OK;
+}
+
+int ks_set_default_schedule(ks_params *P, const ks_schedule *schedule)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if ((rc = check_schedule(schedule)) != KS_OK) return rc;
+    P->sched = *schedule;
     return KS_OK;
 }
 
@@ -567,23 +698,54 @@ int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs
     HostStage *h = nullptr;
     if ((rc = get_stage(PP, &h)) != KS_OK) return rc;
     cudaStream_t cs = (cudaStream_t)stream;
-    for (uint32_t i = 0; i < n; ++i) {
-        const ks_host_job &j = jobs[i];
-        const int s = (int)(i & 1);
-        const size_t bytes = (size_t)j.level_towers * P->N * sizeof(u64);
-        // copy in once the key switch that last read this slot has finished
+    const size_t N = P->N;
+    const size_t slot_words = (size_t)P->nq * N;
+    const size_t scr = oc_scratch_words(P->tables, P->nq);
+    int c = 0;
+    for (uint32_t i0 = 0; i0 < n; i0 += kHostChunk, ++c) {
+        const int s = c & 1;
+        const uint32_t m = std::min<uint32_t>(kHostChunk, n - i0);
+        // copy the chunk in once the chunk that last used this slot is computed
         rc = cuda_check(cudaStreamWaitEvent(h->s_in, h->comp[s], 0), "wait");
-        if (rc == KS_OK) rc = cuda_check(cudaMemcpyAsync(h->din[s], j.h_in, bytes, cudaMemcpyHostToDevice, h->s_in), "H2D copy");
+        for (uint32_t k = 0; k < m && rc == KS_OK; ++k) {
+            const ks_host_job &j = jobs[i0 + k];
+            const size_t bytes = (size_t)j.level_towers * N * sizeof(u64);
+            rc = cuda_check(cudaMemcpyAsync(h->din[s] + k * slot_words, j.h_in, bytes, cudaMemcpyHostToDevice, h->s_in),
+                            "H2D copy");
+        }
         if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->h2d[s], h->s_in), "record");
-        // compute once the input is in and the slot's previous outputs are out
+        // compute once the inputs are in and the slot's previous outputs are out
         if (rc == KS_OK) rc = cuda_check(cudaStreamWaitEvent(cs, h->h2d[s], 0), "wait");
         if (rc == KS_OK) rc = cuda_check(cudaStreamWaitEvent(cs, h->d2h[s], 0), "wait");
-        if (rc == KS_OK) rc = switch_one(PP, j.key, j.level_towers, h->din[s], h->dout0[s], h->dout1[s], dataflow, cs);
+        if (rc == KS_OK) {
+            if (dataflow == KS_MP || dataflow == KS_DC) {
+                for (uint32_t k = 0; k < m && rc == KS_OK; ++k) {
+                    const ks_host_job &j = jobs[i0 + k];
+                    rc = switch_one(PP, j.key, j.level_towers, h->din[s] + k * slot_words,
+                                    h->dout0[s] + k * slot_words, h->dout1[s] + k * slot_words, dataflow, cs);
+                }
+            } else {
+                OcJob oj[kHostChunk];
+                for (uint32_t k = 0; k < m; ++k) {
+                    const ks_host_job &j = jobs[i0 + k];
+                    oj[k] = oc_job(P, j.key, (int)j.level_towers, h->din[s] + k * slot_words,
+                                   h->dout0[s] + k * slot_words, h->dout1[s] + k * slot_words, h->scratch + k * scr);
+                }
+                rc = launch_oc(P->tables, (int)m, oj, P->sched.oc_variant, cs);
+            }
+        }
         if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->comp[s], cs), "record");
         // copy out
         if (rc == KS_OK) rc = cuda_check(cudaStreamWaitEvent(h->s_out, h->comp[s], 0), "wait");
-        if (rc == KS_OK) rc = cuda_check(cudaMemcpyAsync(j.h_out0, h->dout0[s], bytes, cudaMemcpyDeviceToHost, h->s_out), "D2H copy");
-        if (rc == KS_OK) rc = cuda_check(cudaMemcpyAsync(j.h_out1, h->dout1[s], bytes, cudaMemcpyDeviceToHost, h->s_out), "D2H copy");
+        for (uint32_t k = 0; k < m && rc == KS_OK; ++k) {
+            const ks_host_job &j = jobs[i0 + k];
+            const size_t bytes = (size_t)j.level_towers * N * sizeof(u64);
+            rc = cuda_check(cudaMemcpyAsync(j.h_out0, h->dout0[s] + k * slot_words, bytes, cudaMemcpyDeviceToHost,
+                                            h->s_out), "D2H copy");
+            if (rc == KS_OK)
+                rc = cuda_check(cudaMemcpyAsync(j.h_out1, h->dout1[s] + k * slot_words, bytes, cudaMemcpyDeviceToHost,
+                                                h->s_out), "D2H copy");
+        }
         if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->d2h[s], h->s_out), "record");
         if (rc) return rc;
     }
@@ -643,9 +805,9 @@ int ks_ntt(const ks_params *P, uint32_t first_tower, uint32_t n_towers, uint64_t
     if (!d_data) return fail(KS_EINVAL, "NULL data");
     if ((uint64_t)first_tower + n_towers > (uint64_t)(P->nq + P->kp)) return fail(KS_EINVAL, "tower range outside the basis");
     if ((rc = set_device(P)) != KS_OK) return rc;
-    LimbMap m{d_data, d_data, (int)n_towers, 0, 0, (int)first_tower, P->nq, -1};
-    if (inverse) return launch_ntt_inv(P->tables, m, (int)n_towers, nullptr, true, (cudaStream_t)stream);
-    return launch_ntt_fwd(P->tables, m, (int)n_towers, true, (cudaStream_t)stream);
+    LimbMap m{d_data, d_data, nullptr, (int)n_towers, 0, 0, (int)first_tower, P->nq, -1};
+    if (inverse) return launch_ntt_inv(P->tables, one_map(m, (int)n_towers), true, (cudaStream_t)stream);
+    return launch_ntt_fwd(P->tables, one_map(m, (int)n_towers), true, (cudaStream_t)stream);
 }
 
 int ks_modup(const ks_params *P, uint32_t level_towers, const uint64_t *d_in, uint64_t *d_ext, ks_stream_t stream)
@@ -663,11 +825,14 @@ int ks_modup(const ks_params *P, uint32_t level_towers, const uint64_t *d_in, ui
     const int nt = nact + P->kp;
     const int nd = active_digits(P, nact);
     const Tables &T = P->tables;
-    LimbMap m1{d_in, w->y, nact, 0, 0, 0, nact, -1};
-    if ((rc = launch_ntt_inv(T, m1, nact, pre_level(P, nact), false, st)) != KS_OK) return rc;
-    if ((rc = launch_bconv_up(T, nact, w->y, d_ext, st)) != KS_OK) return rc;
-    LimbMap mD{d_ext, d_ext, nt, nt, 0, 0, nact, 0};
-    if ((rc = launch_ntt_fwd(T, mD, nd * nt, true, st)) != KS_OK) return rc;
+    LimbMap m1{d_in, w->y, pre_level(P, nact), nact, 0, 0, 0, nact, -1};
+    if ((rc = launch_ntt_inv(T, one_map(m1, nact), false, st)) != KS_OK) return rc;
+    BUpJobs bu;
+    bu.n = 0;
+    add_bup(bu, T, BUpJob{w->y, d_ext, (size_t)nt * P->N, nact, 0, nt, 0, -1});
+    if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;
+    LimbMap mD{d_ext, d_ext, nullptr, nt, nt, 0, 0, nact, 0};
+    if ((rc = launch_ntt_fwd(T, one_map(mD, nd * nt), true, st)) != KS_OK) return rc;
     return launch_bypass_copy(T, nact, d_in, d_ext, st);
 }
 
@@ -685,8 +850,8 @@ int ks_moddown(const ks_params *P, uint32_t level_towers, const uint64_t *d_cp, 
     const int nact = (int)level_towers;
     const int nt = nact + P->kp;
     // fold the ModDown factors in (the key normally carries them)
-    LimbMap ms{d_cp, w->cp, nt, 0, 0, 0, nact, -1};
-    if ((rc = launch_scale(P->tables, ms, nt, P->d_plain_sc, st)) != KS_OK) return rc;
+    LimbMap ms{d_cp, w->cp, nullptr, nt, 0, 0, 0, nact, -1};
+    if ((rc = launch_scale(P->tables, one_map(ms, nt), P->d_plain_sc, st)) != KS_OK) return rc;
     return run_moddown(P, w, nact, 1, d_out, d_out, st);
 }
 

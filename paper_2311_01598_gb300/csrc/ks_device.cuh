@@ -3,12 +3,14 @@
 // Modular arithmetic (all moduli q < 2^56, one uint64 per residue):
 //   * Shoup multiplication by a known constant w with w' = floor(w*2^64/q):
 //     a*w - floor(a*w'/2^64)*q lies in [0, 2q) for every a < 2^64 (Shoup).
-//   * Harvey's lazy butterflies: the forward (Cooley-Tukey) butterfly keeps
-//     values in [0, 4q), the inverse (Gentleman-Sande) one in [0, 2q).
+//   * Lazy butterflies (after Harvey): the forward (Cooley-Tukey) butterfly
+//     lets values grow by at most 2q per stage and is reduced once at the
+//     end; the inverse (Gentleman-Sande) one keeps them in [0, 2q).
 //   * Montgomery reduction (REDC) of a 128-bit sum of products with the
 //     stored key, whose factor 2^64 is folded in at upload.
 //   * Base conversion accumulates 28-bit-split partial products in three
-//     64-bit accumulators (no carries) and reduces once per output.
+//     64-bit accumulators (no carries) and reduces once per output with a
+//     Montgomery reduction (constants stored times 2^64).
 //
 // NTT structure.  The negacyclic NTT of N = 2^(LA+LB) points is the in-place
 // Cooley-Tukey network whose stage s pairs indices differing in bit
@@ -48,13 +50,22 @@ __device__ __forceinline__ u64 reduce4(u64 x, u64 q, u64 q2)  // [0, 4q) -> [0, 
     return x >= q ? x - q : x;
 }
 
-// Forward Harvey butterfly: X, Y in [0, 4q) -> [0, 4q).
+// Forward Cooley-Tukey butterfly without a per-stage correction of X: with
+// X, Y < B the outputs are below B + 2q (the Shoup product is below 2q for
+// any 64-bit Y), so a transform of at most 17 stages fed with values below
+// 4q ends below 38q < 2^62 for q < 2^56.  Consumers reduce with reduce_any.
 __device__ __forceinline__ void fwd_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2)
 {
-    u64 x = X >= q2 ? X - q2 : X;
-    u64 t = shoup_lazy(Y, w, wp, q);
-    X = x + t;
-    Y = x - t + q2;
+    const u64 t = shoup_lazy(Y, w, wp, q);
+    Y = X + q2 - t;
+    X = X + t;
+}
+
+// Any 64-bit x -> [0, q): Shoup product by 1 (into [0, 2q)), one correction.
+__device__ __forceinline__ u64 reduce_any(u64 x, u64 q, u64 one_sh)
+{
+    const u64 r = x - __umul64hi(x, one_sh) * q;
+    return r >= q ? r - q : r;
 }
 
 // Inverse Harvey butterfly: X, Y in [0, 2q) -> [0, 2q).
@@ -98,21 +109,37 @@ __device__ __forceinline__ void bacc_mac(BAcc &A, u32 y0, u32 y1, u64 csplit)
     A.a1 += (u64)y1 * c0;
     A.a2 += (u64)y1 * c1;
 }
-// (a0 + a1*2^28 + a2*2^56) mod q, lazily in [0, 2q).
+// Constants are stored times 2^64 (Montgomery form), so the accumulated value
+// S = a0 + a1*2^28 + a2*2^56 is reduced by one Montgomery reduction:
+// REDC(S) = S*2^-64 mod q = sum y*c mod q.  With at most 64 terms of
+// 56-bit factors S < 2^119 and S*2^-64 < q*(64q/2^64) < q, so the result lies
+// in [0, 2q).
 __device__ __forceinline__ u64 bacc_reduce(const BAcc &A, const ModC &m)
 {
-    u64 t0 = A.a0 - __umul64hi(A.a0, m.one_sh) * m.q;
-    u64 t1 = shoup_lazy(A.a1, m.r28, m.r28_sh, m.q);
-    u64 t2 = shoup_lazy(A.a2, m.r56, m.r56_sh, m.q);
-    u64 s = t0 + t1 + t2;  // [0, 6q)
-    const u64 q4 = 2 * m.q2;
-    s = s >= q4 ? s - q4 : s;
-    return s >= m.q2 ? s - m.q2 : s;
+    // 128-bit S from the three column sums
+    const u64 t1 = A.a1 << 28;
+    u64 lo = A.a0 + t1;
+    u64 hi = (A.a1 >> 36) + (lo < t1 ? 1 : 0);
+    const u64 t2 = A.a2 << 56;
+    lo += t2;
+    hi += (A.a2 >> 8) + (lo < t2 ? 1 : 0);
+    U128 S = {lo, hi};
+    return redc(S, m.q, m.mont);
 }
 __device__ __forceinline__ void split_y(u64 y, u32 &y0, u32 &y1)
 {
     y0 = (u32)y & ((1u << kSplit) - 1);
     y1 = (u32)(y >> kSplit);
+}
+
+// Bulk prefetch of a contiguous block into L2 (TMA, one instruction for the
+// whole block).  The bulk copy needs a 16-byte aligned address and a size
+// that is a multiple of 16 bytes; blocks of caller buffers that are only
+// 8-byte aligned are simply not prefetched.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes)
+{
+    if ((((uintptr_t)p) & 15) != 0 || (bytes & 15) != 0) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // ------------------------------------------------------------------ NTT shape
@@ -236,6 +263,19 @@ struct TwRow {
     const ulonglong2 *t;  // tower table
     int G;
     __device__ __forceinline__ ulonglong2 operator()(int s, int i) const { return __ldg(t + (G << s) + i); }
+};
+// Same table, fetched with a volatile load: kernels that run several row
+// transforms of one tower in a loop would otherwise keep every twiddle of the
+// row live in registers across iterations.
+struct TwRowV {
+    const ulonglong2 *t;
+    int G;
+    __device__ __forceinline__ ulonglong2 operator()(int s, int i) const
+    {
+        ulonglong2 r;
+        asm volatile("ld.global.nc.v2.u64 {%0, %1}, [%2];" : "=l"(r.x), "=l"(r.y) : "l"(t + (G << s) + i));
+        return r;
+    }
 };
 
 }  // namespace ks

@@ -95,6 +95,10 @@ static u64 brv(u64 x, int bits)
 
 static u64 split28(u64 c) { return (c & ((1ull << kSplit) - 1)) | ((c >> kSplit) << 32); }
 
+// c * 2^64 mod r: base-conversion constants are stored in Montgomery form, so
+// one Montgomery reduction of the 128-bit sum of products yields the sum mod r.
+static u64 to_mont(u64 c, u64 r) { return (u64)((((unsigned __int128)c) << 64) % r); }
+
 static ulonglong2 shoup_pair(u64 w, u64 q)
 {
     ulonglong2 r;
@@ -201,7 +205,7 @@ int build_tables(ks_params *P)
                     u64 hat = 1;
                     for (int k = 0; k < a; ++k)
                         if (k != i) hat = mulmod_h(hat, prim[lo + k] % r, r);
-                    mat.push_back(split28(hat));
+                    mat.push_back(split28(to_mont(hat, r)));
                 }
         }
     }
@@ -215,10 +219,19 @@ int build_tables(ks_params *P)
             pre_lvl[(size_t)(nact - 1) * P->nq + i] = pre[P->up_off.pre[j * (A + 1) + a] + (i - lo)];
         }
 
+    // ModUp matrix offset of each active digit, per level
+    std::vector<int> mat_lvl((size_t)P->nq * P->ndig, 0);
+    for (int nact = 1; nact <= P->nq; ++nact)
+        for (int j = 0; j * A < nact; ++j) {
+            int a = std::min(A, nact - j * A);
+            mat_lvl[(size_t)(nact - 1) * P->ndig + j] = P->up_off.mat[j * (A + 1) + a];
+        }
+
     // ModDown matrix: (P/p_k) * P^-1 = p_k^-1 mod q_i
     std::vector<u64> dn((size_t)P->kp * P->nq);
     for (int k = 0; k < P->kp; ++k)
-        for (int i = 0; i < P->nq; ++i) dn[(size_t)k * P->nq + i] = split28(invmod_h(P->p[k] % P->q[i], P->q[i]));
+        for (int i = 0; i < P->nq; ++i)
+            dn[(size_t)k * P->nq + i] = split28(to_mont(invmod_h(P->p[k] % P->q[i], P->q[i]), P->q[i]));
 
     // factors folded into the stored key
     std::vector<ulonglong2> ksc(nt), psc(nt);
@@ -247,6 +260,7 @@ int build_tables(ks_params *P)
     if ((rc = upload(&P->d_itw, itw)) != KS_OK) return rc;
     if ((rc = upload(&P->d_up_pre, pre)) != KS_OK) return rc;
     if ((rc = upload(&P->d_up_pre_lvl, pre_lvl)) != KS_OK) return rc;
+    if ((rc = upload(&P->d_up_mat_lvl, mat_lvl)) != KS_OK) return rc;
     if ((rc = upload(&P->d_up_mat, mat)) != KS_OK) return rc;
     if ((rc = upload(&P->d_dn_mat, dn)) != KS_OK) return rc;
     if ((rc = upload(&P->d_key_sc, ksc)) != KS_OK) return rc;
@@ -261,7 +275,7 @@ int build_tables(ks_params *P)
     T.dn_mat = P->d_dn_mat;
     T.key_sc = P->d_key_sc;
     T.plain_sc = P->d_plain_sc;
-    T.h_up_mat_off = P->up_off.mat.data();
+    T.up_mat_lvl = P->d_up_mat_lvl;
     T.logN = P->logN;
     T.nq = P->nq;
     T.kp = P->kp;
@@ -272,13 +286,14 @@ int build_tables(ks_params *P)
 
 void free_tables(ks_params *P)
 {
-    void *ptrs[] = {P->d_modc,   P->d_tw,     P->d_itw,    P->d_up_pre,  P->d_up_pre_lvl,
-                    P->d_up_mat, P->d_dn_mat, P->d_key_sc, P->d_plain_sc};
+    void *ptrs[] = {P->d_modc,   P->d_tw,     P->d_itw,    P->d_up_pre,   P->d_up_pre_lvl,
+                    P->d_up_mat, P->d_dn_mat, P->d_key_sc, P->d_plain_sc, P->d_up_mat_lvl};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     P->d_modc = nullptr;
     P->d_tw = P->d_itw = P->d_up_pre = P->d_up_pre_lvl = P->d_key_sc = P->d_plain_sc = nullptr;
     P->d_up_mat = P->d_dn_mat = nullptr;
+    P->d_up_mat_lvl = nullptr;
 }
 
 }  // namespace ks

@@ -61,8 +61,7 @@ struct Tables {
     const u64 *dn_mat;
     const ulonglong2 *key_sc;   // Montgomery-form fold factors (see header)
     const ulonglong2 *plain_sc; // the same factors without 2^64
-    const int *h_up_mat_off;  // HOST pointer: ModUp matrix offset of (digit j, active
-                              // towers a) at [j*(alpha+1)+a]; never read on the device
+    const int *up_mat_lvl;    // ModUp matrix offset of digit j at level nact: [(nact-1)*ndig + j]
     int logN;
     int nq, kp, alpha, ndig;
 };
@@ -90,6 +89,7 @@ struct ks_params {
     ulonglong2 *d_tw = nullptr, *d_itw = nullptr;
     ulonglong2 *d_up_pre = nullptr;
     ulonglong2 *d_up_pre_lvl = nullptr;  // [nq levels][nq]: ModUp P1 factor per level
+    int *d_up_mat_lvl = nullptr;         // [nq levels][ndig]: ModUp matrix offsets per level
     uint64_t *d_up_mat = nullptr;
     uint64_t *d_dn_mat = nullptr;
     ulonglong2 *d_key_sc = nullptr, *d_plain_sc = nullptr;
@@ -97,6 +97,8 @@ struct ks_params {
     // per-stream scratch
     std::mutex mu;
     std::map<void *, ks::Workspace *> ws;
+    // default schedule (KS_OC / KS_AUTO without a tuned entry)
+    ks_schedule sched{KS_OC, 1, 64, 0};
     // double-buffered device staging of ks_switch_batch_host
     std::mutex host_mu;
     ks::HostStage *stage = nullptr;

@@ -1,7 +1,7 @@
 // ks_kernels.cu -- NTT passes and the per-stage kernels of hybrid key
-// switching (CiFlow Sec. III: ModUp P1-P5, ModDown P1-P4).  The Max-Parallel
-// and Digit-Centric executors are built from these; the Output-Centric fused
-// kernels live in ks_oc.cu.
+// switching (CiFlow Sec. III: ModUp P1-P5, ModDown P1-P4).  Stage launches
+// take per-job descriptor tables (ks_launch.h), so one launch covers every
+// job of a batch.  The Output-Centric fused kernels live in ks_oc.cu.
 #include <algorithm>
 
 #include "ks_ntt_core.cuh"
@@ -9,14 +9,14 @@
 namespace ks {
 
 // ------------------------------------------------------------------ NTT passes
-// Forward column pass (stages 0..LA-1).  grid (2^LB/COLS, nlimbs).
+// Forward column pass (stages 0..LA-1).  grid (2^LB/COLS, limbs).
 template <class S>
-__global__ void __launch_bounds__(S::THREADS_A) k_fwd_col(Tables T, LimbMap m)
+__global__ void __launch_bounds__(S::THREADS_A) k_fwd_col(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
     ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(sm + (1 << S::LA) * S::COLS);
-    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
     const u64 q = T.modc[L.tf].q, q2 = 2 * q;
     const ulonglong2 *twt = T.tw + ((size_t)L.tf << S::LOGN);
@@ -43,15 +43,17 @@ __global__ void __launch_bounds__(S::THREADS_A) k_fwd_col(Tables T, LimbMap m)
         for (int k2 = 0; k2 < M; ++k2) L.dst[((size_t)((tau * NG + gg) * M + k2) << S::LB) + c] = x[gg * M + k2];
 }
 
-// Forward row pass (stages LA..logN-1).  grid (2^LA/ROWS, nlimbs).
+// Forward row pass (stages LA..logN-1).  grid (2^LA/ROWS, limbs).  Output
+// canonical (CANON) or lazy below 40q.
 template <class S, bool CANON>
-__global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMap m)
+__global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
-    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
-    const u64 q = T.modc[L.tf].q, q2 = 2 * q;
+    const ModC &mc = T.modc[L.tf];
+    const u64 q = mc.q, q2 = 2 * q;
     const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
     const int h = blockIdx.x * S::ROWS + rr;
     const TwRow tw{T.tw + ((size_t)L.tf << S::LOGN), (1 << S::LA) + h};
@@ -61,18 +63,19 @@ __global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMap m)
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) x[k] = gin[k * S::TB + tau];
     row_fwd_core<S>(x, tw, sm + rr * S::ROWPAD, tau, q, q2);
+    const u64 one_sh = CANON ? mc.one_sh : 0;
 #pragma unroll
-    for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = CANON ? reduce4(x[k], q, q2) : x[k];
+    for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = CANON ? reduce_any(x[k], q, one_sh) : x[k];
 }
 
-// Inverse row pass (stages logN-1..LA), first half of the iNTT.  Input in
-// [0, 2q); output in [0, 2q).
+// Inverse row pass (stages logN-1..LA), first half of the iNTT.  Input below
+// 2q; output below 2q.
 template <class S>
-__global__ void __launch_bounds__(S::THREADS_B) k_inv_row(Tables T, LimbMap m)
+__global__ void __launch_bounds__(S::THREADS_B) k_inv_row(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
-    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
     const u64 q = T.modc[L.tf].q, q2 = 2 * q;
     const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
@@ -89,17 +92,16 @@ __global__ void __launch_bounds__(S::THREADS_B) k_inv_row(Tables T, LimbMap m)
 }
 
 // Inverse column pass (stages LA-1..0), second half of the iNTT, then the
-// optional scale; output canonical.  SC: 0 none, 1 per-limb scale[b],
-// 2 N^-1.
+// scale (SC: 0 none, 1 the job's per-entry scale, 2 N^-1); output canonical.
 template <class S, int SC>
-__global__ void __launch_bounds__(S::THREADS_A) k_inv_col(Tables T, LimbMap m, const ulonglong2 *scale)
+__global__ void __launch_bounds__(S::THREADS_A) k_inv_col(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
     ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(sm + (1 << S::LA) * S::COLS);
-    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
-    const ModC mc = T.modc[L.tf];
+    const ModC &mc = T.modc[L.tf];
     const u64 q = mc.q, q2 = 2 * q;
     const ulonglong2 *twt = T.itw + ((size_t)L.tf << S::LOGN);
     for (int i = threadIdx.x; i < (1 << S::LA); i += S::THREADS_A) tws[i] = twt[i];
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(S::THREADS_A) k_inv_col(Tables T, LimbMap m, c
     inv_round1<S::RA>(x, TwSmem{tws}, q, q2);
     u64 w = 0, wp = 0;
     if (SC == 1) {
-        const ulonglong2 f = scale[L.b];
+        const ulonglong2 f = L.scale[L.b];
         w = f.x;
         wp = f.y;
     } else if (SC == 2) {
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(S::THREADS_A) k_inv_col(Tables T, LimbMap m, c
 template <class S>
 static void set_smem_attrs()
 {
-    static bool done = false;  // per instantiation; attributes are per device function
+    static bool done = false;  // per instantiation
     if (done) return;
     cudaFuncSetAttribute(k_fwd_col<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
     cudaFuncSetAttribute(k_inv_col<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
@@ -160,35 +162,51 @@ static int launch_status(const char *what)
     return KS_OK;
 }
 
-template <class S>
-static void ntt_fwd_S(const Tables &T, const LimbMap &m, int nlimbs, bool canonical, cudaStream_t st)
+static bool any_scale(const LimbMaps &ms)
 {
-    set_smem_attrs<S>();
-    dim3 ga((1 << S::LB) / S::COLS, nlimbs), gb((1 << S::LA) / S::ROWS, nlimbs);
-    KS_LAUNCH(st, "ntt_fwd_col", k_fwd_col<S><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
-    LimbMap m2 = m;
-    m2.src = m.dst;
-    if (canonical)
-        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m2));
-    else
-        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, false><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m2));
+    for (int j = 0; j < ms.n; ++j)
+        if (ms.m[j].scale) return true;
+    return false;
 }
 
 template <class S>
-static void ntt_inv_S(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool ninv,
-                      cudaStream_t st)
+static void fwd_col_S(const Tables &T, const LimbMaps &m, cudaStream_t st)
 {
     set_smem_attrs<S>();
-    dim3 ga((1 << S::LB) / S::COLS, nlimbs), gb((1 << S::LA) / S::ROWS, nlimbs);
-    KS_LAUNCH(st, "ntt_inv_row", k_inv_row<S><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
-    LimbMap m2 = m;
-    m2.src = m.dst;
-    if (scale)
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, scale));
-    else if (ninv)
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, nullptr));
+    KS_LAUNCH(st, "ntt_fwd_col",
+              k_fwd_col<S><<<dim3((1 << S::LB) / S::COLS, m.pre[m.n]), S::THREADS_A, S::SMEM_A, st>>>(T, m));
+}
+
+template <class S>
+static void fwd_row_S(const Tables &T, const LimbMaps &m, bool canonical, cudaStream_t st)
+{
+    set_smem_attrs<S>();
+    dim3 gb((1 << S::LA) / S::ROWS, m.pre[m.n]);
+    if (canonical)
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
     else
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m2, nullptr));
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, false><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
+}
+
+template <class S>
+static void inv_row_S(const Tables &T, const LimbMaps &m, cudaStream_t st)
+{
+    set_smem_attrs<S>();
+    KS_LAUNCH(st, "ntt_inv_row",
+              k_inv_row<S><<<dim3((1 << S::LA) / S::ROWS, m.pre[m.n]), S::THREADS_B, S::SMEM_B, st>>>(T, m));
+}
+
+template <class S>
+static void inv_col_S(const Tables &T, const LimbMaps &m, bool ninv, cudaStream_t st)
+{
+    set_smem_attrs<S>();
+    dim3 ga((1 << S::LB) / S::COLS, m.pre[m.n]);
+    if (any_scale(m))
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+    else if (ninv)
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+    else
+        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
 }
 
 #define KS_DISPATCH_LOGN(logN, FN, ...)                                                                   \
@@ -204,91 +222,93 @@ static void ntt_inv_S(const Tables &T, const LimbMap &m, int nlimbs, const ulong
     default: return fail(KS_EUNSUPPORTED, "logN outside 10..17");                                         \
     }
 
-template <class S>
-static void fwd_col_S(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
+LimbMaps one_map(const LimbMap &m, int nlimbs)
 {
-    set_smem_attrs<S>();
-    KS_LAUNCH(st, "ntt_fwd_col", k_fwd_col<S><<<dim3((1 << S::LB) / S::COLS, nlimbs), S::THREADS_A, S::SMEM_A, st>>>(T, m));
+    LimbMaps ms;
+    ms.n = 0;
+    ms.pre[0] = 0;
+    add_map(ms, m, nlimbs);
+    return ms;
 }
 
-template <class S>
-static void inv_col_S(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool ninv,
-                      cudaStream_t st)
+void add_map(LimbMaps &ms, const LimbMap &m, int nlimbs)
 {
-    set_smem_attrs<S>();
-    dim3 ga((1 << S::LB) / S::COLS, nlimbs);
-    if (scale)
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, scale));
-    else if (ninv)
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, nullptr));
-    else
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m, nullptr));
+    if (ms.n == 0) ms.pre[0] = 0;
+    ms.m[ms.n] = m;
+    ms.pre[ms.n + 1] = ms.pre[ms.n] + nlimbs;
+    ms.n += 1;
 }
 
-int launch_fwd_col(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
+int launch_fwd_col(const Tables &T, const LimbMaps &m, cudaStream_t st)
 {
-    if (nlimbs <= 0) return KS_OK;
-    KS_DISPATCH_LOGN(T.logN, fwd_col_S, T, m, nlimbs, st);
+    if (m.n == 0 || m.pre[m.n] == 0) return KS_OK;
+    KS_DISPATCH_LOGN(T.logN, fwd_col_S, T, m, st);
     return launch_status("forward column pass launch");
 }
 
-int launch_inv_col(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool scale_by_ninv,
-                   cudaStream_t st)
+int launch_inv_col(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaStream_t st)
 {
-    if (nlimbs <= 0) return KS_OK;
-    KS_DISPATCH_LOGN(T.logN, inv_col_S, T, m, nlimbs, scale, scale_by_ninv, st);
+    if (m.n == 0 || m.pre[m.n] == 0) return KS_OK;
+    KS_DISPATCH_LOGN(T.logN, inv_col_S, T, m, scale_by_ninv, st);
     return launch_status("inverse column pass launch");
 }
 
-int launch_ntt_fwd(const Tables &T, const LimbMap &m, int nlimbs, bool canonical, cudaStream_t st)
+int launch_ntt_fwd(const Tables &T, const LimbMaps &m, bool canonical, cudaStream_t st)
 {
-    if (nlimbs <= 0) return KS_OK;
-    KS_DISPATCH_LOGN(T.logN, ntt_fwd_S, T, m, nlimbs, canonical, st);
+    if (m.n == 0 || m.pre[m.n] == 0) return KS_OK;
+    KS_DISPATCH_LOGN(T.logN, fwd_col_S, T, m, st);
+    LimbMaps m2 = m;
+    for (int j = 0; j < m2.n; ++j) m2.m[j].src = m2.m[j].dst;
+    KS_DISPATCH_LOGN(T.logN, fwd_row_S, T, m2, canonical, st);
     return launch_status("forward NTT launch");
 }
 
-int launch_ntt_inv(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool scale_by_ninv,
-                   cudaStream_t st)
+int launch_ntt_inv(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaStream_t st)
 {
-    if (nlimbs <= 0) return KS_OK;
-    KS_DISPATCH_LOGN(T.logN, ntt_inv_S, T, m, nlimbs, scale, scale_by_ninv, st);
+    if (m.n == 0 || m.pre[m.n] == 0) return KS_OK;
+    KS_DISPATCH_LOGN(T.logN, inv_row_S, T, m, st);
+    LimbMaps m2 = m;
+    for (int j = 0; j < m2.n; ++j) m2.m[j].src = m2.m[j].dst;
+    KS_DISPATCH_LOGN(T.logN, inv_col_S, T, m2, scale_by_ninv, st);
     return launch_status("inverse NTT launch");
 }
 
 // ------------------------------------------------------------------ BConv
-constexpr int BC_TT = 8;      // target towers per block
+constexpr int BC_TT = 8;  // target towers per block
 constexpr int BC_THREADS = 256;
 
-struct DigitOffs {
-    int mat[kMaxQ];
-};
+void add_bup(BUpJobs &b, const Tables &T, const BUpJob &j)
+{
+    if (b.n == 0) b.zpre[0] = 0;
+    const int nd = j.jsel >= 0 ? 1 : (j.nact + T.alpha - 1) / T.alpha;
+    b.job[b.n] = j;
+    b.zpre[b.n + 1] = b.zpre[b.n] + nd;
+    b.n += 1;
+}
 
-// ModUp P2: grid (N/256, ceil(targets/TT), digits).  Digit j (or jsel)
-// converts its canonical coefficient-form towers y[lo..hi) to the towers of
-// D_l with compact index in [t_begin, t_end) outside the digit; output lazy
-// in [0, 2r) at D + j*dstride + (t - t_base)*N (j = 0 when jsel is set).
-__global__ void __launch_bounds__(BC_THREADS) k_bconv_up(Tables T, int nact, int jsel, int t_begin, int t_end,
-                                                         int t_base, DigitOffs offs, const u64 *y, u64 *D,
-                                                         size_t dstride)
+// ModUp P2: grid (N/256, ceil(max targets/TT), digit blocks of all jobs).
+__global__ void __launch_bounds__(BC_THREADS) k_bconv_up(Tables T, BUpJobs bj)
 {
     __shared__ u64 cs[kMaxQ][BC_TT];
     __shared__ int s_t[BC_TT];
     __shared__ int s_tf[BC_TT];
-    const int j = jsel >= 0 ? jsel : (int)blockIdx.z;
+    const int jb = find_slot(bj.zpre, bj.n, blockIdx.z);
+    const BUpJob &J = bj.job[jb];
+    const int nact = J.nact;
+    const int j = J.jsel >= 0 ? J.jsel : (int)blockIdx.z - bj.zpre[jb];
     const int lo = j * T.alpha;
     const int hi = min(lo + T.alpha, nact);
     const int a = hi - lo;
-    // overlap of the digit with the target range
-    const int olo = max(lo, t_begin), ohi = min(hi, t_end);
+    const int olo = max(lo, J.t_begin), ohi = min(hi, J.t_end);
     const int ov = ohi > olo ? ohi - olo : 0;
-    const int nb = (t_end - t_begin) - ov;
+    const int nb = (J.t_end - J.t_begin) - ov;
     const int u0 = blockIdx.y * BC_TT;
     if (u0 >= nb) return;
     const int nfull = T.nq + T.kp;
-    const u64 *mat = T.up_mat + offs.mat[j];
+    const u64 *mat = T.up_mat + T.up_mat_lvl[(size_t)(nact - 1) * T.ndig + j];
     if (threadIdx.x < BC_TT) {
         const int u = min(u0 + (int)threadIdx.x, nb - 1);
-        int t = t_begin + u;
+        int t = J.t_begin + u;
         if (ov > 0 && t >= olo) t += ov;
         s_t[threadIdx.x] = t;
         s_tf[threadIdx.x] = full_tower(t, nact, T.nq);
@@ -304,66 +324,114 @@ __global__ void __launch_bounds__(BC_THREADS) k_bconv_up(Tables T, int nact, int
     BAcc acc[BC_TT];
 #pragma unroll
     for (int g = 0; g < BC_TT; ++g) bacc_zero(acc[g]);
-    for (int i = 0; i < a; ++i) {
+    // sources in groups of four: the loads of a group are issued together
+    int i = 0;
+    for (; i + 4 <= a; i += 4) {
+        u64 yv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) yv[u] = J.y[(size_t)(lo + i + u) * N + n];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            u32 y0, y1;
+            split_y(yv[u], y0, y1);
+#pragma unroll
+            for (int g = 0; g < BC_TT; ++g) bacc_mac(acc[g], y0, y1, cs[i + u][g]);
+        }
+    }
+    for (; i < a; ++i) {
         u32 y0, y1;
-        split_y(y[(size_t)(lo + i) * N + n], y0, y1);
+        split_y(J.y[(size_t)(lo + i) * N + n], y0, y1);
 #pragma unroll
         for (int g = 0; g < BC_TT; ++g) bacc_mac(acc[g], y0, y1, cs[i][g]);
     }
-    u64 *Dj = D + (size_t)(jsel >= 0 ? 0 : j) * dstride;
+    u64 *Dj = J.D + (size_t)(J.jsel >= 0 ? 0 : j) * J.dstride;
 #pragma unroll
     for (int g = 0; g < BC_TT; ++g) {
-        if (u0 + g < nb) {
-            const ModC mc = T.modc[s_tf[g]];
-            Dj[(size_t)(s_t[g] - t_base) * N + n] = bacc_reduce(acc[g], mc);
+        if (u0 + g < nb) Dj[(size_t)(s_t[g] - J.t_base) * N + n] = bacc_reduce(acc[g], T.modc[s_tf[g]]);
+    }
+}
+
+int launch_bconv_up(const Tables &T, const BUpJobs &b, cudaStream_t st)
+{
+    if (b.n == 0) return KS_OK;
+    int span = 0;
+    for (int i = 0; i < b.n; ++i) span = std::max(span, b.job[i].t_end - b.job[i].t_begin);
+    if (span <= 0) return KS_OK;
+    const size_t N = (size_t)1 << T.logN;
+    dim3 g((unsigned)(N / BC_THREADS), (unsigned)((span + BC_TT - 1) / BC_TT), (unsigned)b.zpre[b.n]);
+    KS_LAUNCH(st, "bconv_up", k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, b));
+    return launch_status("ModUp BConv launch");
+}
+
+void add_bdn(BDnJobs &b, const BDnJob &j)
+{
+    if (b.n == 0) b.zpre[0] = 0;
+    b.job[b.n] = j;
+    b.zpre[b.n + 1] = b.zpre[b.n] + j.npoly;
+    b.n += 1;
+}
+
+// ModDown P2: grid (N/256, ceil(max nact/TT), polynomials of all jobs).
+__global__ void __launch_bounds__(BC_THREADS) k_bconv_down(Tables T, BDnJobs bj)
+{
+    __shared__ u64 cs[kMaxP][BC_TT];
+    const int jb = find_slot(bj.zpre, bj.n, blockIdx.z);
+    const BDnJob &J = bj.job[jb];
+    const int x = blockIdx.z - bj.zpre[jb];
+    const int nact = J.nact;
+    const int i0 = blockIdx.y * BC_TT;
+    if (i0 >= nact) return;
+    const int K = T.kp;
+    for (int idx = threadIdx.x; idx < K * BC_TT; idx += blockDim.x) {
+        const int k = idx / BC_TT, g = idx % BC_TT;
+        cs[k][g] = (i0 + g < nact) ? T.dn_mat[(size_t)k * T.nq + i0 + g] : 0;
+    }
+    __syncthreads();
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 *w = J.cp + (size_t)x * J.cp_stride + (size_t)nact * N;
+    BAcc acc[BC_TT];
+#pragma unroll
+    for (int g = 0; g < BC_TT; ++g) bacc_zero(acc[g]);
+    int k = 0;
+    for (; k + 4 <= K; k += 4) {
+        u64 wv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) wv[u] = w[(size_t)(k + u) * N + n];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            u32 y0, y1;
+            split_y(wv[u], y0, y1);
+#pragma unroll
+            for (int g = 0; g < BC_TT; ++g) bacc_mac(acc[g], y0, y1, cs[k + u][g]);
         }
     }
-}
-
-static DigitOffs digit_offsets(const Tables &T, int nact)
-{
-    const int *mat_off = T.h_up_mat_off;
-    DigitOffs o;
-    const int nd = (nact + T.alpha - 1) / T.alpha;
-    for (int j = 0; j < nd; ++j) {
-        const int a = std::min(T.alpha, nact - j * T.alpha);
-        o.mat[j] = mat_off[j * (T.alpha + 1) + a];
+    for (; k < K; ++k) {
+        u32 y0, y1;
+        split_y(w[(size_t)k * N + n], y0, y1);
+#pragma unroll
+        for (int g = 0; g < BC_TT; ++g) bacc_mac(acc[g], y0, y1, cs[k][g]);
     }
-    return o;
+    u64 *vo = J.v + (size_t)x * J.v_stride;
+#pragma unroll
+    for (int g = 0; g < BC_TT; ++g)
+        if (i0 + g < nact) vo[(size_t)(i0 + g) * N + n] = bacc_reduce(acc[g], T.modc[i0 + g]);
 }
 
-int launch_bconv_up_range(const Tables &T, int nact, int t_begin, int t_end, int t_base, const u64 *y, u64 *D,
-                          size_t dstride, cudaStream_t st)
+int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st)
 {
-    const int nd = (nact + T.alpha - 1) / T.alpha;
+    if (b.n == 0) return KS_OK;
+    int span = 0;
+    for (int i = 0; i < b.n; ++i) span = std::max(span, b.job[i].nact);
     const size_t N = (size_t)1 << T.logN;
-    if (t_end <= t_begin) return KS_OK;
-    DigitOffs o = digit_offsets(T, nact);
-    dim3 g((unsigned)(N / BC_THREADS), (unsigned)((t_end - t_begin + BC_TT - 1) / BC_TT), (unsigned)nd);
-    KS_LAUNCH(st, "bconv_up", k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, nact, -1, t_begin, t_end, t_base, o, y, D, dstride));
-    return launch_status("ModUp BConv launch");
-}
-
-int launch_bconv_up(const Tables &T, int nact, const u64 *y, u64 *D, cudaStream_t st)
-{
-    const int nt = nact + T.kp;
-    const size_t N = (size_t)1 << T.logN;
-    return launch_bconv_up_range(T, nact, 0, nt, 0, y, D, (size_t)nt * N, st);
-}
-
-int launch_bconv_up_digit(const Tables &T, int nact, int j, const u64 *y, u64 *Dj, cudaStream_t st)
-{
-    const int nt = nact + T.kp;
-    const size_t N = (size_t)1 << T.logN;
-    DigitOffs o = digit_offsets(T, nact);
-    dim3 g((unsigned)(N / BC_THREADS), (unsigned)((nt + BC_TT - 1) / BC_TT), 1);
-    KS_LAUNCH(st, "bconv_up", k_bconv_up<<<g, BC_THREADS, 0, st>>>(T, nact, j, 0, nt, 0, o, y, Dj, 0));
-    return launch_status("ModUp BConv launch");
+    dim3 g((unsigned)(N / BC_THREADS), (unsigned)((span + BC_TT - 1) / BC_TT), (unsigned)b.zpre[b.n]);
+    KS_LAUNCH(st, "bconv_down", k_bconv_down<<<g, BC_THREADS, 0, st>>>(T, b));
+    return launch_status("ModDown BConv launch");
 }
 
 // ------------------------------------------------------------------ apply key
-// ModUp P4+P5: grid (N/256, nact+K).  Stored key = evk * key_sc * 2^64, so
-// REDC of the 128-bit sum gives the folded c' directly.
+// ModUp P4+P5 (single job): grid (N/256, nact+K).  The stored key carries the
+// folded factors and 2^64, so REDC of the 128-bit sum gives the folded c'.
 __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, int j1, const u64 *d, const u64 *D,
                                                    size_t dstride, const u64 *evk, u64 *cp, int accumulate)
 {
@@ -373,7 +441,7 @@ __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, i
     const int tf = full_tower(t, nact, T.nq);
     const size_t N = (size_t)1 << T.logN;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const ModC mc = T.modc[tf];
+    const ModC &mc = T.modc[tf];
     U128 sb = {0, 0}, sa = {0, 0};
     for (int j = j0; j < j1; ++j) {
         const bool own = t < nact && t / T.alpha == j;
@@ -383,8 +451,9 @@ __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, i
         mac128(sb, dv, kb);
         mac128(sa, dv, ka);
     }
-    u64 rb = reduce2(redc(sb, mc.q, mc.mont), mc.q);
-    u64 ra = reduce2(redc(sa, mc.q, mc.mont), mc.q);
+    // D below 40q: the REDC result is below q + 40*nd*q^2/2^64, reduced fully.
+    u64 rb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
+    u64 ra = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
     u64 *cb = cp + (size_t)t * N + n;
     u64 *ca = cp + ((size_t)nt + t) * N + n;
     if (accumulate) {
@@ -405,61 +474,20 @@ int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u6
     return launch_status("apply-key launch");
 }
 
-// ------------------------------------------------------------------ ModDown
-// P2: grid (N/256, ceil(nact/TT), npoly).
-__global__ void __launch_bounds__(BC_THREADS) k_bconv_down(Tables T, int nact, const u64 *cp, size_t cp_stride,
-                                                           u64 *v, size_t v_stride)
-{
-    __shared__ u64 cs[kMaxP][BC_TT];
-    const int i0 = blockIdx.y * BC_TT;
-    const int K = T.kp;
-    for (int idx = threadIdx.x; idx < K * BC_TT; idx += blockDim.x) {
-        const int k = idx / BC_TT, g = idx % BC_TT;
-        cs[k][g] = (i0 + g < nact) ? T.dn_mat[(size_t)k * T.nq + i0 + g] : 0;
-    }
-    __syncthreads();
-    const size_t N = (size_t)1 << T.logN;
-    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const u64 *w = cp + (size_t)blockIdx.z * cp_stride + (size_t)nact * N;
-    BAcc acc[BC_TT];
-#pragma unroll
-    for (int g = 0; g < BC_TT; ++g) bacc_zero(acc[g]);
-    for (int k = 0; k < K; ++k) {
-        u32 y0, y1;
-        split_y(w[(size_t)k * N + n], y0, y1);
-#pragma unroll
-        for (int g = 0; g < BC_TT; ++g) bacc_mac(acc[g], y0, y1, cs[k][g]);
-    }
-    u64 *vo = v + (size_t)blockIdx.z * v_stride;
-#pragma unroll
-    for (int g = 0; g < BC_TT; ++g)
-        if (i0 + g < nact) vo[(size_t)(i0 + g) * N + n] = bacc_reduce(acc[g], T.modc[i0 + g]);
-}
-
-int launch_bconv_down(const Tables &T, int nact, int npoly, const u64 *cp, size_t cp_stride, u64 *v,
-                      size_t v_stride, cudaStream_t st)
-{
-    const size_t N = (size_t)1 << T.logN;
-    dim3 g((unsigned)(N / BC_THREADS), (unsigned)((nact + BC_TT - 1) / BC_TT), (unsigned)npoly);
-    KS_LAUNCH(st, "bconv_down", k_bconv_down<<<g, BC_THREADS, 0, st>>>(T, nact, cp, cp_stride, v, v_stride));
-    return launch_status("ModDown BConv launch");
-}
-
 struct OutPtrs {
     u64 *p[2];
 };
 
-// P4: out = cp - v mod q (cp canonical, v lazy in [0, 4q)).
+// ModDown P4: out = cp - v mod q (cp canonical, v lazy below 40q).
 __global__ void __launch_bounds__(256) k_down_final(Tables T, const u64 *cp, size_t cp_stride, const u64 *v,
                                                     size_t v_stride, OutPtrs outs)
 {
     const int i = blockIdx.y, x = blockIdx.z;
     const size_t N = (size_t)1 << T.logN;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const u64 q = T.modc[i].q, q2 = 2 * q;
-    u64 r = cp[x * cp_stride + (size_t)i * N + n] + 2 * q2 - v[x * v_stride + (size_t)i * N + n];
-    r = r >= 2 * q2 ? r - 2 * q2 : r;
-    outs.p[x][(size_t)i * N + n] = reduce4(r, q, q2);
+    const ModC &mc = T.modc[i];
+    const u64 r = cp[x * cp_stride + (size_t)i * N + n] + 40 * mc.q - v[x * v_stride + (size_t)i * N + n];
+    outs.p[x][(size_t)i * N + n] = reduce_any(r, mc.q, mc.one_sh);
 }
 
 int launch_down_final(const Tables &T, int nact, int npoly, const u64 *cp, size_t cp_stride, const u64 *v,
@@ -475,10 +503,10 @@ int launch_down_final(const Tables &T, int nact, int npoly, const u64 *cp, size_
 }
 
 // ------------------------------------------------------------------ helpers
-// grid (N/256, nlimbs)
-__global__ void k_scale(Tables T, LimbMap m, const ulonglong2 *fac)
+// grid (N/256, limbs)
+__global__ void k_scale(Tables T, LimbMaps ms, const ulonglong2 *fac)
 {
-    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, T.logN);
+    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, T.logN);
     if (L.skip) return;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const u64 q = T.modc[L.tf].q;
@@ -486,29 +514,12 @@ __global__ void k_scale(Tables T, LimbMap m, const ulonglong2 *fac)
     L.dst[n] = reduce2(shoup_lazy(L.src[n], f.x, f.y, q), q);
 }
 
-int launch_scale(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *factors_full, cudaStream_t st)
+int launch_scale(const Tables &T, const LimbMaps &m, const ulonglong2 *factors_full, cudaStream_t st)
 {
-    if (nlimbs <= 0) return KS_OK;
+    if (m.n == 0 || m.pre[m.n] == 0) return KS_OK;
     const size_t N = (size_t)1 << T.logN;
-    KS_LAUNCH(st, "scale", k_scale<<<dim3((unsigned)(N / 256), nlimbs), 256, 0, st>>>(T, m, factors_full));
+    KS_LAUNCH(st, "scale", k_scale<<<dim3((unsigned)(N / 256), m.pre[m.n]), 256, 0, st>>>(T, m, factors_full));
     return launch_status("scale launch");
-}
-
-__global__ void k_canon(Tables T, LimbMap m)
-{
-    const LimbRef L = limb_ref(m, blockIdx.y, T.nq, T.alpha, T.logN);
-    if (L.skip) return;
-    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const u64 q = T.modc[L.tf].q;
-    L.dst[n] = reduce4(L.src[n], q, 2 * q);
-}
-
-int launch_canon(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st)
-{
-    if (nlimbs <= 0) return KS_OK;
-    const size_t N = (size_t)1 << T.logN;
-    KS_LAUNCH(st, "canon", k_canon<<<dim3((unsigned)(N / 256), nlimbs), 256, 0, st>>>(T, m));
-    return launch_status("canonicalise launch");
 }
 
 // grid (N/256, nact, nd): D[j][t] = d[t] for t in digit j.
@@ -553,7 +564,7 @@ int launch_key_convert(const Tables &T, u64 *evk, cudaStream_t st)
     return launch_status("key conversion launch");
 }
 
-// a*b mod q for arbitrary a, b < q (two Montgomery reductions).
+// a*b mod q for a, b < q (two Montgomery reductions).
 __device__ __forceinline__ u64 mulmod_dev(u64 a, u64 b, const ModC &m)
 {
     U128 t = {0, 0};
@@ -572,7 +583,7 @@ __global__ void k_keygen_combine(Tables T, const u64 *s_hat, const u64 *sp_hat, 
     const int nfull = T.nq + T.kp;
     const size_t N = (size_t)1 << T.logN;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const ModC mc = T.modc[tf];
+    const ModC &mc = T.modc[tf];
     const u64 q = mc.q;
     const u64 a = evk[(((size_t)j * 2 + 1) * nfull + tf) * N + n];
     const u64 sh = s_hat[(size_t)tf * N + n];
@@ -590,7 +601,7 @@ int launch_keygen_combine(const Tables &T, const u64 *s_hat, const u64 *sp_hat, 
 {
     const size_t N = (size_t)1 << T.logN;
     KS_LAUNCH(st, "keygen_combine", k_keygen_combine<<<dim3((unsigned)(N / 256), T.nq + T.kp, T.ndig), 256, 0, st>>>(
-                                          T, s_hat, sp_hat, e_hat, pmod, evk));
+                                        T, s_hat, sp_hat, e_hat, pmod, evk));
     return launch_status("keygen combine launch");
 }
 
@@ -612,7 +623,8 @@ __global__ void k_signed_to_towers(Tables T, const int64_t *in, u64 *out)
 int launch_signed_to_towers(const Tables &T, const int64_t *v, int nvec, u64 *out, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
-    KS_LAUNCH(st, "signed_to_towers", k_signed_to_towers<<<dim3((unsigned)(N / 256), T.nq + T.kp, nvec), 256, 0, st>>>(T, v, out));
+    KS_LAUNCH(st, "signed_to_towers",
+              k_signed_to_towers<<<dim3((unsigned)(N / 256), T.nq + T.kp, nvec), 256, 0, st>>>(T, v, out));
     return launch_status("signed residue launch");
 }
 

@@ -1,18 +1,27 @@
 // ks_launch.h -- host-side launchers of the key-switching kernels.
+//
+// Every stage launcher takes a small table of per-job descriptors passed to
+// the kernel by value (kernel parameters, up to kMaxBatch jobs), so one launch
+// covers the limbs of every job of a batch; a single key switch is a batch of
+// one.  Blocks find their job by a search over per-launch prefix counts.
 #pragma once
 #include "ks_internal.h"
 
 namespace ks {
+
+constexpr int kMaxBatch = 64;
 
 // A set of limbs addressed arithmetically.  Limb l of the set is entry
 // b = l % per of limb-row a = l / per; it lives at (a*row_stride + aoff + b)*N
 // words from src/dst and belongs to compact tower t = toff + b of the level
 // basis D_l (Q towers 0..nact-1, then the K special towers).  With
 // skip_base >= 0, limbs whose tower lies inside digit a + skip_base are
-// skipped (the ModUp bypass); -1 skips nothing.
+// skipped (the ModUp bypass); -1 skips nothing.  scale (optional) holds one
+// Shoup pair per entry b for the inverse column pass.
 struct LimbMap {
     const u64 *src;
     u64 *dst;
+    const ulonglong2 *scale;
     int per;
     int row_stride;
     int aoff;
@@ -21,67 +30,120 @@ struct LimbMap {
     int skip_base;
 };
 
+// One LimbMap per job; job j owns launch limbs [pre[j], pre[j+1]).
+struct LimbMaps {
+    int n;
+    int pre[kMaxBatch + 1];
+    LimbMap m[kMaxBatch];
+};
+
 __host__ __device__ inline int full_tower(int t, int nact, int nq) { return t < nact ? t : nq + (t - nact); }
 
-// Single passes (column pass of the forward NTT, column pass of the inverse
-// NTT with the same scale options as launch_ntt_inv).
-int launch_fwd_col(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st);
-int launch_inv_col(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool scale_by_ninv,
-                   cudaStream_t st);
-// ModUp P2 for digits [0, nd) restricted to targets of compact tower index
-// in [t_begin, t_end) (outside the digit); output row t goes to
-// D + j*dstride + (t - t_base)*N.
-int launch_bconv_up_range(const Tables &T, int nact, int t_begin, int t_end, int t_base, const u64 *y, u64 *D,
-                          size_t dstride, cudaStream_t st);
+// Job of launch item x given prefix counts pre[0..n] (binary search).
+__host__ __device__ inline int find_slot(const int *pre, int n, int x)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
 
-// Forward NTT (column pass src->dst, row pass in place on dst).  Input in
-// [0, 4q); output canonical or lazy in [0, 4q).
-int launch_ntt_fwd(const Tables &T, const LimbMap &m, int nlimbs, bool canonical, cudaStream_t st);
+// Host helpers to build launch tables.
+LimbMaps one_map(const LimbMap &m, int nlimbs);
+void add_map(LimbMaps &ms, const LimbMap &m, int nlimbs);
+
+// Forward NTT (column pass src->dst, row pass in place on dst).  Input below
+// 4q.  canonical: output in [0, q); otherwise lazy, below 40q (every
+// consumer of lazy output reduces it).
+int launch_ntt_fwd(const Tables &T, const LimbMaps &m, bool canonical, cudaStream_t st);
 // Inverse NTT without the N^-1 factor (row pass src->dst, column pass in
-// place); the column pass multiplies limb b by scale[b] when scale is set
-// (the Shoup pair of the wanted factor), and the output is canonical.
-int launch_ntt_inv(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *scale, bool scale_by_ninv,
-                   cudaStream_t st);
+// place); the column pass multiplies by the per-entry scale when the job's
+// map has one, or by N^-1 when scale_by_ninv; output canonical.  Input below 2q.
+int launch_ntt_inv(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaStream_t st);
+// Single passes.
+int launch_fwd_col(const Tables &T, const LimbMaps &m, cudaStream_t st);
+int launch_inv_col(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaStream_t st);
 
-// ModUp P2 over all active digits: y [nact][N] canonical coefficient form ->
-// D [nd][nact+K][N] (entries outside each digit), lazy [0, 2r).
-int launch_bconv_up(const Tables &T, int nact, const u64 *y, u64 *D, cudaStream_t st);
-// Same for one digit j only (Digit-Centric).
-int launch_bconv_up_digit(const Tables &T, int nact, int j, const u64 *y, u64 *Dj, cudaStream_t st);
-// ModUp P4+P5: cp[x][t] = sum_j D_{j,t} * evk_{j,x,t}, D_{j,t} = d_t inside digit j.
-// accumulate: add to the existing cp (Digit-Centric partial sums).
+// ModUp P2.  Job: digit j (all active digits, or only jsel >= 0) converts its
+// canonical coefficient-form towers y[lo..hi) to the towers of D_l with
+// compact index in [t_begin, t_end) outside the digit; output lazy in
+// [0, 2r) at D + j'*dstride + (t - t_base)*N, j' = j (or 0 with jsel).
+struct BUpJob {
+    const u64 *y;
+    u64 *D;
+    size_t dstride;
+    int nact, t_begin, t_end, t_base, jsel;
+};
+struct BUpJobs {
+    int n;
+    int zpre[kMaxBatch + 1];  // digit blocks of job j: [zpre[j], zpre[j+1])
+    BUpJob job[kMaxBatch];
+};
+void add_bup(BUpJobs &b, const Tables &T, const BUpJob &j);
+int launch_bconv_up(const Tables &T, const BUpJobs &b, cudaStream_t st);
+
+// ModDown P2: w = cp rows [nact, nact+K) of each polynomial (canonical,
+// coefficient form) -> v[x][i] = sum_k w_k * p_k^-1 mod q_i, lazy [0, 2q).
+struct BDnJob {
+    const u64 *cp;
+    size_t cp_stride;
+    u64 *v;
+    size_t v_stride;
+    int nact, npoly;
+};
+struct BDnJobs {
+    int n;
+    int zpre[kMaxBatch + 1];
+    BDnJob job[kMaxBatch];
+};
+void add_bdn(BDnJobs &b, const BDnJob &j);
+int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st);
+
+// ModUp P4+P5 (single job): cp[x][t] = sum_j D_{j,t} * evk_{j,x,t}, D_{j,t} = d_t
+// inside digit j; D holds lazy NTT output.  accumulate: add to cp.
 int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u64 *d, const u64 *D,
                      size_t D_digit_stride, const u64 *evk, u64 *cp, bool accumulate, cudaStream_t st);
-// ModDown P2: w = cp[x][nact..nact+K) canonical coefficient form ->
-// v[x][i] = sum_k w_k * p_k^-1 mod q_i, lazy [0, 2q).  npoly polynomials,
-// cp rows strided by cp_stride words, v rows by v_stride words.
-int launch_bconv_down(const Tables &T, int nact, int npoly, const u64 *cp, size_t cp_stride, u64 *v,
-                      size_t v_stride, cudaStream_t st);
-// ModDown P4 (P^-1 already folded): out_x[i] = cp[x][i] - v[x][i] mod q_i.
+// ModDown P4 (single job; P^-1 folded): out_x[i] = cp[x][i] - v[x][i] mod q_i,
+// v lazy NTT output.
 int launch_down_final(const Tables &T, int nact, int npoly, const u64 *cp, size_t cp_stride, const u64 *v,
                       size_t v_stride, u64 *const *outs, cudaStream_t st);
-// Multiply limbs by per-tower factors (plain, Shoup) and canonicalise:
-// used by the stage entry points that take unscaled inputs.
-int launch_scale(const Tables &T, const LimbMap &m, int nlimbs, const ulonglong2 *factors_full, cudaStream_t st);
+// Multiply limbs by per-tower factors (plain, Shoup; indexed by full tower).
+int launch_scale(const Tables &T, const LimbMaps &m, const ulonglong2 *factors_full, cudaStream_t st);
 // Copy the input towers of every digit into D (ModUp bypass, stage entry).
 int launch_bypass_copy(const Tables &T, int nact, const u64 *d, u64 *D, cudaStream_t st);
-// Canonicalise limbs in [0, 4q).
-int launch_canon(const Tables &T, const LimbMap &m, int nlimbs, cudaStream_t st);
 
 // Key preparation: canonical evk [ndig][2][nq+kp][N] -> stored form
 // (times key_sc[t], Montgomery factor included), in place.
 int launch_key_convert(const Tables &T, u64 *evk, cudaStream_t st);
-// Key generation combine on the device: inputs are residues already in
-// evaluation form; b_j = -a_j*s + e_j + g_j*s' per tower (g_j = [P]_{q_i} on
-// the digit's towers).  a is read from the a-slots of evk, e_hat [ndig][nt][N].
+// Key generation combine: b_j = -a_j*s + e_j + g_j*s' per tower.
 int launch_keygen_combine(const Tables &T, const u64 *s_hat, const u64 *sp_hat, const u64 *e_hat,
                           const u64 *pmod, u64 *evk, cudaStream_t st);
-// Signed coefficients -> residues per tower: out[t][n] = v[n] mod r_t.
+// Signed coefficients -> residues per tower: out[v][t][n] = in[v][n] mod r_t.
 int launch_signed_to_towers(const Tables &T, const int64_t *v, int nvec, u64 *out, cudaStream_t st);
 
-// Output-Centric fused kernels.
-// prescale: ModUp P1 factors of the level (nact Shoup pairs).
-int launch_oc(const Tables &T, int nact, const u64 *d, const u64 *evk, u64 *out0, u64 *out1, u64 *y, u64 *tmp,
-              u64 *cp, const ulonglong2 *prescale, cudaStream_t st);
+// Output-Centric key switch of a batch of jobs.
+struct OcJob {
+    const u64 *d;
+    u64 *out0, *out1;
+    const u64 *evk;
+    u64 *y;    // [nact][N]
+    u64 *tmp;  // [max(nd*K, (nd+2)*nact)][N]
+    u64 *cp;   // [2][nact+K][N]
+    const ulonglong2 *pre;  // ModUp P1 factors of the level
+    int nact, nd;
+};
+// Scratch words one job needs at level nact.
+size_t oc_scratch_words(const Tables &T, int nact);
+// Output-Centric variants: FUSED runs each section's row pass, key product
+// and ModDown step in one kernel per row block; SPLIT runs the row passes
+// with the plain row-pass kernel and the key product / subtraction in a
+// streaming combine kernel.
+enum { KS_OC_FUSED = 0, KS_OC_SPLIT = 1 };
+int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st);
 
 }  // namespace ks

@@ -51,12 +51,7 @@ static int noalloc_scratch(int device, u64 **out)
 // Scratch words the Output-Centric schedule needs at level nact: y (nact
 // limbs), the section temporaries (max(nd*K, (nd+2)*nact) limbs) and c'
 // (2*(nact+K) limbs).
-static size_t noalloc_words(const ks_params *P, int nact)
-{
-    const size_t nd = (size_t)(nact + P->alpha - 1) / P->alpha;
-    const size_t tmp = std::max(nd * P->kp, (nd + 2) * (size_t)nact);
-    return ((size_t)nact + tmp + 2 * ((size_t)nact + P->kp)) * P->N;
-}
+static size_t noalloc_words(const ks_params *P, int nact) { return oc_scratch_words(P->tables, nact); }
 
 }  // namespace ks
 
@@ -95,9 +90,16 @@ extern "C" int ks_switch_noalloc(const ks_params *P, const ks_key *K, uint32_t l
     // call, so nothing needs clearing between calls.
     const size_t N = P->N;
     const int nd = (nact + P->alpha - 1) / P->alpha;
-    u64 *y = base;
-    u64 *tmp = y + (size_t)nact * N;
-    u64 *cp = tmp + std::max((size_t)nd * P->kp, (size_t)(nd + 2) * nact) * N;
-    const ulonglong2 *pre = P->d_up_pre_lvl + (size_t)(nact - 1) * P->nq;
-    return launch_oc(P->tables, nact, d_in, K->d_evk, d_out0, d_out1, y, tmp, cp, pre, (cudaStream_t)stream);
+    OcJob J;
+    J.d = d_in;
+    J.out0 = d_out0;
+    J.out1 = d_out1;
+    J.evk = K->d_evk;
+    J.y = base;
+    J.tmp = J.y + (size_t)nact * N;
+    J.cp = J.tmp + std::max((size_t)nd * P->kp, (size_t)(nd + 2) * nact) * N;
+    J.pre = P->d_up_pre_lvl + (size_t)(nact - 1) * P->nq;
+    J.nact = nact;
+    J.nd = nd;
+    return launch_oc(P->tables, 1, &J, P->sched.oc_variant, (cudaStream_t)stream);
 }

@@ -10,18 +10,23 @@ namespace ks {
 struct LimbRef {
     const u64 *src;
     u64 *dst;
+    const ulonglong2 *scale;
     int t, tf, b;
     bool skip;
 };
 
-__device__ __forceinline__ LimbRef limb_ref(const LimbMap &m, int l, int nq, int alpha, int logN)
+__device__ __forceinline__ LimbRef limb_ref(const LimbMaps &ms, int lg, int nq, int alpha, int logN)
 {
+    const int jb = find_slot(ms.pre, ms.n, lg);
+    const LimbMap &m = ms.m[jb];
+    const int l = lg - ms.pre[jb];
     const int a = l / m.per, b = l % m.per;
     const int t = m.toff + b;
     const size_t o = ((size_t)a * m.row_stride + m.aoff + b) << logN;
     LimbRef r;
     r.src = m.src ? m.src + o : nullptr;
     r.dst = m.dst ? m.dst + o : nullptr;
+    r.scale = m.scale;
     r.t = t;
     r.b = b;
     r.tf = full_tower(t, m.nact, nq);
@@ -41,8 +46,8 @@ __device__ __forceinline__ int rpad(int c)
 // leaves in the first-round layout (x[k] is element k*TB + tau of the row),
 // srow is the row's padded shared-memory buffer.  Contains block barriers:
 // every thread of the block must call it.
-template <class S>
-__device__ __forceinline__ void row_fwd_core(u64 (&x)[S::REGB], const TwRow &tw, u64 *srow, int tau, u64 q, u64 q2)
+template <class S, class TW>
+__device__ __forceinline__ void row_fwd_core(u64 (&x)[S::REGB], const TW &tw, u64 *srow, int tau, u64 q, u64 q2)
 {
     constexpr int M = S::MB, NG = S::REGB / S::MB;
     fwd_round1<S::RB>(x, tw, q, q2);
@@ -66,8 +71,8 @@ __device__ __forceinline__ void row_fwd_core(u64 (&x)[S::REGB], const TwRow &tw,
 }
 
 // Row pass of the inverse NTT (stages logN-1 .. LA), same layout contract.
-template <class S>
-__device__ __forceinline__ void row_inv_core(u64 (&x)[S::REGB], const TwRow &tw, u64 *srow, int tau, u64 q, u64 q2)
+template <class S, class TW>
+__device__ __forceinline__ void row_inv_core(u64 (&x)[S::REGB], const TW &tw, u64 *srow, int tau, u64 q, u64 q2)
 {
     constexpr int M = S::MB, NG = S::REGB / S::MB;
 #pragma unroll

@@ -1,178 +1,233 @@
-// ks_oc.cu -- Output-Centric dataflow (CiFlow Sec. IV-C).
+// ks_oc.cu -- Output-Centric dataflow (CiFlow Sec. IV-C), batched.
 //
 // OC computes the key-switch output tower by tower instead of stage by stage.
-// The GPU schedule (P towers first, reading (v): ModDown of every Q output
-// tower needs all K special towers of c'):
+// GPU schedule (special towers first -- ModDown of every Q output tower needs
+// all K special towers of c'), every launch covering all jobs of the batch:
 //   1. prep       iNTT of every input tower with the (Q_j/q_i)^-1 prescale
 //                 (ModUp P1) -> y, coefficient form;
-//   2. P section  for each special tower p_k only: BConv of every digit to
-//                 p_k (P2), column pass of the NTT (P3), then one fused
-//                 kernel per row block: row pass of each digit's limb, the
-//                 key product accumulated over digits on chip (P4+P5), and
-//                 the row pass of ModDown's iNTT (ModDown P1) -- c' of the
-//                 special towers never leaves the kernel in evaluation form;
-//                 the inverse column pass then yields w;
-//   3. Q section  for each output tower t: BConv of the other digits to t
-//                 and of w to t (ModUp P2, ModDown P2), column passes, then
-//                 one fused kernel per row block: row pass, key product with
-//                 the bypassed digit taken straight from the input (P3-P5),
-//                 row pass of the ModDown limbs (ModDown P3) and the final
-//                 subtraction (ModDown P4) written to the output.
-// The key is read once, in the fused kernels, straight from device memory.
+//   2. P section  BConv of every digit to the special towers only (P2), the
+//                 column pass of their NTT (P3), then one fused kernel per row
+//                 block: row pass of each digit's limb, the key product summed
+//                 over digits on chip (P4+P5), and the row pass of ModDown's
+//                 iNTT (ModDown P1); the inverse column pass then yields w;
+//   3. Q section  BConv of the other digits to each output tower and of w to
+//                 it (ModUp P2, ModDown P2), column passes, then one fused
+//                 kernel per row block: row pass, key product with the
+//                 bypassed digit read straight from the input (P3-P5), row
+//                 pass of the ModDown limbs (ModDown P3) and the subtraction
+//                 (ModDown P4) written to the output.
+// The key is read once, inside the fused row kernels, while they compute.
+#include <algorithm>
+
 #include "ks_ntt_core.cuh"
 
 namespace ks {
 
-// Accumulate x * e (e the stored key word) into a canonical accumulator.
-__device__ __forceinline__ u64 mac_redc(u64 acc, u64 x, u64 e, u64 q, u64 mont)
+struct OcJobs {
+    int n;
+    int pre[kMaxBatch + 1];  // Q-section row blocks of job j: [pre[j], pre[j+1]) (units of towers)
+    OcJob job[kMaxBatch];
+};
+
+// x * e with the stored key word e: REDC of the 128-bit product; x < 40q,
+// so the result is below q + 40q^2/2^64 < 2q before the correction.
+__device__ __forceinline__ u64 key_mul(u64 x, u64 e, u64 q, u64 mont)
 {
     U128 t = {0, 0};
     mac128(t, x, e);
-    return reduce2(acc + reduce2(redc(t, q, mont), q), q);
+    return reduce2(redc(t, q, mont), q);
 }
 
-// P section, fused row kernel.  grid (2^LA/ROWS, K).
+// Shared memory of the fused row kernels: the row-exchange buffer, then the
+// two accumulators (b and a parts of c') of every element of the block's rows.
 template <class S>
-__global__ void __launch_bounds__(S::THREADS_B) k_oc_rowP(Tables T, int nact, int nd, const u64 *tmp1, const u64 *evk,
-                                                          u64 *cp)
+struct RowSmem {
+    static constexpr int ACC = S::ROWS * (1 << S::LB);  // words per accumulator
+    static constexpr int BYTES = S::SMEM_B + 2 * ACC * 8;
+};
+
+// The per-limb bodies of the fused row kernels are not inlined: each row
+// transform then gets its own register allocation, instead of the compiler
+// keeping values of one transform live across the next (which tripled the
+// register count of the kernels and halved their occupancy).
+
+// One digit's share of the key product for the block's rows: the row pass of
+// the limb at gin (skipped for the bypassed digit, whose input is already in
+// evaluation form), then x * evk_b and x * evk_a added into the accumulators.
+template <class S>
+__device__ __noinline__ void oc_digit(const u64 *gin, int transform, const ulonglong2 *twt, int G, u64 *srow, int tau,
+                                      const u64 *eb, const u64 *ea, u64 *ab, u64 *aa, int first, u64 q, u64 mont)
+{
+    u64 x[S::REGB];
+#pragma unroll
+    for (int i = 0; i < S::REGB; ++i) x[i] = gin[i * S::TB + tau];
+    if (transform) row_fwd_core<S>(x, TwRow{twt, G}, srow, tau, q, 2 * q);
+#pragma unroll
+    for (int i = 0; i < S::REGB; ++i) {
+        const int c = i * S::TB + tau;
+        const u64 pb = key_mul(x[i], __ldg(eb + c), q, mont);
+        const u64 pa = key_mul(x[i], __ldg(ea + c), q, mont);
+        ab[c] = first ? pb : reduce2(ab[c] + pb, q);
+        aa[c] = first ? pa : reduce2(aa[c] + pa, q);
+    }
+}
+
+// Row pass of the inverse NTT of an accumulator row, stored to out.
+template <class S>
+__device__ __noinline__ void oc_inv_store(const u64 *acc, const ulonglong2 *itwt, int G, u64 *srow, int tau, u64 *out,
+                                          u64 q)
+{
+    u64 x[S::REGB];
+#pragma unroll
+    for (int i = 0; i < S::REGB; ++i) x[i] = acc[i * S::TB + tau];
+    row_inv_core<S>(x, TwRow{itwt, G}, srow, tau, q, 2 * q);
+#pragma unroll
+    for (int i = 0; i < S::REGB; ++i) out[i * S::TB + tau] = x[i];
+}
+
+// Row pass of a ModDown limb, then out = acc - NTT(v) mod q.
+template <class S>
+__device__ __noinline__ void oc_down_store(const u64 *gin, const ulonglong2 *twt, int G, u64 *srow, int tau,
+                                           const u64 *acc, u64 *out, u64 q, u64 one_sh)
+{
+    u64 v[S::REGB];
+#pragma unroll
+    for (int i = 0; i < S::REGB; ++i) v[i] = gin[i * S::TB + tau];
+    row_fwd_core<S>(v, TwRow{twt, G}, srow, tau, q, 2 * q);
+    const u64 q40 = 40 * q;
+#pragma unroll
+    for (int i = 0; i < S::REGB; ++i) {
+        const int c = i * S::TB + tau;
+        out[c] = reduce_any(acc[c] + q40 - v[i], q, one_sh);
+    }
+}
+
+// P section, fused row kernel.  grid (2^LA/ROWS, jobs*K).
+template <class S>
+__global__ void __launch_bounds__(S::THREADS_B) k_oc_rowP(Tables T, OcJobs oj)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
     const int K = T.kp;
-    const int k = blockIdx.y;
+    const OcJob &J = oj.job[blockIdx.y / K];
+    const int k = blockIdx.y % K;
+    const int nact = J.nact;
     const int t = nact + k;
     const int tf = T.nq + k;
     const int nt = nact + K;
     const int nfull = T.nq + K;
-    const ModC mc = T.modc[tf];
-    const u64 q = mc.q, q2 = 2 * q;
+    const ModC &mc = T.modc[tf];
     const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
     const int h = blockIdx.x * S::ROWS + rr;
     u64 *srow = sm + rr * S::ROWPAD;
-    const TwRow tw{T.tw + ((size_t)tf << S::LOGN), (1 << S::LA) + h};
+    u64 *ab = sm + S::SMEM_B / 8 + rr * (1 << S::LB);
+    u64 *aa = ab + RowSmem<S>::ACC;
+    const int G = (1 << S::LA) + h;
     const size_t rowoff = (size_t)h << S::LB;
-    u64 accb[S::REGB], acca[S::REGB];
-#pragma unroll
-    for (int i = 0; i < S::REGB; ++i) accb[i] = acca[i] = 0;
-    for (int j = 0; j < nd; ++j) {
-        const u64 *gin = tmp1 + ((size_t)(j * K + k) << S::LOGN) + rowoff;
-        u64 x[S::REGB];
-#pragma unroll
-        for (int i = 0; i < S::REGB; ++i) x[i] = gin[i * S::TB + tau];
-        row_fwd_core<S>(x, tw, srow, tau, q, q2);
-        const u64 *eb = evk + ((size_t)((j * 2 + 0) * nfull + tf) << S::LOGN) + rowoff;
-        const u64 *ea = evk + ((size_t)((j * 2 + 1) * nfull + tf) << S::LOGN) + rowoff;
-#pragma unroll
-        for (int i = 0; i < S::REGB; ++i) {
-            const int c = i * S::TB + tau;
-            accb[i] = mac_redc(accb[i], x[i], __ldg(eb + c), q, mc.mont);
-            acca[i] = mac_redc(acca[i], x[i], __ldg(ea + c), q, mc.mont);
-        }
+    const ulonglong2 *twt = T.tw + ((size_t)tf << S::LOGN);
+    // the block's rows of one limb are one contiguous block of global memory
+    const size_t brow = (size_t)blockIdx.x * S::ROWS << S::LB;
+    constexpr uint32_t BLK = S::ROWS * (1 << S::LB) * 8;
+    auto prefetch_digit = [&](int j) {
+        prefetch_l2(J.tmp + ((size_t)(j * K + k) << S::LOGN) + brow, BLK);
+        prefetch_l2(J.evk + ((size_t)((j * 2 + 0) * nfull + tf) << S::LOGN) + brow, BLK);
+        prefetch_l2(J.evk + ((size_t)((j * 2 + 1) * nfull + tf) << S::LOGN) + brow, BLK);
+    };
+    if (threadIdx.x == 0) prefetch_digit(0);
+    for (int j = 0; j < J.nd; ++j) {
+        if (threadIdx.x == 0 && j + 1 < J.nd) prefetch_digit(j + 1);
+        oc_digit<S>(J.tmp + ((size_t)(j * K + k) << S::LOGN) + rowoff, 1, twt, G, srow, tau,
+                    J.evk + ((size_t)((j * 2 + 0) * nfull + tf) << S::LOGN) + rowoff,
+                    J.evk + ((size_t)((j * 2 + 1) * nfull + tf) << S::LOGN) + rowoff, ab, aa, j == 0, mc.q, mc.mont);
     }
-    const TwRow itw{T.itw + ((size_t)tf << S::LOGN), (1 << S::LA) + h};
-    row_inv_core<S>(accb, itw, srow, tau, q, q2);
-    u64 *ob = cp + ((size_t)t << S::LOGN) + rowoff;
-#pragma unroll
-    for (int i = 0; i < S::REGB; ++i) ob[i * S::TB + tau] = accb[i];
-    row_inv_core<S>(acca, itw, srow, tau, q, q2);
-    u64 *oa = cp + ((size_t)(nt + t) << S::LOGN) + rowoff;
-#pragma unroll
-    for (int i = 0; i < S::REGB; ++i) oa[i * S::TB + tau] = acca[i];
+    const ulonglong2 *itwt = T.itw + ((size_t)tf << S::LOGN);
+    oc_inv_store<S>(ab, itwt, G, srow, tau, J.cp + ((size_t)t << S::LOGN) + rowoff, mc.q);
+    oc_inv_store<S>(aa, itwt, G, srow, tau, J.cp + ((size_t)(nt + t) << S::LOGN) + rowoff, mc.q);
 }
 
-// Q section, fused row kernel.  grid (2^LA/ROWS, nact).  tmp2 holds
-// [nd + 2][nact] limbs: rows j < nd the ModUp limbs of digit j (slot of the
-// own digit unused), rows nd, nd+1 the ModDown limbs of the two polynomials.
+// Q section, fused row kernel.  grid (2^LA/ROWS, sum of nact over jobs).
+// tmp holds [nd + 2][nact] limbs: rows j < nd the ModUp limbs of digit j
+// (the slot of the tower's own digit unused), rows nd and nd+1 the ModDown
+// limbs of the two polynomials.
 template <class S>
-__global__ void __launch_bounds__(S::THREADS_B) k_oc_rowQ(Tables T, int nact, int nd, const u64 *tmp2, const u64 *d,
-                                                          const u64 *evk, u64 *out0, u64 *out1)
+__global__ void __launch_bounds__(S::THREADS_B) k_oc_rowQ(Tables T, OcJobs oj)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
-    const int t = blockIdx.y;
+    const int jb = find_slot(oj.pre, oj.n, blockIdx.y);
+    const OcJob &J = oj.job[jb];
+    const int t = blockIdx.y - oj.pre[jb];
+    const int nact = J.nact;
     const int j0 = t / T.alpha;
     const int nfull = T.nq + T.kp;
-    const ModC mc = T.modc[t];
-    const u64 q = mc.q, q2 = 2 * q;
+    const ModC &mc = T.modc[t];
     const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
     const int h = blockIdx.x * S::ROWS + rr;
     u64 *srow = sm + rr * S::ROWPAD;
-    const TwRow tw{T.tw + ((size_t)t << S::LOGN), (1 << S::LA) + h};
+    u64 *ab = sm + S::SMEM_B / 8 + rr * (1 << S::LB);
+    u64 *aa = ab + RowSmem<S>::ACC;
+    const int G = (1 << S::LA) + h;
     const size_t rowoff = (size_t)h << S::LB;
-    u64 accb[S::REGB], acca[S::REGB];
-#pragma unroll
-    for (int i = 0; i < S::REGB; ++i) accb[i] = acca[i] = 0;
-    for (int j = 0; j < nd; ++j) {
-        u64 x[S::REGB];
-        if (j == j0) {
-            const u64 *gin = d + ((size_t)t << S::LOGN) + rowoff;
-#pragma unroll
-            for (int i = 0; i < S::REGB; ++i) x[i] = gin[i * S::TB + tau];
-        } else {
-            const u64 *gin = tmp2 + ((size_t)(j * nact + t) << S::LOGN) + rowoff;
-#pragma unroll
-            for (int i = 0; i < S::REGB; ++i) x[i] = gin[i * S::TB + tau];
-            row_fwd_core<S>(x, tw, srow, tau, q, q2);
+    const ulonglong2 *twt = T.tw + ((size_t)t << S::LOGN);
+    const size_t brow = (size_t)blockIdx.x * S::ROWS << S::LB;
+    constexpr uint32_t BLK = S::ROWS * (1 << S::LB) * 8;
+    auto prefetch_digit = [&](int j) {
+        const u64 *src = j == j0 ? J.d + ((size_t)t << S::LOGN) : J.tmp + ((size_t)(j * nact + t) << S::LOGN);
+        prefetch_l2(src + brow, BLK);
+        prefetch_l2(J.evk + ((size_t)((j * 2 + 0) * nfull + t) << S::LOGN) + brow, BLK);
+        prefetch_l2(J.evk + ((size_t)((j * 2 + 1) * nfull + t) << S::LOGN) + brow, BLK);
+    };
+    if (threadIdx.x == 0) prefetch_digit(0);
+    for (int j = 0; j < J.nd; ++j) {
+        if (threadIdx.x == 0) {
+            if (j + 1 < J.nd) {
+                prefetch_digit(j + 1);
+            } else {
+                prefetch_l2(J.tmp + ((size_t)(J.nd * nact + t) << S::LOGN) + brow, BLK);
+                prefetch_l2(J.tmp + ((size_t)((J.nd + 1) * nact + t) << S::LOGN) + brow, BLK);
+            }
         }
-        const u64 *eb = evk + ((size_t)((j * 2 + 0) * nfull + t) << S::LOGN) + rowoff;
-        const u64 *ea = evk + ((size_t)((j * 2 + 1) * nfull + t) << S::LOGN) + rowoff;
-#pragma unroll
-        for (int i = 0; i < S::REGB; ++i) {
-            const int c = i * S::TB + tau;
-            accb[i] = mac_redc(accb[i], x[i], __ldg(eb + c), q, mc.mont);
-            acca[i] = mac_redc(acca[i], x[i], __ldg(ea + c), q, mc.mont);
-        }
+        const u64 *gin = j == j0 ? J.d + ((size_t)t << S::LOGN) + rowoff
+                                 : J.tmp + ((size_t)(j * nact + t) << S::LOGN) + rowoff;
+        oc_digit<S>(gin, j != j0, twt, G, srow, tau, J.evk + ((size_t)((j * 2 + 0) * nfull + t) << S::LOGN) + rowoff,
+                    J.evk + ((size_t)((j * 2 + 1) * nfull + t) << S::LOGN) + rowoff, ab, aa, j == 0, mc.q, mc.mont);
     }
-    const u64 q4 = 2 * q2;
-#pragma unroll
-    for (int xp = 0; xp < 2; ++xp) {
-        u64 v[S::REGB];
-        const u64 *gin = tmp2 + ((size_t)((nd + xp) * nact + t) << S::LOGN) + rowoff;
-#pragma unroll
-        for (int i = 0; i < S::REGB; ++i) v[i] = gin[i * S::TB + tau];
-        row_fwd_core<S>(v, tw, srow, tau, q, q2);
-        u64 *o = (xp == 0 ? out0 : out1) + ((size_t)t << S::LOGN) + rowoff;
-#pragma unroll
-        for (int i = 0; i < S::REGB; ++i) {
-            u64 r = (xp == 0 ? accb[i] : acca[i]) + q4 - v[i];
-            r = r >= q4 ? r - q4 : r;
-            o[i * S::TB + tau] = reduce4(r, q, q2);
-        }
-    }
+    for (int xp = 0; xp < 2; ++xp)
+        oc_down_store<S>(J.tmp + ((size_t)((J.nd + xp) * nact + t) << S::LOGN) + rowoff, twt, G, srow, tau,
+                         xp == 0 ? ab : aa, (xp == 0 ? J.out0 : J.out1) + ((size_t)t << S::LOGN) + rowoff, mc.q,
+                         mc.one_sh);
 }
 
 template <class S>
-static void oc_rows_S(const Tables &T, int nact, int nd, const u64 *tmp1, const u64 *tmp2, const u64 *d,
-                      const u64 *evk, u64 *cp, u64 *out0, u64 *out1, bool p_section, cudaStream_t st)
+static void oc_rows_S(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
 {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_oc_rowP<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
-        cudaFuncSetAttribute(k_oc_rowQ<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+        cudaFuncSetAttribute(k_oc_rowP<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowSmem<S>::BYTES);
+        cudaFuncSetAttribute(k_oc_rowQ<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowSmem<S>::BYTES);
         attr = true;
     }
     if (p_section)
         KS_LAUNCH(st, "oc_row_p",
-                  k_oc_rowP<S><<<dim3((1 << S::LA) / S::ROWS, T.kp), S::THREADS_B, S::SMEM_B, st>>>(T, nact, nd, tmp1,
-                                                                                                  evk, cp));
+                  k_oc_rowP<S><<<dim3((1 << S::LA) / S::ROWS, oj.n * T.kp), S::THREADS_B, RowSmem<S>::BYTES, st>>>(
+                      T, oj));
     else
         KS_LAUNCH(st, "oc_row_q",
-                  k_oc_rowQ<S><<<dim3((1 << S::LA) / S::ROWS, nact), S::THREADS_B, S::SMEM_B, st>>>(
-                      T, nact, nd, tmp2, d, evk, out0, out1));
+                  k_oc_rowQ<S><<<dim3((1 << S::LA) / S::ROWS, oj.pre[oj.n]), S::THREADS_B, RowSmem<S>::BYTES, st>>>(
+                      T, oj));
 }
 
-static int oc_rows(const Tables &T, int nact, int nd, const u64 *tmp1, const u64 *tmp2, const u64 *d,
-                   const u64 *evk, u64 *cp, u64 *out0, u64 *out1, bool p_section, cudaStream_t st)
+static int oc_rows(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
 {
     switch (T.logN) {
-    case 10: oc_rows_S<ShapeOf<10>::T>(T, nact, nd, tmp1, tmp2, d, evk, cp, out0, out1, p_section, st); break;
-    case 11: oc_rows_S<ShapeOf<11>::T>(T, nact, nd, tmp1, tmp2, d, evk, cp, out0, out1, p_section, st); break;
-    case 12: oc_rows_S<ShapeOf<12>::T>(T, nact, nd, tmp1, tmp2, d, evk, cp, out0, out1, p_section, st); break;
-    case 13: oc_rows_S<ShapeOf<13>::T>(T, nact, nd, tmp1, tmp2, d, evk, cp, out0, out1, p_section, st); break;
-    case 14: oc_rows_S<ShapeOf<14>::T>(T, nact, nd, tmp1, tmp2, d, evk, cp, out0, out1, p_section, st); break;
-    case 15: oc_rows_S<ShapeOf<15>::T>(T, nact, nd, tmp1, tmp2, d, evk, cp, out0, out1, p_section, st); break;
-    case 16: oc_rows_S<ShapeOf<16>::T>(T, nact, nd, tmp1, tmp2, d, evk, cp, out0, out1, p_section, st); break;
-    case 17: oc_rows_S<ShapeOf<17>::T>(T, nact, nd, tmp1, tmp2, d, evk, cp, out0, out1, p_section, st); break;
+    case 10: oc_rows_S<ShapeOf<10>::T>(T, oj, p_section, st); break;
+    case 11: oc_rows_S<ShapeOf<11>::T>(T, oj, p_section, st); break;
+    case 12: oc_rows_S<ShapeOf<12>::T>(T, oj, p_section, st); break;
+    case 13: oc_rows_S<ShapeOf<13>::T>(T, oj, p_section, st); break;
+    case 14: oc_rows_S<ShapeOf<14>::T>(T, oj, p_section, st); break;
+    case 15: oc_rows_S<ShapeOf<15>::T>(T, oj, p_section, st); break;
+    case 16: oc_rows_S<ShapeOf<16>::T>(T, oj, p_section, st); break;
+    case 17: oc_rows_S<ShapeOf<17>::T>(T, oj, p_section, st); break;
     default: return fail(KS_EUNSUPPORTED, "logN outside 10..17");
     }
     cudaError_t e = cudaGetLastError();
@@ -180,35 +235,157 @@ static int oc_rows(const Tables &T, int nact, int nd, const u64 *tmp1, const u64
     return KS_OK;
 }
 
-int launch_oc(const Tables &T, int nact, const u64 *d, const u64 *evk, u64 *out0, u64 *out1, u64 *y, u64 *tmp,
-              u64 *cp, const ulonglong2 *prescale, cudaStream_t st)
+// ------------------------------------------------------------------ split variant
+// The same schedule with the row passes run by the plain row-pass kernel and
+// the key product / ModDown subtraction by streaming combine kernels: more
+// resident warps per SM than the fused row kernels, at the price of one more
+// round trip of the section's limbs through L2/HBM.
+
+// P section combine: c'_{x,p_k} = sum_j NTT(z_{j,p_k}) * evk_{j,x,p_k} for
+// every coefficient, written canonical to cp.  grid (N/256, jobs*K).
+__global__ void __launch_bounds__(256) k_oc_comb_p(Tables T, OcJobs oj)
+{
+    const int K = T.kp;
+    const OcJob &J = oj.job[blockIdx.y / K];
+    const int k = blockIdx.y % K;
+    const int tf = T.nq + k;
+    const int t = J.nact + k;
+    const int nt = J.nact + K;
+    const int nfull = T.nq + K;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const ModC &mc = T.modc[tf];
+    U128 sb = {0, 0}, sa = {0, 0};
+    for (int j = 0; j < J.nd; ++j) {
+        const u64 x = J.tmp[(size_t)(j * K + k) * N + n];
+        mac128(sb, x, J.evk[((size_t)(j * 2 + 0) * nfull + tf) * N + n]);
+        mac128(sa, x, J.evk[((size_t)(j * 2 + 1) * nfull + tf) * N + n]);
+    }
+    J.cp[(size_t)t * N + n] = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
+    J.cp[(size_t)(nt + t) * N + n] = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+}
+
+// Q section combine: out_x = sum_j D_j * evk_{j,x} - NTT(v_x), D_j the
+// transformed ModUp limb or the input tower for the own digit.
+// grid (N/256, sum of nact over jobs).
+__global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
+{
+    const int jb = find_slot(oj.pre, oj.n, blockIdx.y);
+    const OcJob &J = oj.job[jb];
+    const int t = blockIdx.y - oj.pre[jb];
+    const int nact = J.nact;
+    const int j0 = t / T.alpha;
+    const int nfull = T.nq + T.kp;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const ModC &mc = T.modc[t];
+    U128 sb = {0, 0}, sa = {0, 0};
+    for (int j = 0; j < J.nd; ++j) {
+        const u64 x = j == j0 ? J.d[(size_t)t * N + n] : J.tmp[(size_t)(j * nact + t) * N + n];
+        mac128(sb, x, J.evk[((size_t)(j * 2 + 0) * nfull + t) * N + n]);
+        mac128(sa, x, J.evk[((size_t)(j * 2 + 1) * nfull + t) * N + n]);
+    }
+    const u64 q40 = 40 * mc.q;
+    const u64 cb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
+    const u64 ca = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+    const u64 vb = J.tmp[(size_t)(J.nd * nact + t) * N + n];
+    const u64 va = J.tmp[(size_t)((J.nd + 1) * nact + t) * N + n];
+    J.out0[(size_t)t * N + n] = reduce_any(cb + q40 - vb, mc.q, mc.one_sh);
+    J.out1[(size_t)t * N + n] = reduce_any(ca + q40 - va, mc.q, mc.one_sh);
+}
+
+static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    if (p_section)
+        KS_LAUNCH(st, "oc_comb_p", k_oc_comb_p<<<dim3((unsigned)(N / 256), oj.n * T.kp), 256, 0, st>>>(T, oj));
+    else
+        KS_LAUNCH(st, "oc_comb_q", k_oc_comb_q<<<dim3((unsigned)(N / 256), oj.pre[oj.n]), 256, 0, st>>>(T, oj));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(KS_ECUDA, std::string("OC combine launch: ") + cudaGetErrorString(e));
+    return KS_OK;
+}
+
+size_t oc_scratch_words(const Tables &T, int nact)
+{
+    const size_t N = (size_t)1 << T.logN;
+    const size_t nd = (size_t)(nact + T.alpha - 1) / T.alpha;
+    const size_t tmp = std::max(nd * T.kp, (nd + 2) * (size_t)nact);
+    return ((size_t)nact + tmp + 2 * ((size_t)nact + T.kp)) * N;
+}
+
+static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int variant, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
     const int K = T.kp;
-    const int nt = nact + K;
-    const int nd = (nact + T.alpha - 1) / T.alpha;
     int rc;
     // 1. prep (ModUp P1)
-    LimbMap m1{d, y, nact, 0, 0, 0, nact, -1};
-    if ((rc = launch_ntt_inv(T, m1, nact, prescale, false, st)) != KS_OK) return rc;
-    // 2. P section: BConv to the special towers, column pass, fused rows, inverse column pass
-    u64 *tmp1 = tmp;
-    if ((rc = launch_bconv_up_range(T, nact, nact, nt, nact, y, tmp1, (size_t)K * N, st)) != KS_OK) return rc;
-    LimbMap mp{tmp1, tmp1, K, K, 0, nact, nact, -1};
-    if ((rc = launch_fwd_col(T, mp, nd * K, st)) != KS_OK) return rc;
-    if ((rc = oc_rows(T, nact, nd, tmp1, nullptr, nullptr, evk, cp, nullptr, nullptr, true, st)) != KS_OK) return rc;
-    LimbMap mw{cp, cp, K, nt, nact, nact, nact, -1};
-    if ((rc = launch_inv_col(T, mw, 2 * K, nullptr, false, st)) != KS_OK) return rc;
-    // 3. Q section: BConv of the other digits and of w to each output tower,
-    //    column passes, fused rows with ModDown
-    u64 *tmp2 = tmp;
-    if ((rc = launch_bconv_up_range(T, nact, 0, nact, 0, y, tmp2, (size_t)nact * N, st)) != KS_OK) return rc;
-    if ((rc = launch_bconv_down(T, nact, 2, cp, (size_t)nt * N, tmp2 + (size_t)nd * nact * N, (size_t)nact * N, st)) !=
-        KS_OK)
-        return rc;
-    LimbMap mq{tmp2, tmp2, nact, nact, 0, 0, nact, 0};
-    if ((rc = launch_fwd_col(T, mq, (nd + 2) * nact, st)) != KS_OK) return rc;
-    return oc_rows(T, nact, nd, nullptr, tmp2, d, evk, nullptr, out0, out1, false, st);
+    LimbMaps m1;
+    m1.n = 0;
+    for (int i = 0; i < n; ++i) {
+        const OcJob &J = jobs[i];
+        add_map(m1, LimbMap{J.d, J.y, J.pre, J.nact, 0, 0, 0, J.nact, -1}, J.nact);
+    }
+    if ((rc = launch_ntt_inv(T, m1, false, st)) != KS_OK) return rc;
+    // 2. P section
+    BUpJobs bp;
+    bp.n = 0;
+    LimbMaps mp, mw;
+    mp.n = 0;
+    mw.n = 0;
+    OcJobs oj;
+    oj.n = n;
+    oj.pre[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const OcJob &J = jobs[i];
+        const int nt = J.nact + K;
+        add_bup(bp, T, BUpJob{J.y, J.tmp, (size_t)K * N, J.nact, J.nact, nt, J.nact, -1});
+        add_map(mp, LimbMap{J.tmp, J.tmp, nullptr, K, K, 0, J.nact, J.nact, -1}, J.nd * K);
+        add_map(mw, LimbMap{J.cp, J.cp, nullptr, K, nt, J.nact, J.nact, J.nact, -1}, 2 * K);
+        oj.job[i] = J;
+        oj.pre[i + 1] = oj.pre[i] + J.nact;
+    }
+    if ((rc = launch_bconv_up(T, bp, st)) != KS_OK) return rc;
+    if (variant == KS_OC_FUSED) {
+        if ((rc = launch_fwd_col(T, mp, st)) != KS_OK) return rc;
+        if ((rc = oc_rows(T, oj, true, st)) != KS_OK) return rc;
+        if ((rc = launch_inv_col(T, mw, false, st)) != KS_OK) return rc;
+    } else {
+        if ((rc = launch_ntt_fwd(T, mp, false, st)) != KS_OK) return rc;
+        if ((rc = oc_combine(T, oj, true, st)) != KS_OK) return rc;
+        if ((rc = launch_ntt_inv(T, mw, false, st)) != KS_OK) return rc;
+    }
+    // 3. Q section
+    BUpJobs bq;
+    bq.n = 0;
+    BDnJobs bd;
+    bd.n = 0;
+    LimbMaps mq;
+    mq.n = 0;
+    for (int i = 0; i < n; ++i) {
+        const OcJob &J = jobs[i];
+        const int nt = J.nact + K;
+        add_bup(bq, T, BUpJob{J.y, J.tmp, (size_t)J.nact * N, J.nact, 0, J.nact, 0, -1});
+        add_bdn(bd, BDnJob{J.cp, (size_t)nt * N, J.tmp + (size_t)J.nd * J.nact * N, (size_t)J.nact * N, J.nact, 2});
+        add_map(mq, LimbMap{J.tmp, J.tmp, nullptr, J.nact, J.nact, 0, 0, J.nact, 0}, (J.nd + 2) * J.nact);
+    }
+    if ((rc = launch_bconv_up(T, bq, st)) != KS_OK) return rc;
+    if ((rc = launch_bconv_down(T, bd, st)) != KS_OK) return rc;
+    if (variant == KS_OC_FUSED) {
+        if ((rc = launch_fwd_col(T, mq, st)) != KS_OK) return rc;
+        return oc_rows(T, oj, false, st);
+    }
+    if ((rc = launch_ntt_fwd(T, mq, false, st)) != KS_OK) return rc;
+    return oc_combine(T, oj, false, st);
+}
+
+int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st)
+{
+    for (int i0 = 0; i0 < njobs; i0 += kMaxBatch) {
+        int rc = launch_oc_chunk(T, std::min(kMaxBatch, njobs - i0), jobs + i0, variant, st);
+        if (rc != KS_OK) return rc;
+    }
+    return KS_OK;
 }
 
 }  // namespace ks

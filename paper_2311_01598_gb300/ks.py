@@ -29,6 +29,19 @@ class KSError(RuntimeError):
         self.code = code
 
 
+class Schedule(ctypes.Structure):
+    """ks_schedule: dataflow (MP/DC/OC), oc_variant (0 fused, 1 split),
+    chunk (jobs per batched launch group), order (0 given, 1 by level, 2 by key)."""
+    _fields_ = [("dataflow", ctypes.c_int32), ("oc_variant", ctypes.c_int32), ("chunk", ctypes.c_int32),
+                ("order", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.dataflow, self.oc_variant, self.chunk, self.order)
+
+    def __repr__(self):
+        return f"Schedule(dataflow={self.dataflow}, oc_variant={self.oc_variant}, chunk={self.chunk}, order={self.order})"
+
+
 class HostJob(ctypes.Structure):
     _fields_ = [("key", ctypes.c_void_p), ("level_towers", ctypes.c_uint32),
                 ("h_in", ctypes.c_void_p), ("h_out0", ctypes.c_void_p), ("h_out1", ctypes.c_void_p)]
@@ -72,6 +85,12 @@ def lib():
         L.ks_modup.argtypes = [vp, u32, vp, vp, vp]
         L.ks_moddown.argtypes = [vp, u32, vp, vp, vp]
         L.ks_switch_batch_host.argtypes = [vp, u32, ctypes.POINTER(HostJob), ci, vp]
+        L.ks_switch_batch_sched.argtypes = [vp, u32, ctypes.POINTER(Job), ctypes.POINTER(Schedule), vp]
+        L.ks_switch_batch_sched.restype = ci
+        L.ks_get_default_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
+        L.ks_get_default_schedule.restype = ci
+        L.ks_set_default_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
+        L.ks_set_default_schedule.restype = ci
         L.ks_switch_noalloc.argtypes = [vp, vp, u32, vp, vp, vp, vp]
         L.ks_switch_noalloc.restype = ci
         L.ks_switch_noalloc_max_words.argtypes = []
@@ -215,6 +234,26 @@ class Params:
         for i, (key, nact, d, o0, o1) in enumerate(jobs):
             arr[i] = Job(key.handle, nact, _ptr(d).value, _ptr(o0).value, _ptr(o1).value)
         check(lib().ks_switch_batch(self.handle, len(jobs), arr, df, _stream_handle(stream)))
+
+    @staticmethod
+    def _jobs(jobs):
+        jobs = list(jobs)
+        arr = (Job * max(1, len(jobs)))()
+        for i, (key, nact, d, o0, o1) in enumerate(jobs):
+            arr[i] = Job(key.handle, nact, _ptr(d).value, _ptr(o0).value, _ptr(o1).value)
+        return arr, len(jobs)
+
+    def switch_batch_sched(self, jobs, schedule: "Schedule", stream=None) -> None:
+        arr, n = self._jobs(jobs)
+        check(lib().ks_switch_batch_sched(self.handle, n, arr, ctypes.byref(schedule), _stream_handle(stream)))
+
+    def default_schedule(self) -> "Schedule":
+        sc = Schedule()
+        check(lib().ks_get_default_schedule(self.handle, ctypes.byref(sc)))
+        return sc
+
+    def set_default_schedule(self, schedule: "Schedule") -> None:
+        check(lib().ks_set_default_schedule(self.handle, ctypes.byref(schedule)))
 
     def switch_batch_host(self, jobs, dataflow=OC, stream=None) -> None:
         """jobs: iterable of (key, nact, h_in, h_out0, h_out1) with host
