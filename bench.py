@@ -75,11 +75,11 @@ def algorithmic_work(nact=NQ):
 
 
 def class_work(nact=NQ):
-    """Algorithmic work of the Output-Centric schedule per key switch, per
-    kernel class: (modular multiplications, bytes that must cross the
-    kernel's boundary).  A butterfly counts one modmul; each base-conversion
-    or key multiply-accumulate one; bytes are each limb read or written once
-    by the kernel (1 limb = N words of 8 bytes)."""
+    """Algorithmic work per key switch of each kernel class of the
+    Output-Centric schedule (split variant): (kind, units, bytes).  kind
+    "bfly": units are NTT butterflies; "mac": base-conversion
+    multiply-accumulates; "hbm": a streaming kernel judged on bytes.  Bytes
+    count each limb the kernel must read or write once (1 limb = 8N bytes)."""
     alpha = (NQ + DNUM - 1) // DNUM
     nd = (nact + alpha - 1) // alpha
     al = [min(alpha, nact - j * alpha) for j in range(nd)]
@@ -87,17 +87,18 @@ def class_work(nact=NQ):
     LA = {16: 8, 17: 9}.get(LOGN, (LOGN + 1) // 2)
     LB = LOGN - LA
     q_modup = sum(nact - a for a in al)          # ModUp limbs produced for Q towers
-    w = {}
-    w["ntt_inv_row"] = (nact * half * LB, 2 * nact * LIMB)
-    w["ntt_inv_col"] = ((nact + 2 * K) * half * LA + nact * N, 2 * (nact + 2 * K) * LIMB)
-    fc = nd * K + q_modup + 2 * nact
-    w["ntt_fwd_col"] = (fc * half * LA, 2 * fc * LIMB)
-    w["bconv_up"] = (sum(a * (K + nact - a) for a in al) * N, (2 * nact + nd * K + q_modup) * LIMB)
-    w["bconv_down"] = (2 * K * nact * N, (2 * K + 2 * nact) * LIMB)
-    w["oc_row_p"] = ((nd * K + 2 * K) * half * LB + 2 * nd * K * N, (nd * K + 2 * nd * K + 2 * K) * LIMB)
-    w["oc_row_q"] = ((q_modup + 2 * nact) * half * LB + 2 * nd * nact * N,
-                     (q_modup + 2 * nact + nact + 2 * nd * nact + 2 * nact) * LIMB)
-    return w
+    inv_limbs = nact + 2 * K                      # prep + ModDown P1
+    fwd_limbs = nd * K + q_modup + 2 * nact       # P section + Q section (ModUp, ModDown)
+    return {
+        "ntt_inv_row": ("bfly", inv_limbs * half * LB, 2 * inv_limbs * LIMB),
+        "ntt_inv_col": ("bfly", inv_limbs * half * LA, 2 * inv_limbs * LIMB),
+        "ntt_fwd_col": ("bfly", fwd_limbs * half * LA, 2 * fwd_limbs * LIMB),
+        "ntt_fwd_row": ("bfly", fwd_limbs * half * LB, 2 * fwd_limbs * LIMB),
+        "bconv_up": ("mac", sum(a * (K + nact - a) for a in al) * N, (2 * nact + nd * K + q_modup) * LIMB),
+        "bconv_down": ("mac", 2 * K * nact * N, (2 * K + 2 * nact) * LIMB),
+        "oc_comb_p": ("hbm", 2 * nd * K * N, (3 * nd * K + 2 * K) * LIMB),
+        "oc_comb_q": ("hbm", 2 * nd * nact * N, (q_modup + nact + 2 * nd * nact + 2 * nact + 2 * nact) * LIMB),
+    }
 
 
 def workload_config(B, dataflow, world):
@@ -314,29 +315,36 @@ def main():
 
     hbm_gbs, sm_max_mhz, peak_src = peaks()
     hbm_achieved = value / world * ALG_BYTES_PER_KS / 1e9
-    work = algorithmic_work()
 
-    roofline = None
-    if top is not None:
-        name, (cnt, tot_ms) = top
-        model = class_work().get(name) if args.dataflow == "OC" else None
-        # integer-multiply peak: 152 SMs x 64 IMAD lanes/clk x max SM clock,
-        # 10 32-bit multiplies per 64-bit Shoup/Montgomery modular product
-        alu_peak = 152 * 64 * sm_max_mhz * 1e6 / 10 / 1e9
-        roofline = {"bound": "alu", "kernel": name, "unit": "Gmodmul/s", "peak": round(alu_peak, 2),
-                    "peak_basis": f"152 SMs x 64 int-mul lanes/clk x {sm_max_mhz:.0f} MHz / 10 per modmul",
-                    "traffic": None, "launches_per_step": cnt / args.steps,
-                    "per_launch_ms": round(tot_ms / cnt, 4), "share_of_step": round(tot_ms / ms_prof, 4)}
-        if model is not None:
-            mm_ks, by_ks = model
-            secs_per_ks = tot_ms / 1e3 / (args.steps * B)
-            achieved = mm_ks / secs_per_ks / 1e9
-            roofline.update({"achieved": round(achieved, 2), "frac": round(achieved / alu_peak, 4),
-                             "algorithmic_modmul_per_launch": int(mm_ks * B * args.steps / cnt),
-                             "algorithmic_bytes_per_launch": int(by_ks * B * args.steps / cnt),
-                             "hbm_frac_of_kernel": round(by_ks / secs_per_ks / 1e9 / hbm_gbs, 4)})
+    bfly_peak, mac_peak = ks.probe_alu()
+    work = class_work()
+
+    def class_roofline(name, cnt, tot_ms):
+        secs_per_ks = tot_ms / 1e3 / (args.steps * B)
+        out = {"kernel": name, "launches_per_step": cnt / args.steps, "per_launch_ms": round(tot_ms / cnt, 4),
+               "share_of_step": round(tot_ms / ms_prof, 4), "traffic": None}
+        wk = work.get(name) if args.dataflow == "OC" and P.default_schedule().oc_variant == 1 else None
+        if wk is None:
+            out.update({"bound": "alu", "achieved": None, "peak": None, "frac": None})
+            return out
+        kind, units, nbytes = wk
+        gbs = nbytes / secs_per_ks / 1e9
+        out["algorithmic_bytes_per_launch"] = int(nbytes * B * args.steps / cnt)
+        if kind == "hbm":
+            out.update({"bound": "hbm", "unit": "GB/s", "achieved": round(gbs, 1), "peak": hbm_gbs,
+                        "frac": round(gbs / hbm_gbs, 4), "peak_basis": f"{peak_src} copy bandwidth"})
         else:
-            roofline.update({"achieved": None, "frac": None})
+            peak = bfly_peak if kind == "bfly" else mac_peak
+            rate = units / secs_per_ks
+            out.update({"bound": "alu", "unit": "G" + ("butterfly" if kind == "bfly" else "mac") + "/s",
+                        "achieved": round(rate / 1e9, 2), "peak": round(peak / 1e9, 2), "frac": round(rate / peak, 4),
+                        "algorithmic_units_per_launch": int(units * B * args.steps / cnt),
+                        "peak_basis": "ks_probe_alu: register-only loop of the same device code on all 152 SMs",
+                        "hbm_frac_of_kernel": round(gbs / hbm_gbs, 4)})
+        return out
+
+    roofline = class_roofline(top[0], *top[1]) if top is not None else None
+    per_kernel = {k: class_roofline(k, c, t) for k, (c, t) in prof.items()}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -359,9 +367,11 @@ def main():
                              "frac": round(hbm_achieved / hbm_gbs, 4), "basis": f"{peak_src} copy bandwidth",
                              "algorithmic_bytes_per_ks": ALG_BYTES_PER_KS},
             "roofline": roofline,
-            "kernels": {k: {"launches": c, "ms": round(t, 3)} for k, (c, t) in sorted(prof.items(),
-                                                                                     key=lambda kv: -kv[1][1])},
-            "work_per_ks": work,
+            "kernels": {k: {"launches": c, "ms": round(t, 3), "frac": per_kernel[k].get("frac"),
+                            "bound": per_kernel[k].get("bound")}
+                        for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "alu_probe": {"butterflies_per_s": bfly_peak, "bconv_macs_per_s": mac_peak},
+            "work_per_ks": algorithmic_work(),
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": B * NQ * LIMB,
                     "d2h_bytes_per_step": 2 * B * NQ * LIMB, "outputs_match_device_path": e2e_ok},

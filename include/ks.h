@@ -211,6 +211,65 @@ int ks_switch_batch_sched(const ks_params *params, uint32_t n, const ks_job *h_j
 int ks_get_default_schedule(const ks_params *params, ks_schedule *out);
 int ks_set_default_schedule(ks_params *params, const ks_schedule *schedule);
 
+/* ---------------------------------------------------------------------
+ * Autotuning (schedule search by measurement) and its cache.
+ * ------------------------------------------------------------------- */
+
+/* The candidate schedules the autotuner measures, in a fixed order (the
+ * same order the learned cost model predicts).  *n_out = count; up to max
+ * are written. */
+int ks_tune_candidates(const ks_params *params, uint32_t max, ks_schedule *out, uint32_t *n_out);
+
+/* Time every candidate on this batch (each: one untimed run, then the best
+ * of `reps` timed runs with CUDA events on `stream`; the jobs' outputs are
+ * overwritten -- every schedule writes the same values).  ms_out[i] gets
+ * candidate i's time in ms (max entries).  The fastest schedule is written
+ * to *best and stored in the params' tuning cache under this batch's
+ * signature (job count rounded up to a power of two, mean level rounded
+ * to a multiple of 4), where KS_AUTO finds it.  Synchronises `stream`. */
+int ks_autotune(ks_params *params, uint32_t n, const ks_job *h_jobs, uint32_t reps, ks_stream_t stream,
+                uint32_t max, float *ms_out, ks_schedule *best);
+
+/* Tuning cache: store / look up the schedule of a signature (n jobs, mean
+ * level); lookup returns KS_OK and fills *out, or KS_EINVAL if absent. */
+int ks_tune_cache_put(ks_params *params, uint32_t n_jobs, uint32_t mean_level, const ks_schedule *s);
+int ks_tune_cache_get(const ks_params *params, uint32_t n_jobs, uint32_t mean_level, ks_schedule *out);
+/* Persist / restore the cache as text (one entry per line, with the
+ * parameter set and device name it was measured on; entries for another
+ * parameter set or device are skipped on load). */
+int ks_tune_cache_save(const ks_params *params, const char *path);
+int ks_tune_cache_load(ks_params *params, const char *path);
+
+/* ---------------------------------------------------------------------
+ * Learned schedule cost model: an FP32 multilayer perceptron trained and
+ * evaluated on the device by the library's own kernels (dense layers with
+ * ReLU between them, linear output, mean-squared error with an optional
+ * 0/1 mask, backpropagation, Adam).  Parameters are laid out per layer as
+ * W [out][in] then b [out].  Device pointers d_*: row-major [batch][width].
+ * ------------------------------------------------------------------- */
+typedef struct ks_mlp ks_mlp;
+/* dims[0..n_layers]: input width, hidden widths, output width (each 1..256);
+ * weights He-normal from a SplitMix64 stream of `seed`, biases zero. */
+int ks_mlp_create(uint32_t n_layers, const uint32_t *dims, uint64_t seed, ks_mlp **out);
+void ks_mlp_destroy(ks_mlp *mlp);
+size_t ks_mlp_num_params(const ks_mlp *mlp);
+int ks_mlp_get_params(const ks_mlp *mlp, float *h_params);
+/* Replaces the parameters and resets the optimiser state. */
+int ks_mlp_set_params(ks_mlp *mlp, const float *h_params);
+int ks_mlp_forward(ks_mlp *mlp, uint32_t batch, const float *d_x, float *d_y, ks_stream_t stream);
+/* Loss sum(mask*(y-t)^2)/sum(mask) of the batch and its gradient with
+ * respect to every parameter (h_grad, same layout; may be NULL).
+ * Synchronises `stream` when h_loss or h_grad is given. */
+int ks_mlp_gradients(ks_mlp *mlp, uint32_t batch, const float *d_x, const float *d_t, const float *d_mask,
+                     float *h_grad, float *h_loss, ks_stream_t stream);
+/* One Adam step (beta 0.9/0.999, eps 1e-8) on the batch's gradient. */
+int ks_mlp_train_step(ks_mlp *mlp, uint32_t batch, const float *d_x, const float *d_t, const float *d_mask,
+                      float lr, float *h_loss, ks_stream_t stream);
+
+/* A key with pseudo-random residues generated on the device (for timing
+ * and tuning; it switches to no particular secret). */
+int ks_key_synthetic(const ks_params *params, uint64_t seed, ks_stream_t stream, ks_key **out);
+
 /* One job of a batched key switch whose data live in HOST memory. */
 typedef struct {
     const ks_key *key;
@@ -232,8 +291,65 @@ int ks_switch_batch_host(const ks_params *params, uint32_t n, const ks_host_job 
                          ks_dataflow dataflow, ks_stream_t stream);
 
 /* ---------------------------------------------------------------------
+ * Serving: continuous batching of key-switch requests.
+ *
+ * A server owns one scheduler thread, n_streams device lanes and a scratch
+ * pool of hbm_budget_bytes allocated at creation.  Requests are admitted in
+ * arrival order while fewer than max_inflight_jobs are on the device and
+ * their scratch fits in the pool (HBM-budget admission); admitted requests
+ * that share a parameter set are launched together (up to max_batch) as one
+ * Output-Centric batch on the next lane, so batches overlap on the device
+ * and requests that arrive meanwhile join the next batch.  Results equal
+ * ks_switch's.  Params, keys and data buffers stay owned by the caller and
+ * must outlive their requests.
+ * ------------------------------------------------------------------- */
+typedef struct ks_server ks_server;
+typedef struct {
+    uint32_t max_inflight_jobs;  /* slots: requests on the device at once (>= 1)     */
+    uint32_t max_batch;          /* requests per batched launch, 1..64               */
+    uint32_t n_streams;          /* device lanes, 1..16                              */
+    uint32_t reserved;           /* set to 0                                         */
+    uint64_t hbm_budget_bytes;   /* scratch pool, >= 1 MiB                           */
+} ks_server_config;
+typedef struct {
+    const ks_params *params;
+    const ks_key *key;
+    uint32_t level_towers;
+    const uint64_t *d_in;  /* device [l+1][N] */
+    uint64_t *d_out0;      /* device [l+1][N] */
+    uint64_t *d_out1;      /* device [l+1][N] */
+} ks_request;
+
+/* Create on the current device; starts the scheduler thread. */
+int ks_server_create(const ks_server_config *cfg, ks_server **out);
+/* Finish every queued and running request, then stop and free. */
+void ks_server_destroy(ks_server *server);
+/* Queue a request (thread-safe, non-blocking); *ticket identifies it.
+ * Requests whose scratch exceeds the whole budget fail with KS_EINVAL. */
+int ks_server_submit(ks_server *server, const ks_request *req, uint64_t *ticket);
+/* Wait for a request: its status, or KS_ETIMEOUT if still unfinished after
+ * timeout_ms (the request keeps running). */
+int ks_server_wait(ks_server *server, uint64_t ticket, uint32_t timeout_ms);
+/* Arrival, admission and completion times (seconds since the server was
+ * created) of a finished request. */
+int ks_server_times(ks_server *server, uint64_t ticket, double *t_arrive, double *t_admit, double *t_done);
+/* Requests finished, batches launched, largest batch so far. */
+int ks_server_stats(ks_server *server, uint64_t *n_done, uint64_t *n_batches, uint64_t *max_batch);
+/* Replay a trace: submit request i at arrival_s[i] seconds after the call
+ * (precise host timing), wait for all, write each request's latency
+ * (completion minus arrival, seconds) to latency_s. */
+int ks_server_run_trace(ks_server *server, uint32_t n, const ks_request *reqs, const double *arrival_s,
+                        double *latency_s, uint32_t timeout_ms);
+
+/* ---------------------------------------------------------------------
  * Measurement hooks (used by the benchmark; cheap when disabled).
  * ------------------------------------------------------------------- */
+
+/* Arithmetic ceilings of the current GPU for the two inner loops of key
+ * switching, measured with register-only loops of the same device code:
+ * forward NTT butterflies per second and base-conversion multiply-
+ * accumulates per second.  iters: loop trips per thread (e.g. 4096). */
+int ks_probe_alu(int iters, double *bfly_per_s, double *mac_per_s);
 
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t ks_kernel_launches(void);

@@ -259,7 +259,7 @@ static OcJob oc_job(const ks_params *P, const ks_key *K, int nact, const u64 *d,
     J.evk = K->d_evk;
     J.y = scratch;
     J.tmp = J.y + (size_t)nact * N;
-    J.cp = J.tmp + std::max((size_t)nd * P->kp, (size_t)(nd + 2) * nact) * N;
+    J.cp = J.tmp + ((size_t)nd * (nact + P->kp) + 2 * (size_t)nact) * N;
     J.pre = pre_level(P, nact);
     J.nact = nact;
     J.nd = nd;
@@ -564,18 +564,22 @@ int ks_switch(const ks_params *P, const ks_key *K, uint32_t level_towers, const 
                       (cudaStream_t)stream);
 }
 
-static int check_schedule(const ks_schedule *sc)
+}  // extern "C"
+
+namespace ks {
+
+int check_schedule(const ks_schedule *sc)
 {
     if (!sc) return fail(KS_EINVAL, "schedule is NULL");
     if (sc->dataflow < KS_MP || sc->dataflow > KS_OC) return fail(KS_EINVAL, "schedule dataflow must be MP, DC or OC");
-    if (sc->oc_variant < 0 || sc->oc_variant > 1) return fail(KS_EINVAL, "schedule oc_variant must be 0 or 1");
+    if (sc->oc_variant < 0 || sc->oc_variant > 2) return fail(KS_EINVAL, "schedule oc_variant must be 0, 1 or 2");
     if (sc->chunk < 1 || sc->chunk > kMaxBatch) return fail(KS_EINVAL, "schedule chunk must be in 1..64");
     if (sc->order < 0 || sc->order > 2) return fail(KS_EINVAL, "schedule order must be 0, 1 or 2");
     return KS_OK;
 }
 
 // Run a validated batch under a schedule.
-static int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st)
+int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st)
 {
     int rc;
     std::vector<uint32_t> idx(n);
@@ -628,7 +632,7 @@ static int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_sche
     return KS_OK;
 }
 
-static int check_batch(const ks_params *P, uint32_t n, const ks_job *jobs)
+int check_batch(const ks_params *P, uint32_t n, const ks_job *jobs)
 {
     int rc = check_params(P);
     if (rc) return rc;
@@ -639,6 +643,10 @@ static int check_batch(const ks_params *P, uint32_t n, const ks_job *jobs)
     return KS_OK;
 }
 
+}  // namespace ks
+
+extern "C" {
+
 int ks_switch_batch(const ks_params *P, uint32_t n, const ks_job *jobs, ks_dataflow dataflow, ks_stream_t stream)
 {
     int rc = check_batch(P, n, jobs);
@@ -648,6 +656,12 @@ int ks_switch_batch(const ks_params *P, uint32_t n, const ks_job *jobs, ks_dataf
     ks_schedule sc = P->sched;
     if (dataflow == KS_MP || dataflow == KS_DC) sc.dataflow = dataflow;
     if (dataflow == KS_OC) sc.dataflow = KS_OC;
+    if (dataflow == KS_AUTO && n > 0) {
+        uint64_t lv = 0;
+        for (uint32_t i = 0; i < n; ++i) lv += jobs[i].level_towers;
+        auto it = P->tune.find(tune_signature(n, (uint32_t)(lv / n)));
+        if (it != P->tune.end()) sc = it->second;
+    }
     return run_batch(const_cast<ks_params *>(P), n, jobs, sc, (cudaStream_t)stream);
 }
 

@@ -99,6 +99,8 @@ struct ks_params {
     std::map<void *, ks::Workspace *> ws;
     // default schedule (KS_OC / KS_AUTO without a tuned entry)
     ks_schedule sched{KS_OC, 1, 64, 0};
+    // tuning cache: (job-count bucket, mean-level bucket) -> schedule
+    std::map<std::pair<uint32_t, uint32_t>, ks_schedule> tune;
     // double-buffered device staging of ks_switch_batch_host
     std::mutex host_mu;
     ks::HostStage *stage = nullptr;
@@ -144,6 +146,15 @@ u64 mulmod_h(u64 a, u64 b, u64 m);
 u64 powmod_h(u64 b, u64 e, u64 m);
 u64 invmod_h(u64 a, u64 m);
 u64 shoup_h(u64 w, u64 q);  // floor(w * 2^64 / q)
+
+// Batch execution under a schedule (ks_api.cu), used by the autotuner.
+int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st);
+int check_batch(const ks_params *P, uint32_t n, const ks_job *jobs);
+int check_schedule(const ks_schedule *sc);
+// Tuning-cache signature of a batch.
+std::pair<uint32_t, uint32_t> tune_signature(uint32_t n, uint32_t mean_level);
+// Fill a key buffer with pseudo-random canonical residues (ks_kernels.cu).
+int launch_key_random(const Tables &T, u64 *evk, uint64_t seed, cudaStream_t st);
 
 // Build every host table and upload it (ks_host.cpp).
 int build_tables(ks_params *P);

@@ -16,7 +16,9 @@ __global__ void __launch_bounds__(S::THREADS_A) k_fwd_col(Tables T, LimbMaps ms)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
     ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(sm + (1 << S::LA) * S::COLS);
-    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    const int lg = blockIdx.y + blockIdx.z * gridDim.y;
+    if (lg >= ms.pre[ms.n]) return;
+    const LimbRef L = limb_ref(ms, lg, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
     const u64 q = T.modc[L.tf].q, q2 = 2 * q;
     const ulonglong2 *twt = T.tw + ((size_t)L.tf << S::LOGN);
@@ -50,7 +52,9 @@ __global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
-    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    const int lg = blockIdx.y + blockIdx.z * gridDim.y;
+    if (lg >= ms.pre[ms.n]) return;
+    const LimbRef L = limb_ref(ms, lg, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
     const ModC &mc = T.modc[L.tf];
     const u64 q = mc.q, q2 = 2 * q;
@@ -75,7 +79,9 @@ __global__ void __launch_bounds__(S::THREADS_B) k_inv_row(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
-    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    const int lg = blockIdx.y + blockIdx.z * gridDim.y;
+    if (lg >= ms.pre[ms.n]) return;
+    const LimbRef L = limb_ref(ms, lg, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
     const u64 q = T.modc[L.tf].q, q2 = 2 * q;
     const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
@@ -99,7 +105,9 @@ __global__ void __launch_bounds__(S::THREADS_A) k_inv_col(Tables T, LimbMaps ms)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
     ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(sm + (1 << S::LA) * S::COLS);
-    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, S::LOGN);
+    const int lg = blockIdx.y + blockIdx.z * gridDim.y;
+    if (lg >= ms.pre[ms.n]) return;
+    const LimbRef L = limb_ref(ms, lg, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
     const ModC &mc = T.modc[L.tf];
     const u64 q = mc.q, q2 = 2 * q;
@@ -162,6 +170,14 @@ static int launch_status(const char *what)
     return KS_OK;
 }
 
+// Grid over a limb set: the limb index is blockIdx.y + blockIdx.z*gridDim.y
+// (grid y and z are limited to 65535 each).
+static dim3 limb_grid(unsigned gx, int limbs)
+{
+    const unsigned gy = (unsigned)std::min(limbs, 32768);
+    return dim3(gx, gy, (unsigned)((limbs + gy - 1) / gy));
+}
+
 static bool any_scale(const LimbMaps &ms)
 {
     for (int j = 0; j < ms.n; ++j)
@@ -174,14 +190,14 @@ static void fwd_col_S(const Tables &T, const LimbMaps &m, cudaStream_t st)
 {
     set_smem_attrs<S>();
     KS_LAUNCH(st, "ntt_fwd_col",
-              k_fwd_col<S><<<dim3((1 << S::LB) / S::COLS, m.pre[m.n]), S::THREADS_A, S::SMEM_A, st>>>(T, m));
+              k_fwd_col<S><<<limb_grid((1 << S::LB) / S::COLS, m.pre[m.n]), S::THREADS_A, S::SMEM_A, st>>>(T, m));
 }
 
 template <class S>
 static void fwd_row_S(const Tables &T, const LimbMaps &m, bool canonical, cudaStream_t st)
 {
     set_smem_attrs<S>();
-    dim3 gb((1 << S::LA) / S::ROWS, m.pre[m.n]);
+    const dim3 gb = limb_grid((1 << S::LA) / S::ROWS, m.pre[m.n]);
     if (canonical)
         KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
     else
@@ -193,14 +209,14 @@ static void inv_row_S(const Tables &T, const LimbMaps &m, cudaStream_t st)
 {
     set_smem_attrs<S>();
     KS_LAUNCH(st, "ntt_inv_row",
-              k_inv_row<S><<<dim3((1 << S::LA) / S::ROWS, m.pre[m.n]), S::THREADS_B, S::SMEM_B, st>>>(T, m));
+              k_inv_row<S><<<limb_grid((1 << S::LA) / S::ROWS, m.pre[m.n]), S::THREADS_B, S::SMEM_B, st>>>(T, m));
 }
 
 template <class S>
 static void inv_col_S(const Tables &T, const LimbMaps &m, bool ninv, cudaStream_t st)
 {
     set_smem_attrs<S>();
-    dim3 ga((1 << S::LB) / S::COLS, m.pre[m.n]);
+    const dim3 ga = limb_grid((1 << S::LB) / S::COLS, m.pre[m.n]);
     if (any_scale(m))
         KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
     else if (ninv)
@@ -506,7 +522,9 @@ int launch_down_final(const Tables &T, int nact, int npoly, const u64 *cp, size_
 // grid (N/256, limbs)
 __global__ void k_scale(Tables T, LimbMaps ms, const ulonglong2 *fac)
 {
-    const LimbRef L = limb_ref(ms, blockIdx.y, T.nq, T.alpha, T.logN);
+    const int lg = blockIdx.y + blockIdx.z * gridDim.y;
+    if (lg >= ms.pre[ms.n]) return;
+    const LimbRef L = limb_ref(ms, lg, T.nq, T.alpha, T.logN);
     if (L.skip) return;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const u64 q = T.modc[L.tf].q;
@@ -518,7 +536,7 @@ int launch_scale(const Tables &T, const LimbMaps &m, const ulonglong2 *factors_f
 {
     if (m.n == 0 || m.pre[m.n] == 0) return KS_OK;
     const size_t N = (size_t)1 << T.logN;
-    KS_LAUNCH(st, "scale", k_scale<<<dim3((unsigned)(N / 256), m.pre[m.n]), 256, 0, st>>>(T, m, factors_full));
+    KS_LAUNCH(st, "scale", k_scale<<<limb_grid((unsigned)(N / 256), m.pre[m.n]), 256, 0, st>>>(T, m, factors_full));
     return launch_status("scale launch");
 }
 
@@ -562,6 +580,29 @@ int launch_key_convert(const Tables &T, u64 *evk, cudaStream_t st)
     const int limbs = T.ndig * 2 * (T.nq + T.kp);
     KS_LAUNCH(st, "key_convert", k_key_convert<<<dim3((unsigned)(N / 256), limbs), 256, 0, st>>>(T, evk));
     return launch_status("key conversion launch");
+}
+
+// Pseudo-random canonical residues (SplitMix64 finaliser of seed + index).
+__global__ void k_key_random(Tables T, u64 *evk, uint64_t seed)
+{
+    const int nfull = T.nq + T.kp;
+    const int limb = blockIdx.y;
+    const int tf = limb % nfull;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    u64 z = seed + ((size_t)limb * N + n + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    evk[(size_t)limb * N + n] = z % T.modc[tf].q;
+}
+
+int launch_key_random(const Tables &T, u64 *evk, uint64_t seed, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    const int limbs = T.ndig * 2 * (T.nq + T.kp);
+    KS_LAUNCH(st, "key_random", k_key_random<<<dim3((unsigned)(N / 256), limbs), 256, 0, st>>>(T, evk, seed));
+    return launch_status("synthetic key launch");
 }
 
 // a*b mod q for a, b < q (two Montgomery reductions).

@@ -132,7 +132,7 @@ struct OcJob {
     u64 *out0, *out1;
     const u64 *evk;
     u64 *y;    // [nact][N]
-    u64 *tmp;  // [max(nd*K, (nd+2)*nact)][N]
+    u64 *tmp;  // [nd*(nact+K) + 2*nact][N]
     u64 *cp;   // [2][nact+K][N]
     const ulonglong2 *pre;  // ModUp P1 factors of the level
     int nact, nd;
@@ -142,8 +142,10 @@ size_t oc_scratch_words(const Tables &T, int nact);
 // Output-Centric variants: FUSED runs each section's row pass, key product
 // and ModDown step in one kernel per row block; SPLIT runs the row passes
 // with the plain row-pass kernel and the key product / subtraction in a
-// streaming combine kernel.
-enum { KS_OC_FUSED = 0, KS_OC_SPLIT = 1 };
+// streaming combine kernel; WHOLE raises every digit to every tower in one
+// base-conversion launch and one NTT launch, then runs the same per-tower
+// combine kernels (special towers, ModDown, Q towers).
+enum { KS_OC_FUSED = 0, KS_OC_SPLIT = 1, KS_OC_WHOLE = 2 };
 int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st);
 
 }  // namespace ks

@@ -97,7 +97,7 @@ extern "C" int ks_switch_noalloc(const ks_params *P, const ks_key *K, uint32_t l
     J.evk = K->d_evk;
     J.y = base;
     J.tmp = J.y + (size_t)nact * N;
-    J.cp = J.tmp + std::max((size_t)nd * P->kp, (size_t)(nd + 2) * nact) * N;
+    J.cp = J.tmp + ((size_t)nd * (nact + P->kp) + 2 * (size_t)nact) * N;
     J.pre = P->d_up_pre_lvl + (size_t)(nact - 1) * P->nq;
     J.nact = nact;
     J.nd = nd;

@@ -310,12 +310,104 @@ size_t oc_scratch_words(const Tables &T, int nact)
 {
     const size_t N = (size_t)1 << T.logN;
     const size_t nd = (size_t)(nact + T.alpha - 1) / T.alpha;
-    const size_t tmp = std::max(nd * T.kp, (nd + 2) * (size_t)nact);
+    const size_t tmp = nd * ((size_t)nact + T.kp) + 2 * (size_t)nact;
     return ((size_t)nact + tmp + 2 * ((size_t)nact + T.kp)) * N;
+}
+
+// Whole-basis variant: tmp holds D [nd][nact+K] then v [2][nact].
+// P-tower combine of this layout: c'_{x,p_k} from D rows at tower nact+k.
+__global__ void __launch_bounds__(256) k_oc_comb_pw(Tables T, OcJobs oj)
+{
+    const int K = T.kp;
+    const OcJob &J = oj.job[blockIdx.y / K];
+    const int k = blockIdx.y % K;
+    const int tf = T.nq + k;
+    const int t = J.nact + k;
+    const int nt = J.nact + K;
+    const int nfull = T.nq + K;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const ModC &mc = T.modc[tf];
+    U128 sb = {0, 0}, sa = {0, 0};
+    for (int j = 0; j < J.nd; ++j) {
+        const u64 x = J.tmp[((size_t)j * nt + t) * N + n];
+        mac128(sb, x, J.evk[((size_t)(j * 2 + 0) * nfull + tf) * N + n]);
+        mac128(sa, x, J.evk[((size_t)(j * 2 + 1) * nfull + tf) * N + n]);
+    }
+    J.cp[(size_t)t * N + n] = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
+    J.cp[(size_t)(nt + t) * N + n] = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+}
+
+// Q-tower combine of the whole-basis layout.  grid (N/256, sum of nact).
+__global__ void __launch_bounds__(256) k_oc_comb_qw(Tables T, OcJobs oj)
+{
+    const int jb = find_slot(oj.pre, oj.n, blockIdx.y);
+    const OcJob &J = oj.job[jb];
+    const int t = blockIdx.y - oj.pre[jb];
+    const int nact = J.nact;
+    const int nt = nact + T.kp;
+    const int j0 = t / T.alpha;
+    const int nfull = T.nq + T.kp;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const ModC &mc = T.modc[t];
+    U128 sb = {0, 0}, sa = {0, 0};
+    for (int j = 0; j < J.nd; ++j) {
+        const u64 x = j == j0 ? J.d[(size_t)t * N + n] : J.tmp[((size_t)j * nt + t) * N + n];
+        mac128(sb, x, J.evk[((size_t)(j * 2 + 0) * nfull + t) * N + n]);
+        mac128(sa, x, J.evk[((size_t)(j * 2 + 1) * nfull + t) * N + n]);
+    }
+    const u64 *v = J.tmp + (size_t)J.nd * nt * N;
+    const u64 q40 = 40 * mc.q;
+    const u64 cb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
+    const u64 ca = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+    J.out0[(size_t)t * N + n] = reduce_any(cb + q40 - v[(size_t)t * N + n], mc.q, mc.one_sh);
+    J.out1[(size_t)t * N + n] = reduce_any(ca + q40 - v[(size_t)(nact + t) * N + n], mc.q, mc.one_sh);
+}
+
+static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    const int K = T.kp;
+    int rc;
+    LimbMaps m1, mD, mw, mv;
+    m1.n = mD.n = mw.n = mv.n = 0;
+    BUpJobs bu;
+    bu.n = 0;
+    BDnJobs bd;
+    bd.n = 0;
+    OcJobs oj;
+    oj.n = n;
+    oj.pre[0] = 0;
+    for (int i = 0; i < n; ++i) {
+        const OcJob &J = jobs[i];
+        const int nt = J.nact + K;
+        add_map(m1, LimbMap{J.d, J.y, J.pre, J.nact, 0, 0, 0, J.nact, -1}, J.nact);
+        add_bup(bu, T, BUpJob{J.y, J.tmp, (size_t)nt * N, J.nact, 0, nt, 0, -1});
+        add_map(mD, LimbMap{J.tmp, J.tmp, nullptr, nt, nt, 0, 0, J.nact, 0}, J.nd * nt);
+        add_map(mw, LimbMap{J.cp, J.cp, nullptr, K, nt, J.nact, J.nact, J.nact, -1}, 2 * K);
+        u64 *v = J.tmp + (size_t)J.nd * nt * N;
+        add_bdn(bd, BDnJob{J.cp, (size_t)nt * N, v, (size_t)J.nact * N, J.nact, 2});
+        add_map(mv, LimbMap{v, v, nullptr, J.nact, J.nact, 0, 0, J.nact, -1}, 2 * J.nact);
+        oj.job[i] = J;
+        oj.pre[i + 1] = oj.pre[i] + J.nact;
+    }
+    if ((rc = launch_ntt_inv(T, m1, false, st)) != KS_OK) return rc;   // ModUp P1
+    if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;          // P2, every tower
+    if ((rc = launch_ntt_fwd(T, mD, false, st)) != KS_OK) return rc;    // P3
+    KS_LAUNCH(st, "oc_comb_p", k_oc_comb_pw<<<dim3((unsigned)(N / 256), n * K), 256, 0, st>>>(T, oj));  // P4+P5, P towers
+    if ((rc = launch_ntt_inv(T, mw, false, st)) != KS_OK) return rc;    // ModDown P1
+    if ((rc = launch_bconv_down(T, bd, st)) != KS_OK) return rc;        // ModDown P2
+    if ((rc = launch_ntt_fwd(T, mv, false, st)) != KS_OK) return rc;    // ModDown P3
+    KS_LAUNCH(st, "oc_comb_q", k_oc_comb_qw<<<dim3((unsigned)(N / 256), oj.pre[n]), 256, 0, st>>>(T, oj));  // P4+P5 Q, ModDown P4
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(KS_ECUDA, std::string("OC whole-basis launch: ") + cudaGetErrorString(e));
+    return KS_OK;
 }
 
 static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int variant, cudaStream_t st)
 {
+    if (variant == KS_OC_WHOLE) return launch_oc_whole(T, n, jobs, st);
     const size_t N = (size_t)1 << T.logN;
     const int K = T.kp;
     int rc;

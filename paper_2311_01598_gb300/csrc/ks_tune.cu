@@ -1,0 +1,207 @@
+// ks_tune.cu -- schedule autotuner: exhaustive timing of the candidate
+// schedules of a batch with CUDA events, a per-parameter-set cache of the
+// winners (used by KS_AUTO), its text persistence, and synthetic keys for
+// tuning runs.
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "ks_internal.h"
+#include "ks_launch.h"
+
+namespace ks {
+
+// Candidate order is part of the interface: the learned cost model predicts
+// one time per candidate in this order.
+static std::vector<ks_schedule> candidates()
+{
+    std::vector<ks_schedule> c;
+    c.push_back({KS_MP, 0, 1, 0});
+    c.push_back({KS_DC, 0, 1, 0});
+    c.push_back({KS_OC, 0, 64, 0});
+    for (int ch : {1, 8, 64}) c.push_back({KS_OC, 1, ch, 0});
+    for (int ch : {1, 8, 16, 64}) c.push_back({KS_OC, 2, ch, 0});
+    c.push_back({KS_OC, 1, 64, 1});
+    c.push_back({KS_OC, 2, 64, 1});
+    return c;
+}
+
+std::pair<uint32_t, uint32_t> tune_signature(uint32_t n, uint32_t mean_level)
+{
+    uint32_t b = 1;
+    while (b < n) b <<= 1;
+    return {b, (mean_level + 2) / 4 * 4};
+}
+
+static std::string device_name(int dev)
+{
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return "unknown";
+    }
+    std::string s = prop.name;
+    for (char &ch : s)
+        if (ch == ' ') ch = '_';
+    return s;
+}
+
+static std::string params_tag(const ks_params *P)
+{
+    std::ostringstream o;
+    o << "logN=" << P->logN << " nq=" << P->nq << " kp=" << P->kp << " dnum=" << P->dnum << " q0=" << P->q[0]
+      << " p0=" << P->p[0];
+    return o.str();
+}
+
+}  // namespace ks
+
+using namespace ks;
+
+extern "C" {
+
+int ks_tune_candidates(const ks_params *P, uint32_t max, ks_schedule *out, uint32_t *n_out)
+{
+    if (!P || !n_out || (max > 0 && !out)) return fail(KS_EINVAL, "ks_tune_candidates: NULL argument");
+    std::vector<ks_schedule> c = candidates();
+    *n_out = (uint32_t)c.size();
+    for (uint32_t i = 0; i < max && i < c.size(); ++i) out[i] = c[i];
+    return KS_OK;
+}
+
+int ks_autotune(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps, ks_stream_t stream, uint32_t max,
+                float *ms_out, ks_schedule *best)
+{
+    int rc = check_batch(P, n, jobs);
+    if (rc) return rc;
+    if (n == 0 || reps < 1 || !best) return fail(KS_EINVAL, "ks_autotune: need n >= 1, reps >= 1 and best");
+    if (cudaSetDevice(P->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "cudaSetDevice failed");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "ks_autotune: event creation failed");
+    }
+    std::vector<ks_schedule> c = candidates();
+    float best_ms = 1e30f;
+    for (size_t i = 0; i < c.size() && rc == KS_OK; ++i) {
+        rc = run_batch(P, n, jobs, c[i], st);  // untimed: scratch allocation, caches
+        float m = 1e30f;
+        for (uint32_t r = 0; r < reps && rc == KS_OK; ++r) {
+            cudaEventRecord(e0, st);
+            rc = run_batch(P, n, jobs, c[i], st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaGetLastError();
+                rc = fail(KS_ECUDA, "ks_autotune: device error while timing");
+                break;
+            }
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            m = std::min(m, t);
+        }
+        if (i < max && ms_out) ms_out[i] = m;
+        if (m < best_ms) {
+            best_ms = m;
+            *best = c[i];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != KS_OK) return rc;
+    uint64_t lv = 0;
+    for (uint32_t i = 0; i < n; ++i) lv += jobs[i].level_towers;
+    P->tune[tune_signature(n, (uint32_t)(lv / n))] = *best;
+    return KS_OK;
+}
+
+int ks_tune_cache_put(ks_params *P, uint32_t n_jobs, uint32_t mean_level, const ks_schedule *s)
+{
+    if (!P) return fail(KS_EINVAL, "params is NULL");
+    int rc = check_schedule(s);
+    if (rc) return rc;
+    P->tune[tune_signature(n_jobs, mean_level)] = *s;
+    return KS_OK;
+}
+
+int ks_tune_cache_get(const ks_params *P, uint32_t n_jobs, uint32_t mean_level, ks_schedule *out)
+{
+    if (!P || !out) return fail(KS_EINVAL, "NULL argument");
+    auto it = P->tune.find(tune_signature(n_jobs, mean_level));
+    if (it == P->tune.end()) return fail(KS_EINVAL, "no tuned schedule for this signature");
+    *out = it->second;
+    return KS_OK;
+}
+
+int ks_tune_cache_save(const ks_params *P, const char *path)
+{
+    if (!P || !path) return fail(KS_EINVAL, "NULL argument");
+    std::ofstream f(path);
+    if (!f) return fail(KS_EINVAL, std::string("cannot write ") + path);
+    f << "# ks tuning cache v1\n";
+    const std::string tag = params_tag(P), dev = device_name(P->device);
+    for (const auto &kv : P->tune)
+        f << dev << " " << tag << " n=" << kv.first.first << " level=" << kv.first.second
+          << " sched=" << kv.second.dataflow << "," << kv.second.oc_variant << "," << kv.second.chunk << ","
+          << kv.second.order << "\n";
+    return f.good() ? KS_OK : fail(KS_EINVAL, std::string("write failed: ") + path);
+}
+
+int ks_tune_cache_load(ks_params *P, const char *path)
+{
+    if (!P || !path) return fail(KS_EINVAL, "NULL argument");
+    std::ifstream f(path);
+    if (!f) return fail(KS_EINVAL, std::string("cannot read ") + path);
+    const std::string prefix = device_name(P->device) + " " + params_tag(P) + " ";
+    std::string line;
+    while (std::getline(f, line)) {
+        if (line.empty() || line[0] == '#' || line.compare(0, prefix.size(), prefix) != 0) continue;
+        unsigned n = 0, lvl = 0;
+        int d = 0, v = 0, ch = 0, o = 0;
+        if (std::sscanf(line.c_str() + prefix.size(), "n=%u level=%u sched=%d,%d,%d,%d", &n, &lvl, &d, &v, &ch, &o) != 6)
+            continue;
+        ks_schedule s{d, v, ch, o};
+        if (check_schedule(&s) != KS_OK) continue;
+        P->tune[{n, lvl}] = s;
+    }
+    set_error("");
+    return KS_OK;
+}
+
+int ks_key_synthetic(const ks_params *P, uint64_t seed, ks_stream_t stream, ks_key **out)
+{
+    if (!P || !out) return fail(KS_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (cudaSetDevice(P->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "cudaSetDevice failed");
+    }
+    ks_key *K = new ks_key();
+    K->params = P;
+    K->bytes = (size_t)P->ndig * 2 * (P->nq + P->kp) * P->N * sizeof(u64);
+    if (cudaMalloc((void **)&K->d_evk, K->bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete K;
+        return fail(KS_ENOMEM, "key allocation failed");
+    }
+    int rc = launch_key_random(P->tables, K->d_evk, seed, (cudaStream_t)stream);
+    if (rc == KS_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(KS_ECUDA, "synthetic key generation failed");
+    }
+    if (rc != KS_OK) {
+        cudaFree(K->d_evk);
+        delete K;
+        return rc;
+    }
+    *out = K;
+    return KS_OK;
+}
+
+}  // extern "C"

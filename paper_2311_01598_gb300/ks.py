@@ -42,6 +42,16 @@ class Schedule(ctypes.Structure):
         return f"Schedule(dataflow={self.dataflow}, oc_variant={self.oc_variant}, chunk={self.chunk}, order={self.order})"
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_inflight_jobs", ctypes.c_uint32), ("max_batch", ctypes.c_uint32),
+                ("n_streams", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("hbm_budget_bytes", ctypes.c_uint64)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("params", ctypes.c_void_p), ("key", ctypes.c_void_p), ("level_towers", ctypes.c_uint32),
+                ("d_in", ctypes.c_void_p), ("d_out0", ctypes.c_void_p), ("d_out1", ctypes.c_void_p)]
+
+
 class HostJob(ctypes.Structure):
     _fields_ = [("key", ctypes.c_void_p), ("level_towers", ctypes.c_uint32),
                 ("h_in", ctypes.c_void_p), ("h_out0", ctypes.c_void_p), ("h_out1", ctypes.c_void_p)]
@@ -95,6 +105,44 @@ def lib():
         L.ks_switch_noalloc.restype = ci
         L.ks_switch_noalloc_max_words.argtypes = []
         L.ks_switch_noalloc_max_words.restype = ctypes.c_size_t
+        L.ks_tune_candidates.argtypes = [vp, u32, ctypes.POINTER(Schedule), ctypes.POINTER(u32)]
+        L.ks_autotune.argtypes = [vp, u32, ctypes.POINTER(Job), u32, vp, u32, ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(Schedule)]
+        L.ks_tune_cache_put.argtypes = [vp, u32, u32, ctypes.POINTER(Schedule)]
+        L.ks_tune_cache_get.argtypes = [vp, u32, u32, ctypes.POINTER(Schedule)]
+        L.ks_tune_cache_save.argtypes = [vp, ctypes.c_char_p]
+        L.ks_tune_cache_load.argtypes = [vp, ctypes.c_char_p]
+        L.ks_key_synthetic.argtypes = [vp, u64, vp, pvp]
+        L.ks_mlp_create.argtypes = [u32, ctypes.POINTER(u32), u64, pvp]
+        L.ks_mlp_destroy.argtypes = [vp]
+        L.ks_mlp_destroy.restype = None
+        L.ks_mlp_num_params.argtypes = [vp]
+        L.ks_mlp_num_params.restype = ctypes.c_size_t
+        L.ks_mlp_get_params.argtypes = [vp, vp]
+        L.ks_mlp_set_params.argtypes = [vp, vp]
+        L.ks_mlp_forward.argtypes = [vp, u32, vp, vp, vp]
+        L.ks_mlp_gradients.argtypes = [vp, u32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
+        L.ks_mlp_train_step.argtypes = [vp, u32, vp, vp, vp, ctypes.c_float, ctypes.POINTER(ctypes.c_float), vp]
+        for name in ("ks_tune_candidates", "ks_autotune", "ks_tune_cache_put", "ks_tune_cache_get",
+                     "ks_tune_cache_save", "ks_tune_cache_load", "ks_key_synthetic", "ks_mlp_create",
+                     "ks_mlp_get_params", "ks_mlp_set_params", "ks_mlp_forward", "ks_mlp_gradients",
+                     "ks_mlp_train_step"):
+            getattr(L, name).restype = ci
+        L.ks_server_create.argtypes = [ctypes.POINTER(ServerConfig), pvp]
+        L.ks_server_destroy.argtypes = [vp]
+        L.ks_server_destroy.restype = None
+        L.ks_server_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(u64)]
+        L.ks_server_wait.argtypes = [vp, u64, u32]
+        L.ks_server_times.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.ks_server_stats.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
+        L.ks_server_run_trace.argtypes = [vp, u32, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_double), u32]
+        for name in ("ks_server_create", "ks_server_submit", "ks_server_wait", "ks_server_times", "ks_server_stats",
+                     "ks_server_run_trace"):
+            getattr(L, name).restype = ci
+        L.ks_probe_alu.argtypes = [ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        L.ks_probe_alu.restype = ci
         L.ks_kernel_launches.argtypes = []
         L.ks_kernel_launches.restype = ctypes.c_uint64
         L.ks_profile_enable.argtypes = [ci]
@@ -255,6 +303,42 @@ class Params:
     def set_default_schedule(self, schedule: "Schedule") -> None:
         check(lib().ks_set_default_schedule(self.handle, ctypes.byref(schedule)))
 
+    # -- autotuning -----------------------------------------------------------
+    def tune_candidates(self) -> list:
+        n = ctypes.c_uint32()
+        check(lib().ks_tune_candidates(self.handle, 0, None, ctypes.byref(n)))
+        arr = (Schedule * n.value)()
+        check(lib().ks_tune_candidates(self.handle, n.value, arr, ctypes.byref(n)))
+        return [arr[i] for i in range(n.value)]
+
+    def autotune(self, jobs, reps: int = 3, stream=None):
+        """Time every candidate schedule on the batch; returns (best, [ms])."""
+        arr, n = self._jobs(jobs)
+        nc = len(self.tune_candidates())
+        ms = (ctypes.c_float * nc)()
+        best = Schedule()
+        check(lib().ks_autotune(self.handle, n, arr, reps, _stream_handle(stream), nc, ms, ctypes.byref(best)))
+        return best, [float(x) for x in ms]
+
+    def tune_cache_put(self, n_jobs: int, mean_level: int, schedule: "Schedule") -> None:
+        check(lib().ks_tune_cache_put(self.handle, n_jobs, mean_level, ctypes.byref(schedule)))
+
+    def tune_cache_get(self, n_jobs: int, mean_level: int):
+        sc = Schedule()
+        rc = lib().ks_tune_cache_get(self.handle, n_jobs, mean_level, ctypes.byref(sc))
+        return sc if rc == KS_OK else None
+
+    def tune_cache_save(self, path: str) -> None:
+        check(lib().ks_tune_cache_save(self.handle, path.encode()))
+
+    def tune_cache_load(self, path: str) -> None:
+        check(lib().ks_tune_cache_load(self.handle, path.encode()))
+
+    def key_synthetic(self, seed: int, stream=None) -> Key:
+        h = ctypes.c_void_p()
+        check(lib().ks_key_synthetic(self.handle, seed & (2**64 - 1), _stream_handle(stream), ctypes.byref(h)))
+        return Key(self, h.value)
+
     def switch_batch_host(self, jobs, dataflow=OC, stream=None) -> None:
         """jobs: iterable of (key, nact, h_in, h_out0, h_out1) with host
         buffers (pinned torch tensors or numpy arrays)."""
@@ -277,9 +361,128 @@ class Params:
         check(lib().ks_moddown(self.handle, nact, _ptr(cp), _ptr(out), _stream_handle(stream)))
 
 
+# -- serving ---------------------------------------------------------------------------
+class Server:
+    """Continuous-batching key-switch server (ks_server_*)."""
+
+    def __init__(self, max_inflight_jobs=32, max_batch=16, n_streams=2, hbm_budget_bytes=8 << 30):
+        cfg = ServerConfig(max_inflight_jobs, max_batch, n_streams, 0, hbm_budget_bytes)
+        h = ctypes.c_void_p()
+        check(lib().ks_server_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = []
+
+    def close(self):
+        if self.handle:
+            lib().ks_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def request(params, key, nact, d, out0, out1) -> Request:
+        return Request(params.handle, key.handle, nact, _ptr(d).value, _ptr(out0).value, _ptr(out1).value)
+
+    def submit(self, params, key, nact, d, out0, out1) -> int:
+        t = ctypes.c_uint64()
+        r = self.request(params, key, nact, d, out0, out1)
+        check(lib().ks_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
+        return int(lib().ks_server_wait(self.handle, ticket, timeout_ms))
+
+    def times(self, ticket: int):
+        a, m, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        check(lib().ks_server_times(self.handle, ticket, ctypes.byref(a), ctypes.byref(m), ctypes.byref(d)))
+        return a.value, m.value, d.value
+
+    def stats(self):
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        check(lib().ks_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"done": a.value, "batches": b.value, "max_batch": c.value}
+
+    def run_trace(self, reqs, arrival_s, timeout_ms: int = 600000):
+        """reqs: list of Request; arrival_s: seconds from now.  Returns latencies (s)."""
+        n = len(reqs)
+        arr = (Request * max(1, n))(*reqs)
+        at = (ctypes.c_double * max(1, n))(*[float(x) for x in arrival_s])
+        lat = (ctypes.c_double * max(1, n))()
+        check(lib().ks_server_run_trace(self.handle, n, arr, at, lat, timeout_ms))
+        return np.array([lat[i] for i in range(n)])
+
+
+# -- learned cost model --------------------------------------------------------------
+class Mlp:
+    """FP32 MLP trained and evaluated by the library's kernels (ks_mlp_*).
+    Inputs and targets are torch float32 CUDA tensors [batch][width]."""
+
+    def __init__(self, dims, seed: int = 1):
+        arr = (ctypes.c_uint32 * len(dims))(*dims)
+        h = ctypes.c_void_p()
+        check(lib().ks_mlp_create(len(dims) - 1, arr, seed & (2**64 - 1), ctypes.byref(h)))
+        self.handle = h.value
+        self.dims = list(dims)
+
+    def close(self):
+        if self.handle:
+            lib().ks_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nparams(self) -> int:
+        return int(lib().ks_mlp_num_params(self.handle))
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        check(lib().ks_mlp_get_params(self.handle, _ptr(out)))
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparams
+        check(lib().ks_mlp_set_params(self.handle, _ptr(p)))
+
+    def forward(self, x, stream=None):
+        import torch
+        y = torch.empty((x.shape[0], self.dims[-1]), dtype=torch.float32, device=x.device)
+        check(lib().ks_mlp_forward(self.handle, x.shape[0], _ptr(x), _ptr(y), _stream_handle(stream)))
+        return y
+
+    def gradients(self, x, t, mask=None, stream=None):
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_float()
+        check(lib().ks_mlp_gradients(self.handle, x.shape[0], _ptr(x), _ptr(t), _ptr(mask), _ptr(g),
+                                     ctypes.byref(loss), _stream_handle(stream)))
+        return float(loss.value), g
+
+    def train_step(self, x, t, lr: float, mask=None, stream=None) -> float:
+        loss = ctypes.c_float()
+        check(lib().ks_mlp_train_step(self.handle, x.shape[0], _ptr(x), _ptr(t), _ptr(mask), lr,
+                                      ctypes.byref(loss), _stream_handle(stream)))
+        return float(loss.value)
+
+
 # -- measurement hooks ---------------------------------------------------------------
 def kernel_launches() -> int:
     return int(lib().ks_kernel_launches())
+
+
+def probe_alu(iters: int = 4096) -> tuple[float, float]:
+    """(forward butterflies/s, base-conversion MACs/s) ceilings of this GPU."""
+    b, m = ctypes.c_double(), ctypes.c_double()
+    check(lib().ks_probe_alu(iters, ctypes.byref(b), ctypes.byref(m)))
+    return b.value, m.value
 
 
 def profile_enable(on: bool = True) -> None:

@@ -1,0 +1,206 @@
+"""Schedule selection: exhaustive autotuning data and the learned cost model.
+
+* ``collect``: sample workloads of the cost model's domain (logN 13-17, L+1
+  2-48, dnum 1..L+1, K 1-12, batch 1-256, capped so one batch holds at most
+  2^16*24*16 words of input), time every candidate schedule of each with
+  ``ks_autotune`` (CUDA events, best of k), and write one JSON line per
+  workload.
+* ``train``: fit the FP32 MLP (7 inputs -> 3 x 64 ReLU -> one predicted
+  log-time per candidate) on those timings with the library's own forward,
+  backward and Adam kernels.
+* ``evaluate``: for held-out workloads, pick the candidate with the lowest
+  predicted time and report its regret against the measured best (the
+  exhaustive search) and against the fixed default schedule.
+
+The MLP replaces exhaustive search at run time: ``choose`` predicts the
+schedule of an unseen workload without timing anything.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DATA_DIR = os.path.join(HERE, "data")
+HIDDEN = (64, 64, 64)
+FEATURE_NAMES = ("logN", "L+1", "dnum", "K", "log2 batch", "alpha", "log2 words")
+WORDS_CAP = (1 << 16) * 24 * 16
+
+
+def features(logN, nq, dnum, kp, batch):
+    """Model inputs, scaled to roughly unit range by fixed constants."""
+    alpha = -(-nq // dnum)
+    words = batch * nq * (1 << logN)
+    return np.array([(logN - 15) / 2.0, (nq - 25) / 14.0, (dnum - 12) / 12.0, (kp - 6.5) / 3.5,
+                     (math.log2(batch) - 4) / 2.5, (alpha - 12) / 12.0, (math.log2(words) - 22) / 3.0],
+                    dtype=np.float32)
+
+
+def sample_workload(rng):
+    logN = int(rng.integers(13, 18))
+    nq = int(rng.integers(2, 49))
+    dnum = int(rng.integers(1, nq + 1))
+    kp = int(rng.integers(1, 13))
+    batch = int(round(2 ** rng.uniform(0, 8)))
+    batch = max(1, min(batch, WORDS_CAP // (nq << logN)))
+    return logN, nq, dnum, kp, batch
+
+
+def collect(n_workloads, seed, out_path, reps=2, log=print):
+    """Time every candidate schedule on n_workloads sampled workloads."""
+    import torch
+
+    from . import ks
+    rng = np.random.default_rng(seed)
+    t0 = time.time()
+    with open(out_path, "w") as f:
+        for w in range(n_workloads):
+            logN, nq, dnum, kp, batch = sample_workload(rng)
+            P = ks.Params(logN, nq, kp, dnum)
+            key = P.key_synthetic(seed * 1000 + w)
+            qmin = min(P.q)
+            jobs = []
+            for b in range(batch):
+                d = torch.randint(0, qmin, (nq, P.N), dtype=torch.int64, device="cuda")
+                jobs.append((key, nq, d, ks.empty((nq, P.N)), ks.empty((nq, P.N))))
+            best, ms = P.autotune(jobs, reps=reps)
+            cands = [c.as_tuple() for c in P.tune_candidates()]
+            row = {"logN": logN, "nq": nq, "dnum": dnum, "kp": kp, "batch": batch,
+                   "ms": [round(m, 5) for m in ms], "best": cands.index(best.as_tuple())}
+            f.write(json.dumps(row) + "\n")
+            f.flush()
+            del jobs, key, P
+            torch.cuda.empty_cache()
+            if log and (w + 1) % 25 == 0:
+                log(f"collected {w + 1}/{n_workloads} workloads in {time.time() - t0:.0f} s")
+    return out_path
+
+
+def load(path):
+    with open(path) as f:
+        return [json.loads(l) for l in f if l.strip()]
+
+
+def arrays(rows):
+    X = np.stack([features(r["logN"], r["nq"], r["dnum"], r["kp"], r["batch"]) for r in rows])
+    # target: log of time per key switch (ms), one per candidate
+    T = np.array([[math.log(m / r["batch"]) for m in r["ms"]] for r in rows], dtype=np.float32)
+    return X, T
+
+
+class CostModel:
+    """The trained MLP plus the target normalisation (mean, scale)."""
+
+    def __init__(self, mlp, t_mean, t_scale):
+        self.mlp, self.t_mean, self.t_scale = mlp, float(t_mean), float(t_scale)
+
+    def predict(self, X):
+        import torch
+        x = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
+        y = self.mlp.forward(x).cpu().numpy()
+        return y * self.t_scale + self.t_mean
+
+    def save(self, path):
+        np.savez(path, params=self.mlp.get_params(), dims=np.array(self.mlp.dims), t_mean=self.t_mean,
+                 t_scale=self.t_scale)
+
+    @staticmethod
+    def load(path):
+        from . import ks
+        z = np.load(path)
+        m = ks.Mlp([int(v) for v in z["dims"]])
+        m.set_params(z["params"])
+        return CostModel(m, float(z["t_mean"]), float(z["t_scale"]))
+
+
+def train(rows, epochs=3000, lr=3e-3, seed=1, log=None):
+    """Full-batch Adam on the normalised log-times; returns a CostModel."""
+    import torch
+
+    from . import ks
+    X, T = arrays(rows)
+    t_mean, t_scale = float(T.mean()), float(T.std() + 1e-6)
+    Tn = (T - t_mean) / t_scale
+    dims = [X.shape[1], *HIDDEN, T.shape[1]]
+    mlp = ks.Mlp(dims, seed=seed)
+    x = torch.from_numpy(X).cuda()
+    t = torch.from_numpy(Tn.astype(np.float32)).cuda()
+    loss = None
+    for ep in range(epochs):
+        step_lr = lr * (0.5 * (1 + math.cos(math.pi * ep / epochs)) * 0.9 + 0.1)
+        loss = mlp.train_step(x, t, step_lr)
+        if log and (ep % 500 == 0 or ep == epochs - 1):
+            log(f"epoch {ep} loss {loss:.4f}")
+    return CostModel(mlp, t_mean, t_scale), loss
+
+
+def evaluate(model, rows, default_index):
+    """Regret of the model's choice and of the default schedule against the
+    measured best, per workload (fractions, 0 = optimal)."""
+    X, T = arrays(rows)
+    pred = model.predict(X)
+    pick = pred.argmin(axis=1)
+    ms = np.array([r["ms"] for r in rows])
+    best = ms.min(axis=1)
+    chosen = ms[np.arange(len(rows)), pick]
+    default = ms[:, default_index]
+    return {"n": len(rows),
+            "model_regret_mean": float(np.mean(chosen / best - 1)),
+            "model_regret_median": float(np.median(chosen / best - 1)),
+            "model_regret_p90": float(np.quantile(chosen / best - 1, 0.9)),
+            "model_time_over_best": float(chosen.sum() / best.sum() - 1),
+            "default_regret_mean": float(np.mean(default / best - 1)),
+            "default_time_over_best": float(default.sum() / best.sum() - 1),
+            "exact_pick_rate": float(np.mean(chosen == best))}
+
+
+def split(rows, frac=0.8, seed=0):
+    idx = np.random.default_rng(seed).permutation(len(rows))
+    k = int(len(rows) * frac)
+    return [rows[i] for i in idx[:k]], [rows[i] for i in idx[k:]]
+
+
+def default_candidate_index(candidates, default):
+    return [c.as_tuple() for c in candidates].index(default.as_tuple())
+
+
+def choose(model, params, batch, candidates):
+    """Schedule the model predicts fastest for a batch on params (no timing)."""
+    x = features(params.logN, params.nq, params.dnum, params.kp, batch)[None, :]
+    return candidates[int(model.predict(x)[0].argmin())]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    c = sub.add_parser("collect")
+    c.add_argument("--n", type=int, default=400)
+    c.add_argument("--seed", type=int, default=7)
+    c.add_argument("--reps", type=int, default=2)
+    c.add_argument("--out", default=os.path.join(DATA_DIR, "tune_gb300.jsonl"))
+    t = sub.add_parser("train")
+    t.add_argument("--data", default=os.path.join(DATA_DIR, "tune_gb300.jsonl"))
+    t.add_argument("--epochs", type=int, default=3000)
+    t.add_argument("--out", default=os.path.join(DATA_DIR, "cost_model_gb300.npz"))
+    a = ap.parse_args()
+    if a.cmd == "collect":
+        os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+        collect(a.n, a.seed, a.out, a.reps)
+    else:
+        from . import ks
+        rows = load(a.data)
+        tr, te = split(rows)
+        model, loss = train(tr, a.epochs, log=print)
+        P = ks.Params(12, 3, 1, 3, prime_bits=50)
+        di = default_candidate_index(P.tune_candidates(), P.default_schedule())
+        print(json.dumps({"train_loss": loss, "train": evaluate(model, tr, di), "test": evaluate(model, te, di)}))
+        model.save(a.out)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,114 @@
+"""Autotuner and learned cost model on the GPU.
+
+* the MLP's forward pass and gradients (library kernels, FP32) agree with
+  the float64 oracle MLP (relative error <= 1e-3);
+* Adam steps reduce the loss;
+* ks_autotune returns the fastest candidate it timed, caches it, and KS_AUTO
+  then runs that schedule with the oracle's results;
+* on the committed GB300 timing dataset, the model trained by the library's
+  kernels picks schedules within 5% of the exhaustive search on held-out
+  workloads and beats the fixed default schedule.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as mo
+from paper_2311_01598_gb300 import inputs
+from tests._gpu import built_lib, need_gpu, pair
+
+pytestmark = pytest.mark.gpu
+DIMS = [7, 64, 64, 64, 12]
+
+
+def _batch(seed, n=37):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, DIMS[0])).astype(np.float32)
+    T = rng.normal(size=(n, DIMS[-1])).astype(np.float32)
+    M = (rng.random((n, DIMS[-1])) > 0.25).astype(np.float32)
+    return X, T, M
+
+
+def test_mlp_forward_and_gradients_match_oracle():
+    torch = need_gpu()
+    ks = built_lib()
+    mlp = ks.Mlp(DIMS, seed=11)
+    p = mlp.get_params().astype(np.float64)
+    X, T, M = _batch(1)
+    x, t, m = (torch.from_numpy(a).cuda() for a in (X, T, M))
+    y = mlp.forward(x).cpu().numpy()
+    y_ref = mo.forward(p, DIMS, X)[-1]
+    assert np.max(np.abs(y - y_ref)) <= 1e-4 * max(1.0, np.max(np.abs(y_ref)))
+    for mask, mref in ((None, None), (m, M)):
+        loss, g = mlp.gradients(x, t, mask)
+        L_ref, g_ref = mo.gradients(p, DIMS, X, T, mref)
+        assert abs(loss - L_ref) <= 1e-4 * max(1.0, abs(L_ref))
+        assert np.linalg.norm(g - g_ref) <= 1e-3 * np.linalg.norm(g_ref)
+        assert np.max(np.abs(g - g_ref)) <= 1e-3 * np.max(np.abs(g_ref))
+
+
+def test_mlp_training_reduces_loss():
+    torch = need_gpu()
+    ks = built_lib()
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(256, 7)).astype(np.float32)
+    W = rng.normal(size=(7, 12)).astype(np.float32)
+    T = np.tanh(X @ W).astype(np.float32)
+    x, t = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
+    mlp = ks.Mlp(DIMS, seed=2)
+    first = mlp.train_step(x, t, 3e-3)
+    for _ in range(300):
+        last = mlp.train_step(x, t, 3e-3)
+    assert last < 0.1 * first
+
+
+def test_autotune_caches_fastest_and_auto_uses_it():
+    need_gpu()
+    ks = built_lib()
+    P, C = pair(12, 5, 2, 2)
+    s = inputs.ternary_secret(C.N, 4)
+    evk = C.keygen(s, inputs.galois_secret(s, 5), seed=4)
+    key = P.upload_key(evk)
+    jobs, want = [], []
+    for i in range(6):
+        d = inputs.uniform_towers(C.q, C.N, seed=200 + i)
+        want.append(C.keyswitch(5, d, evk))
+        jobs.append((key, 5, ks.to_device(d), ks.empty((5, C.N)), ks.empty((5, C.N))))
+    cands = P.tune_candidates()
+    best, ms = P.autotune(jobs, reps=2)
+    assert len(ms) == len(cands) and best.as_tuple() == cands[int(np.argmin(ms))].as_tuple()
+    cached = P.tune_cache_get(6, 5)
+    assert cached is not None and cached.as_tuple() == best.as_tuple()
+    for (_, _, _, o0, o1) in jobs:   # clear, then run KS_AUTO (the cached schedule)
+        o0.zero_()
+        o1.zero_()
+    P.switch_batch(jobs, "AUTO")
+    for (_, _, _, o0, o1), (w0, w1) in zip(jobs, want):
+        assert np.array_equal(ks.to_host(o0), w0) and np.array_equal(ks.to_host(o1), w1)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "cache.txt")
+        P.tune_cache_save(path)
+        P2 = ks.Params(12, 5, 2, 2)
+        P2.tune_cache_load(path)
+        assert P2.tune_cache_get(6, 5).as_tuple() == best.as_tuple()
+
+
+def test_cost_model_regret_on_gb300_dataset():
+    """Held-out regret of the learned schedule <= 5% of the exhaustive
+    autotuner's best, and less total time than the fixed default schedule."""
+    need_gpu()
+    ks = built_lib()
+    from paper_2311_01598_gb300 import tune
+    path = os.path.join(tune.DATA_DIR, "tune_gb300.jsonl")
+    if not os.path.exists(path):
+        pytest.skip("no committed timing dataset")
+    rows = tune.load(path)
+    train_rows, test_rows = tune.split(rows, 0.8, seed=0)
+    model, _ = tune.train(train_rows, epochs=3000)
+    P = ks.Params(12, 3, 1, 3, prime_bits=50)
+    di = tune.default_candidate_index(P.tune_candidates(), P.default_schedule())
+    ev = tune.evaluate(model, test_rows, di)
+    assert ev["model_time_over_best"] <= 0.05, ev
+    assert ev["model_time_over_best"] < ev["default_time_over_best"], ev
