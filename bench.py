@@ -198,12 +198,14 @@ def main():
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--dataflow", default="OC", choices=["MP", "DC", "OC"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default=None,
+                    help="fix the batch schedule 'dataflow,oc_variant,chunk,order' instead of autotuning it "
+                         "(used to take an ncu launch list of the schedule a plain run chose)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2311_01598_gb300 import dist as kdist
+    rank, world, local_rank = kdist.env_rank()
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -242,11 +244,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return kdist.max_over_ranks(x, dev)
 
     def timed(fn, steps, warmup):
         for _ in range(warmup):
@@ -263,7 +261,17 @@ def main():
         barrier()
         return max_over_ranks(e0.elapsed_time(e1))
 
-    step = lambda: P.switch_batch(jobs, args.dataflow, stream)  # noqa: E731
+    # the library's autotuner picks the batch's schedule (untimed); the timed
+    # steps then run KS_AUTO, which finds it in the tuning cache
+    if args.schedule:
+        tuned, tune_ms = ks.Schedule(*[int(x) for x in args.schedule.split(",")]), []
+        P.tune_cache_put(B, NQ, tuned)
+    else:
+        tuned, tune_ms = P.autotune(jobs, reps=2, stream=stream)
+    if args.dataflow == "OC":
+        step = lambda: P.switch_batch(jobs, "AUTO", stream)  # noqa: E731
+    else:
+        step = lambda: P.switch_batch(jobs, args.dataflow, stream)  # noqa: E731
 
     # ---- headline: device-resident inputs, clocks sampled during the region
     for _ in range(args.warmup):
@@ -287,7 +295,7 @@ def main():
 
     # ---- both Output-Centric variants on the same batch (schedule comparison)
     variants = {}
-    for vname, v in (("fused", 0), ("split", 1)):
+    for vname, v in (("fused", 0), ("split", 1), ("whole", 2)):
         sc = ks.Schedule(2, v, 64, 0)
         f = lambda sc=sc: P.switch_batch_sched(jobs, sc, stream)  # noqa: E731
         t = timed(f, max(3, args.steps // 2), 2)
@@ -323,7 +331,7 @@ def main():
         secs_per_ks = tot_ms / 1e3 / (args.steps * B)
         out = {"kernel": name, "launches_per_step": cnt / args.steps, "per_launch_ms": round(tot_ms / cnt, 4),
                "share_of_step": round(tot_ms / ms_prof, 4), "traffic": None}
-        wk = work.get(name) if args.dataflow == "OC" and P.default_schedule().oc_variant == 1 else None
+        wk = work.get(name) if args.dataflow == "OC" and tuned.dataflow == 2 and tuned.oc_variant in (1, 2) else None
         if wk is None:
             out.update({"bound": "alu", "achieved": None, "peak": None, "frac": None})
             return out
@@ -362,7 +370,9 @@ def main():
             "single_ciphertext": {k: round(v, 2) for k, v in singles.items()},
             "oc_batched_over_mp_plain": round(value / singles["MP"], 3),
             "oc_variants": variants,
-            "schedule": list(P.default_schedule().as_tuple()),
+            "schedule": {"tuned": list(tuned.as_tuple()), "fields": "dataflow, oc_variant, chunk, order",
+                         "source": "fixed by --schedule" if args.schedule else "ks_autotune",
+                         "candidates_ms": [round(x, 3) for x in tune_ms]},
             "hbm_roofline": {"achieved": round(hbm_achieved, 1), "peak": hbm_gbs, "unit": "GB/s",
                              "frac": round(hbm_achieved / hbm_gbs, 4), "basis": f"{peak_src} copy bandwidth",
                              "algorithmic_bytes_per_ks": ALG_BYTES_PER_KS},
@@ -376,6 +386,8 @@ def main():
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": B * NQ * LIMB,
                     "d2h_bytes_per_step": 2 * B * NQ * LIMB, "outputs_match_device_path": e2e_ok},
             "gpu_launches": int(launches),
+            "launch_window": {"first": int(l0), "count": int(launches),
+                              "note": "library launches before / inside the timed region"},
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

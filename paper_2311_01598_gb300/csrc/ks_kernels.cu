@@ -46,7 +46,10 @@ __global__ void __launch_bounds__(S::THREADS_A) k_fwd_col(Tables T, LimbMaps ms)
 }
 
 // Forward row pass (stages LA..logN-1).  grid (2^LA/ROWS, limbs).  Output
-// canonical (CANON) or lazy below 40q.
+// canonical (CANON) or lazy below 40q.  Loads and stores are coalesced (a
+// second shared-memory exchange returns the values to the first-round
+// layout; measured faster than storing each thread's consecutive values
+// with strided vector stores).
 template <class S, bool CANON>
 __global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMaps ms)
 {
@@ -303,7 +306,7 @@ void add_bup(BUpJobs &b, const Tables &T, const BUpJob &j)
 }
 
 // ModUp P2: grid (N/256, ceil(max targets/TT), digit blocks of all jobs).
-__global__ void __launch_bounds__(BC_THREADS) k_bconv_up(Tables T, BUpJobs bj)
+__global__ void __launch_bounds__(BC_THREADS, 3) k_bconv_up(Tables T, BUpJobs bj)
 {
     __shared__ u64 cs[kMaxQ][BC_TT];
     __shared__ int s_t[BC_TT];
@@ -388,7 +391,7 @@ void add_bdn(BDnJobs &b, const BDnJob &j)
 }
 
 // ModDown P2: grid (N/256, ceil(max nact/TT), polynomials of all jobs).
-__global__ void __launch_bounds__(BC_THREADS) k_bconv_down(Tables T, BDnJobs bj)
+__global__ void __launch_bounds__(BC_THREADS, 3) k_bconv_down(Tables T, BDnJobs bj)
 {
     __shared__ u64 cs[kMaxP][BC_TT];
     const int jb = find_slot(bj.zpre, bj.n, blockIdx.z);

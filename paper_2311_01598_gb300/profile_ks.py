@@ -3,6 +3,7 @@
 Used under ncu (the launch list and single-kernel captures under profiles/):
     python -m paper_2311_01598_gb300.profile_ks --dataflow OC,MP
     python -m paper_2311_01598_gb300.profile_ks --dataflow OC --batch 16
+    python -m paper_2311_01598_gb300.profile_ks --batch 4 --keys 4 --schedule 2,2,64,0
 Key generation runs first (a few launches), then one key switch per
 dataflow listed (or one batched call per dataflow with --batch B > 1).
 """
@@ -24,20 +25,26 @@ def main():
     ap.add_argument("--dnum", type=int, default=3)
     ap.add_argument("--level", type=int, default=0)
     ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--keys", type=int, default=1, help="distinct keys, used round-robin by the batch")
+    ap.add_argument("--schedule", default=None,
+                    help="'dataflow,oc_variant,chunk,order': one batched call with this schedule")
     a = ap.parse_args()
     P = ks.Params(a.logN, a.nq, a.kp, a.dnum)
     nact = a.level or a.nq
     s = inputs.ternary_secret(P.N, 1)
-    key = P.keygen(s, inputs.galois_secret(s, 5), 7)
+    keys = [P.key_synthetic(7 + k) if k else P.keygen(s, inputs.galois_secret(s, 5), 7) for k in range(a.keys)]
     jobs = []
     for i in range(a.batch):
         d = ks.to_device(inputs.uniform_towers(P.q[:nact], P.N, 3 + i))
-        jobs.append((key, nact, d, ks.empty((nact, P.N)), ks.empty((nact, P.N))))
-    for df in a.dataflow.split(","):
-        if a.batch == 1:
-            P.switch(key, nact, jobs[0][2], jobs[0][3], jobs[0][4], df)
-        else:
-            P.switch_batch(jobs, df)
+        jobs.append((keys[i % a.keys], nact, d, ks.empty((nact, P.N)), ks.empty((nact, P.N))))
+    if a.schedule:
+        P.switch_batch_sched(jobs, ks.Schedule(*[int(x) for x in a.schedule.split(",")]))
+    else:
+        for df in a.dataflow.split(","):
+            if a.batch == 1:
+                P.switch(keys[0], nact, jobs[0][2], jobs[0][3], jobs[0][4], df)
+            else:
+                P.switch_batch(jobs, df)
     torch.cuda.synchronize()
     print("ok launches", ks.kernel_launches())
 
