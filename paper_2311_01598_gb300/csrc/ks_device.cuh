@@ -9,8 +9,9 @@
 //   * Montgomery reduction (REDC) of a 128-bit sum of products with the
 //     stored key, whose factor 2^64 is folded in at upload.
 //   * Base conversion accumulates 28-bit-split partial products in three
-//     64-bit accumulators (no carries) and reduces once per output with a
-//     Montgomery reduction (constants stored times 2^64).
+//     64-bit accumulators (no carries; the middle one in Karatsuba form) and
+//     reduces once per output with a Montgomery reduction (constants stored
+//     times 2^64).
 //
 // NTT structure.  The negacyclic NTT of N = 2^(LA+LB) points is the in-place
 // Cooley-Tukey network whose stage s pairs indices differing in bit
@@ -101,13 +102,16 @@ struct BAcc {
     u64 a0, a1, a2;
 };
 __device__ __forceinline__ void bacc_zero(BAcc &A) { A.a0 = A.a1 = A.a2 = 0; }
+// Karatsuba form: the middle column is accumulated as (y0+y1)(c0+c1) and the
+// outer columns are subtracted at the end, three 32x32->64 products per term
+// instead of four.  Factors below 2^29 give products below 2^58, so up to 64
+// terms fit in 64 bits.
 __device__ __forceinline__ void bacc_mac(BAcc &A, u32 y0, u32 y1, u64 csplit)
 {
     const u32 c0 = (u32)csplit, c1 = (u32)(csplit >> 32);
     A.a0 += (u64)y0 * c0;
-    A.a1 += (u64)y0 * c1;
-    A.a1 += (u64)y1 * c0;
     A.a2 += (u64)y1 * c1;
+    A.a1 += (u64)(y0 + y1) * (c0 + c1);
 }
 // Constants are stored times 2^64 (Montgomery form), so the accumulated value
 // S = a0 + a1*2^28 + a2*2^56 is reduced by one Montgomery reduction:
@@ -116,10 +120,11 @@ __device__ __forceinline__ void bacc_mac(BAcc &A, u32 y0, u32 y1, u64 csplit)
 // in [0, 2q).
 __device__ __forceinline__ u64 bacc_reduce(const BAcc &A, const ModC &m)
 {
-    // 128-bit S from the three column sums
-    const u64 t1 = A.a1 << 28;
+    // 128-bit S from the three column sums (middle column recovered first)
+    const u64 a1 = A.a1 - A.a0 - A.a2;
+    const u64 t1 = a1 << 28;
     u64 lo = A.a0 + t1;
-    u64 hi = (A.a1 >> 36) + (lo < t1 ? 1 : 0);
+    u64 hi = (a1 >> 36) + (lo < t1 ? 1 : 0);
     const u64 t2 = A.a2 << 56;
     lo += t2;
     hi += (A.a2 >> 8) + (lo < t2 ? 1 : 0);
@@ -160,6 +165,15 @@ struct Shape {
     static constexpr int ROWPAD = (1 << LB) + (1 << LB) / MB;  // padded row in shared memory
     static constexpr int SMEM_A = (1 << LA) * COLS * 8 + (1 << LA) * 16;
     static constexpr int SMEM_B = ROWS * ROWPAD * 8;
+    // CTAs per SM requested from the register allocator: four (64 registers
+    // a thread) hides the global-load latency of the passes better than the
+    // compiler's default of three; the 32-value column pass of 2^17 stays at
+    // the default (it would spill).
+    static constexpr int MINB_A = LA <= 8 ? 4 : 1;
+    static constexpr int MINB_B = 4;
+    // The forward row kernel stages its rows' first-round twiddles (REGB
+    // entries a row, REGB-1 used) in shared memory after the row buffers.
+    static constexpr int SMEM_BT = SMEM_B + ROWS * REGB * 16;
 };
 
 template <int LOGN>
@@ -253,8 +267,10 @@ __device__ __forceinline__ void inv_round1(u64 (&x)[1 << RR], const TW &tw, u64 
 }
 
 // Twiddle fetchers.  Column pass: the first 2^LA entries of the tower's table,
-// staged in shared memory (G = 1).  Row pass: read through the read-only
-// path from the tower's global table (G = 2^LA + row).
+// staged in shared memory (G = 1).  Row pass: the forward row kernel stages
+// its rows' first-round twiddles in shared memory (TwStaged,
+// ks_ntt_core.cuh); TwRow reads straight from the tower's global table
+// (G = 2^LA + row).
 struct TwSmem {
     const ulonglong2 *t;
     __device__ __forceinline__ ulonglong2 operator()(int s, int i) const { return t[(1 << s) + i]; }

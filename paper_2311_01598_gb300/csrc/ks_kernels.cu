@@ -11,7 +11,7 @@ namespace ks {
 // ------------------------------------------------------------------ NTT passes
 // Forward column pass (stages 0..LA-1).  grid (2^LB/COLS, limbs).
 template <class S>
-__global__ void __launch_bounds__(S::THREADS_A) k_fwd_col(Tables T, LimbMaps ms)
+__global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_fwd_col(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(S::THREADS_A) k_fwd_col(Tables T, LimbMaps ms)
 // layout; measured faster than storing each thread's consecutive values
 // with strided vector stores).
 template <class S, bool CANON>
-__global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMaps ms)
+__global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_fwd_row(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
@@ -63,13 +63,18 @@ __global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMaps ms)
     const u64 q = mc.q, q2 = 2 * q;
     const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
     const int h = blockIdx.x * S::ROWS + rr;
-    const TwRow tw{T.tw + ((size_t)L.tf << S::LOGN), (1 << S::LA) + h};
+    const int G = (1 << S::LA) + h;
+    const ulonglong2 *twt = T.tw + ((size_t)L.tf << S::LOGN);
+    ulonglong2 *tsh = reinterpret_cast<ulonglong2 *>(sm + S::ROWS * S::ROWPAD) + rr * S::REGB;
     const u64 *gin = L.src + ((size_t)h << S::LB);
     u64 *gout = L.dst + ((size_t)h << S::LB);
     u64 x[S::REGB];
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) x[k] = gin[k * S::TB + tau];
-    row_fwd_core<S>(x, tw, sm + rr * S::ROWPAD, tau, q, q2);
+    stage_row_round1<S>(tsh, twt, G, tau);
+    static_assert(S::TB <= 32, "a row's threads share one warp");
+    __syncwarp();
+    row_fwd_core<S>(x, TwStaged<S>{tsh, twt, G}, sm + rr * S::ROWPAD, tau, q, q2);
     const u64 one_sh = CANON ? mc.one_sh : 0;
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = CANON ? reduce_any(x[k], q, one_sh) : x[k];
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(S::THREADS_B) k_fwd_row(Tables T, LimbMaps ms)
 // Inverse row pass (stages logN-1..LA), first half of the iNTT.  Input below
 // 2q; output below 2q.
 template <class S>
-__global__ void __launch_bounds__(S::THREADS_B) k_inv_row(Tables T, LimbMaps ms)
+__global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_inv_row(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(S::THREADS_B) k_inv_row(Tables T, LimbMaps ms)
 // Inverse column pass (stages LA-1..0), second half of the iNTT, then the
 // scale (SC: 0 none, 1 the job's per-entry scale, 2 N^-1); output canonical.
 template <class S, int SC>
-__global__ void __launch_bounds__(S::THREADS_A) k_inv_col(Tables T, LimbMaps ms)
+__global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_inv_col(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
@@ -160,8 +165,8 @@ static void set_smem_attrs()
     cudaFuncSetAttribute(k_inv_col<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
     cudaFuncSetAttribute(k_inv_col<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
     cudaFuncSetAttribute(k_inv_col<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-    cudaFuncSetAttribute(k_fwd_row<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
-    cudaFuncSetAttribute(k_fwd_row<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+    cudaFuncSetAttribute(k_fwd_row<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
+    cudaFuncSetAttribute(k_fwd_row<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
     cudaFuncSetAttribute(k_inv_row<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
     done = true;
 }
@@ -202,9 +207,9 @@ static void fwd_row_S(const Tables &T, const LimbMaps &m, bool canonical, cudaSt
     set_smem_attrs<S>();
     const dim3 gb = limb_grid((1 << S::LA) / S::ROWS, m.pre[m.n]);
     if (canonical)
-        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
     else
-        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, false><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, false><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
 }
 
 template <class S>
@@ -295,6 +300,8 @@ int launch_ntt_inv(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaS
 // ------------------------------------------------------------------ BConv
 constexpr int BC_TT = 8;  // target towers per block
 constexpr int BC_THREADS = 256;
+// Both base-conversion kernels ask for 4 CTAs/SM (64 registers a thread): the
+// extra warps hide the source loads better than the few spilled words cost.
 
 void add_bup(BUpJobs &b, const Tables &T, const BUpJob &j)
 {
@@ -306,7 +313,7 @@ void add_bup(BUpJobs &b, const Tables &T, const BUpJob &j)
 }
 
 // ModUp P2: grid (N/256, ceil(max targets/TT), digit blocks of all jobs).
-__global__ void __launch_bounds__(BC_THREADS, 3) k_bconv_up(Tables T, BUpJobs bj)
+__global__ void __launch_bounds__(BC_THREADS, 4) k_bconv_up(Tables T, BUpJobs bj)
 {
     __shared__ u64 cs[kMaxQ][BC_TT];
     __shared__ int s_t[BC_TT];
@@ -391,7 +398,7 @@ void add_bdn(BDnJobs &b, const BDnJob &j)
 }
 
 // ModDown P2: grid (N/256, ceil(max nact/TT), polynomials of all jobs).
-__global__ void __launch_bounds__(BC_THREADS, 3) k_bconv_down(Tables T, BDnJobs bj)
+__global__ void __launch_bounds__(BC_THREADS, 4) k_bconv_down(Tables T, BDnJobs bj)
 {
     __shared__ u64 cs[kMaxP][BC_TT];
     const int jb = find_slot(bj.zpre, bj.n, blockIdx.z);

@@ -42,6 +42,35 @@ __device__ __forceinline__ int rpad(int c)
     return c + c / S::MB;
 }
 
+// First-round twiddles of one row (local stages s < RB, group g < 2^s),
+// copied by the row's own TB threads into sh[2^s - 1 + g]: one load each,
+// issued together with the row's data loads, so the first round's
+// butterflies read shared memory instead of waiting on dependent L2 loads
+// (the first round's twiddles are common to the whole row; the second
+// round's differ per thread and stay in the table).
+template <class S>
+__device__ __forceinline__ void stage_row_round1(ulonglong2 *sh, const ulonglong2 *t, int G, int tau)
+{
+    for (int f = tau; f < S::REGB - 1; f += S::TB) {
+        const int st = 31 - __clz(f + 1);
+        sh[f] = __ldg(t + (G << st) + f + 1 - (1 << st));
+    }
+}
+
+// Twiddle fetcher of the forward row pass: first round from the staged row
+// block, second round from the tower table.
+template <class S>
+struct TwStaged {
+    const ulonglong2 *sh;
+    const ulonglong2 *t;
+    int G;
+    __device__ __forceinline__ ulonglong2 operator()(int s, int i) const
+    {
+        if (s < S::RB) return sh[(1 << s) - 1 + i];
+        return __ldg(t + (G << s) + i);
+    }
+};
+
 // Row pass of the forward NTT on one row held by TB threads: x enters and
 // leaves in the first-round layout (x[k] is element k*TB + tau of the row),
 // srow is the row's padded shared-memory buffer.  Contains block barriers:
