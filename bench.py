@@ -108,6 +108,31 @@ def workload_config(B, dataflow, world):
             "l2": "inputs+keys per step exceed L2 (no flush)"}
 
 
+def mixed_batch(P, keys, stream, timed, world, steps, seed, n_jobs=64):
+    """Key switches/s on a batch of n_jobs ciphertexts with levels uniform in
+    4..24 (L+1 towers), each with one of the given keys: the schedule the
+    autotuner picks, and the same schedule with jobs grouped by key."""
+    import numpy as np
+
+    from paper_2311_01598_gb300 import inputs, ks
+    rng = np.random.default_rng(seed)
+    levels = [int(x) for x in rng.integers(4, NQ + 1, size=n_jobs)]
+    kidx = [int(x) for x in rng.integers(0, len(keys), size=n_jobs)]
+    jobs = []
+    for i, (lv, k) in enumerate(zip(levels, kidx)):
+        d = ks.to_device(inputs.uniform_towers(P.q[:lv], N, seed=seed + 1 + i))
+        jobs.append((keys[k], lv, d, ks.empty((lv, N)), ks.empty((lv, N))))
+    tuned, _ = P.autotune(jobs, reps=2, stream=stream)
+    t_auto = timed(lambda: P.switch_batch(jobs, "AUTO", stream), steps, 2)
+    by_key = ks.Schedule(tuned.dataflow, tuned.oc_variant, tuned.chunk, 2)
+    t_key = timed(lambda: P.switch_batch_sched(jobs, by_key, stream), steps, 2)
+    return {"value": round(world * n_jobs * steps / (t_auto / 1e3), 2), "unit": "key-switches/s",
+            "jobs": n_jobs, "levels": "uniform 4..24 of 24", "keys": len(keys),
+            "schedule": list(tuned.as_tuple()),
+            "grouped_by_key": round(world * n_jobs * steps / (t_key / 1e3), 2),
+            "mean_level": round(sum(levels) / n_jobs, 2)}
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -301,6 +326,10 @@ def main():
         t = timed(f, max(3, args.steps // 2), 2)
         variants[vname] = round(world * B * max(3, args.steps // 2) / (t / 1e3), 2)
 
+    # ---- mixed batch: 64 ciphertexts with levels uniform in 4..24, each keyed
+    # by one of the 16 Galois keys (jobs of one key and level share key limbs)
+    mixed = mixed_batch(P, keys, stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 7)
+
     # ---- the plain single-ciphertext paths beside it
     singles = {}
     for df in ("MP", "DC", "OC"):
@@ -326,11 +355,17 @@ def main():
 
     bfly_peak, mac_peak = ks.probe_alu()
     work = class_work()
+    from paper_2311_01598_gb300 import launch_summary
+    traffic_rec = launch_summary.recorded_traffic()  # ncu DRAM bytes per key switch, current sources only
 
     def class_roofline(name, cnt, tot_ms):
         secs_per_ks = tot_ms / 1e3 / (args.steps * B)
         out = {"kernel": name, "launches_per_step": cnt / args.steps, "per_launch_ms": round(tot_ms / cnt, 4),
                "share_of_step": round(tot_ms / ms_prof, 4), "traffic": None}
+        if name in traffic_rec:
+            out["traffic"] = int(traffic_rec[name] * B * args.steps / cnt)
+            out["traffic_basis"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per key switch "
+                                    "(paper_2311_01598_gb300/data/ncu_traffic_gb300.json), scaled to this launch")
         wk = work.get(name) if args.dataflow == "OC" and tuned.dataflow == 2 and tuned.oc_variant in (1, 2) else None
         if wk is None:
             out.update({"bound": "alu", "achieved": None, "peak": None, "frac": None})
@@ -370,6 +405,7 @@ def main():
             "single_ciphertext": {k: round(v, 2) for k, v in singles.items()},
             "oc_batched_over_mp_plain": round(value / singles["MP"], 3),
             "oc_variants": variants,
+            "mixed_batch": mixed,
             "schedule": {"tuned": list(tuned.as_tuple()), "fields": "dataflow, oc_variant, chunk, order",
                          "source": "fixed by --schedule" if args.schedule else "ks_autotune",
                          "candidates_ms": [round(x, 3) for x in tune_ms]},

@@ -9,13 +9,51 @@ and share of the window, as a markdown table.  Library kernels are the ones
 named k_*; other launches (PyTorch's) are ignored.
 
     python -m paper_2311_01598_gb300.launch_summary launches.csv --first F --count C
+
+`traffic` turns an ncu report of a few key switches into DRAM bytes per key
+switch for each captured kernel and records them, with a hash of the kernel
+sources they were taken on, in data/ncu_traffic_gb300.json (bench.py reports
+them only while the sources are unchanged):
+
+    python -m paper_2311_01598_gb300.launch_summary traffic prof.ncu-rep --key-switches 4 \
+        --capture "<the ncu command>"
 """
 from __future__ import annotations
 
 import argparse
 import csv
+import hashlib
+import io
 import json
+import os
 import re
+import subprocess
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TRAFFIC_PATH = os.path.join(HERE, "data", "ncu_traffic_gb300.json")
+# the files whose change invalidates recorded per-kernel DRAM traffic
+KERNEL_SOURCES = ("csrc/ks_kernels.cu", "csrc/ks_oc.cu", "csrc/ks_device.cuh", "csrc/ks_ntt_core.cuh",
+                  "csrc/ks_launch.h", "csrc/ks_api.cu")
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(HERE, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic():
+    """{kernel library name: DRAM bytes per key switch} recorded on the
+    current sources, else {}."""
+    if not os.path.exists(TRAFFIC_PATH):
+        return {}
+    with open(TRAFFIC_PATH) as f:
+        rec = json.load(f)
+    if rec.get("sources_sha256") != kernel_sources_sha():
+        return {}
+    return {k: v["dram_bytes_per_ks"] for k, v in rec.get("kernels", {}).items()}
 
 
 def read_launches(path):
@@ -58,7 +96,55 @@ def to_markdown(table, total, n):
     return "\n".join(out)
 
 
+# library launch names (KS_LAUNCH) of the device kernels
+LIB_NAMES = {"k_fwd_row": "ntt_fwd_row", "k_fwd_col": "ntt_fwd_col", "k_inv_row": "ntt_inv_row",
+             "k_inv_col": "ntt_inv_col", "k_bconv_up": "bconv_up", "k_bconv_down": "bconv_down",
+             "k_oc_comb_qw": "oc_comb_q", "k_oc_comb_pw": "oc_comb_p", "k_oc_comb_q": "oc_comb_q",
+             "k_oc_comb_p": "oc_comb_p"}
+
+
+def traffic_from_report(rep, key_switches):
+    """Sum dram__bytes_read.sum + dram__bytes_write.sum of every captured
+    launch in an ncu report, per library kernel name, divided by the number
+    of key switches the captured launches processed."""
+    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], check=True, capture_output=True,
+                         text=True).stdout
+    rows = list(csv.reader(io.StringIO(out)))
+    hdr, units = rows[0], rows[1]
+    ix = {h: i for i, h in enumerate(hdr)}
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    per = {}
+    for r in rows[2:]:
+        m = re.match(r"(?:void )?(k_[A-Za-z0-9_]+)", r[ix["Kernel Name"]])
+        if not m or m.group(1) not in LIB_NAMES:
+            continue
+        b = 0.0
+        for name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            b += float(r[ix[name]].replace(",", "")) * scale[units[ix[name]]]
+        lib = LIB_NAMES[m.group(1)]
+        c, t = per.get(lib, (0, 0.0))
+        per[lib] = (c + 1, t + b)
+    return {k: {"launches": c, "dram_bytes_per_ks": t / key_switches} for k, (c, t) in per.items()}
+
+
+def main_traffic(argv):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("report")
+    ap.add_argument("--key-switches", type=int, required=True)
+    ap.add_argument("--capture", required=True, help="the command that made the report")
+    a = ap.parse_args(argv)
+    rec = {"sources_sha256": kernel_sources_sha(), "capture": a.capture, "key_switches": a.key_switches,
+           "kernels": traffic_from_report(a.report, a.key_switches)}
+    os.makedirs(os.path.dirname(TRAFFIC_PATH), exist_ok=True)
+    with open(TRAFFIC_PATH, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec, indent=1))
+
+
 def main():
+    import sys
+    if len(sys.argv) > 1 and sys.argv[1] == "traffic":
+        return main_traffic(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("csv")
     ap.add_argument("--first", type=int, default=0)
