@@ -133,6 +133,34 @@ def mixed_batch(P, keys, stream, timed, world, steps, seed, n_jobs=64):
             "mean_level": round(sum(levels) / n_jobs, 2)}
 
 
+TABLE3 = [("BTS1", 17, 28, 28, 1), ("BTS2", 17, 40, 20, 2), ("BTS3", 17, 45, 15, 3),
+          ("ARK", 16, 24, 6, 4), ("DPRIVE", 16, 26, 7, 3)]
+
+
+def table3_sets(stream, timed, world, steps, seed, batch=4):
+    """Key switches/s at the top level of each Table III parameter set (54-bit
+    primes), a batch of `batch` ciphertexts with distinct keys per step, under
+    the autotuned schedule; keys are synthetic (uniform words)."""
+    import torch
+
+    from paper_2311_01598_gb300 import inputs, ks
+    out = {}
+    for name, logN, nq, kp, dnum in TABLE3:
+        P3 = ks.Params(logN, nq, kp, dnum, prime_bits=BITS)
+        n3 = 1 << logN
+        keys3 = [P3.key_synthetic(seed + i) for i in range(batch)]
+        jobs3 = [(keys3[i], nq, ks.to_device(inputs.uniform_towers(P3.q, n3, seed=seed + 10 + i)),
+                  ks.empty((nq, n3)), ks.empty((nq, n3))) for i in range(batch)]
+        tuned3, _ = P3.autotune(jobs3, reps=2, stream=stream)
+        t = timed(lambda: P3.switch_batch(jobs3, "AUTO", stream), steps, 2)
+        out[name] = {"value": round(world * batch * steps / (t / 1e3), 2), "unit": "key-switches/s",
+                     "logN": logN, "q_towers": nq, "p_towers": kp, "dnum": dnum, "batch": batch,
+                     "schedule": list(tuned3.as_tuple())}
+        del jobs3, keys3, P3
+        torch.cuda.empty_cache()
+    return out
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
@@ -330,6 +358,9 @@ def main():
     # by one of the 16 Galois keys (jobs of one key and level share key limbs)
     mixed = mixed_batch(P, keys, stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 7)
 
+    # ---- the paper's parameter sets (Table III): 4 ciphertexts a step, own keys
+    table3 = table3_sets(stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 9)
+
     # ---- the plain single-ciphertext paths beside it
     singles = {}
     for df in ("MP", "DC", "OC"):
@@ -406,6 +437,7 @@ def main():
             "oc_batched_over_mp_plain": round(value / singles["MP"], 3),
             "oc_variants": variants,
             "mixed_batch": mixed,
+            "table3_sets": table3,
             "schedule": {"tuned": list(tuned.as_tuple()), "fields": "dataflow, oc_variant, chunk, order",
                          "source": "fixed by --schedule" if args.schedule else "ks_autotune",
                          "candidates_ms": [round(x, 3) for x in tune_ms]},

@@ -493,6 +493,52 @@ void orc_keyswitch(const orc_ctx *c, int nact, const u64 *d, const u64 *evk, u64
 }
 
 /* ------------------------------------------------------------------ */
+/* Rotations with hoisting (Sec. II-B names rotations as the key switches */
+/* of Galois automorphisms; hoisting shares one ModUp among them).      */
+/* ------------------------------------------------------------------ */
+
+/* X -> X^g on an evaluation-form tower.  Slot k holds a(psi^e_k) with
+ * e_k = 2 brv(k) + 1; a(X^g) there equals a at psi^(e_k g mod 2N), i.e. the
+ * slot k' with e_k' = e_k g mod 2N: a permutation of slots (g odd). */
+void orc_automorph_eval(const u64 *in, u64 *out, int logN, u64 g)
+{
+    u64 N = 1ull << logN, two_n = 2 * N;
+    u64 gg = g % two_n;
+    for (u64 k = 0; k < N; k++) {
+        u64 e = ((2 * bitrev(k, logN) + 1) * gg) % two_n;
+        out[k] = in[bitrev((e - 1) / 2, logN)];
+    }
+}
+
+/* Hoisted key switches of nrot rotations of one polynomial d (evaluation
+ * form, nact towers): the digits are raised once, D_j = ModUp_j(d); for
+ * rotation r every raised tower is mapped by X -> X^g_r and switched with
+ * key r:  out_r = ModDown(sum_j phi_r(D_j) * evk_r,j).  evks:
+ * [nrot][ndig][2][nq+kp][N]; out0, out1: [nrot][nact][N].  With g_r = 1 this
+ * is orc_keyswitch. */
+void orc_keyswitch_hoisted(const orc_ctx *c, int nact, const u64 *d, int nrot, const u64 *evks, const u64 *gal,
+                           u64 *out0, u64 *out1)
+{
+    u64 N = c->N;
+    int nd = orc_active_digits(c, nact);
+    int nt = nact + c->kp;
+    size_t key_words = (size_t)c->ndig * 2 * (c->nq + c->kp) * N;
+    u64 *D = (u64 *)malloc(sizeof(u64) * (size_t)nd * nt * N);
+    u64 *Dg = (u64 *)malloc(sizeof(u64) * (size_t)nd * nt * N);
+    u64 *cb = (u64 *)malloc(sizeof(u64) * (size_t)nt * N);
+    u64 *ca = (u64 *)malloc(sizeof(u64) * (size_t)nt * N);
+    orc_modup(c, nact, d, D);
+    for (int r = 0; r < nrot; r++) {
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int l = 0; l < nd * nt; l++) orc_automorph_eval(D + (size_t)l * N, Dg + (size_t)l * N, c->logN, gal[r]);
+        orc_apply_key(c, nact, Dg, evks + (size_t)r * key_words, cb, ca);
+        orc_moddown(c, nact, cb, out0 + (size_t)r * nact * N);
+        orc_moddown(c, nact, ca, out1 + (size_t)r * nact * N);
+    }
+    free(D); free(Dg); free(cb); free(ca);
+}
+
+/* ------------------------------------------------------------------ */
 /* Key generation (the paper is silent on sampling; reading R9).        */
 /* ------------------------------------------------------------------ */
 

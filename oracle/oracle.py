@@ -87,6 +87,10 @@ def _load():
         lib.orc_moddown.restype = None
         lib.orc_keyswitch.argtypes = [vp, ci, u64p, u64p, u64p, u64p]
         lib.orc_keyswitch.restype = None
+        lib.orc_automorph_eval.argtypes = [u64p, u64p, ci, ctypes.c_uint64]
+        lib.orc_automorph_eval.restype = None
+        lib.orc_keyswitch_hoisted.argtypes = [vp, ci, u64p, ci, u64p, u64p, u64p, u64p]
+        lib.orc_keyswitch_hoisted.restype = None
         lib.orc_keygen.argtypes = [vp, i8p, i64p, ctypes.c_uint64, u64p]
         lib.orc_keygen.restype = None
         lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ci, u64p]
@@ -137,6 +141,14 @@ def gen_primes(logN: int, bits: int, count: int) -> list[int]:
 
 def find_psi(q: int, logN: int) -> int:
     return int(_load().orc_find_psi(int(q), logN))
+
+
+def automorph_eval(a, logN: int, g: int) -> np.ndarray:
+    """X -> X^g on an evaluation-form tower (bit-reversed slot order)."""
+    a = _u64(a)
+    out = np.zeros_like(a)
+    _load().orc_automorph_eval(_p(a), _p(out), logN, g)
+    return out
 
 
 # ---------------------------------------------------------------- NTT
@@ -261,6 +273,18 @@ class Ctx:
         out0 = np.zeros((nact, self.N), dtype=np.uint64)
         out1 = np.zeros_like(out0)
         _lib.orc_keyswitch(self._h, nact, _p(d), _p(evk), _p(out0), _p(out1))
+        return out0, out1
+
+    def keyswitch_hoisted(self, nact: int, d, evks, gals):
+        """Key switches of the rotations X -> X^g (g in gals) of d with one
+        shared ModUp; evks[r] is the key of rotation r.  Returns (out0, out1),
+        each [len(gals)][nact][N]."""
+        d = _u64(d)
+        ev = _u64(np.stack([np.asarray(e, dtype=np.uint64) for e in evks]))
+        g = _u64(np.asarray(gals, dtype=np.uint64))
+        out0 = np.zeros((len(gals), nact, self.N), dtype=np.uint64)
+        out1 = np.zeros_like(out0)
+        _lib.orc_keyswitch_hoisted(self._h, nact, _p(d), len(gals), _p(ev), _p(g), _p(out0), _p(out1))
         return out0, out1
 
     def keygen(self, s, sp, seed: int) -> np.ndarray:

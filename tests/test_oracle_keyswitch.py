@@ -240,3 +240,71 @@ def test_apply_key_pointwise():
         want_a = sum(D[j, t].astype(object) * evk[j, 1, t].astype(object) for j in range(3)) % r
         assert list(cb[t]) == list(want_b) and list(ca[t]) == list(want_a)
     del rng
+
+
+# ------------------------------------------------------------------ rotations, hoisting
+def _coeff_automorph(a, g, q):
+    """a(X) -> a(X^g) mod (X^N + 1, q) on coefficients, written from the
+    definition: X^i goes to X^(i*g mod 2N), and X^N = -1."""
+    N = len(a)
+    out = [0] * N
+    for i, v in enumerate(a):
+        k = (i * g) % (2 * N)
+        if k < N:
+            out[k] = (out[k] + int(v)) % q
+        else:
+            out[k - N] = (out[k - N] - int(v)) % q
+    return np.array(out, dtype=np.uint64)
+
+
+@pytest.mark.parametrize("logN", [3, 6, 10])
+def test_automorph_eval_is_the_galois_map(logN):
+    """In the evaluation domain X -> X^g is a slot permutation equal to
+    NTT(a(X^g)) computed from the coefficients (NTT itself pinned against
+    its O(N^2) definition); it composes as phi_g phi_h = phi_gh and phi_1 = id."""
+    N = 1 << logN
+    q = orc.gen_primes(logN, 54, 1)[0]
+    psi = orc.find_psi(q, logN)
+    x = inputs.uniform_towers([q], N, seed=logN)[0]
+    a = orc.intt(x, logN, q, psi)
+    for g in [1, 3, 5, 2 * N - 1, pow(5, 7, 2 * N)]:
+        want = orc.ntt(_coeff_automorph(a, g, q), logN, q, psi)
+        got = orc.automorph_eval(x, logN, g)
+        assert np.array_equal(got, want), g
+        assert sorted(got.tolist()) == sorted(x.tolist())
+    g, h = 5, pow(5, 3, 2 * N)
+    assert np.array_equal(orc.automorph_eval(orc.automorph_eval(x, logN, h), logN, g),
+                          orc.automorph_eval(x, logN, g * h % (2 * N)))
+
+
+def test_hoisted_identity_is_the_key_switch():
+    """With g = 1 the hoisted path is the plain key switch, bit for bit."""
+    ctx = orc.Ctx(5, 6, 2, 2, bits=54)
+    s = inputs.ternary_secret(ctx.N, seed=21)
+    evk = ctx.keygen(s, inputs.galois_secret(s, 5), seed=22)
+    for nact in (6, 5, 3):
+        d = inputs.uniform_towers(ctx.q[:nact], ctx.N, seed=23 + nact)
+        w0, w1 = ctx.keyswitch(nact, d, evk)
+        h0, h1 = ctx.keyswitch_hoisted(nact, d, [evk], [1])
+        assert np.array_equal(h0[0], w0) and np.array_equal(h1[0], w1)
+
+
+@pytest.mark.parametrize("logN,nq,kp,dnum,nact", [(5, 6, 2, 2, 6), (6, 7, 3, 3, 5), (6, 4, 2, 1, 4)])
+def test_hoisted_rotations_decrypt(logN, nq, kp, dnum, nact):
+    """Each hoisted rotation decrypts: out0 + out1*s = phi_g(d)*s(X^g) up to
+    the key-switching noise bound (the automorphism permutes the raised
+    digits' coefficients up to sign, so the bound is unchanged), with
+    phi_g(d) computed from the coefficient definition."""
+    ctx = orc.Ctx(logN, nq, kp, dnum, bits=54)
+    N = ctx.N
+    s = inputs.ternary_secret(N, seed=31)
+    gals = inputs.galois_elements(N, 3, seed=32)
+    evks = [ctx.keygen(s, inputs.galois_secret(s, g), seed=33 + i) for i, g in enumerate(gals)]
+    d = inputs.uniform_towers(ctx.q[:nact], N, seed=34)
+    out0, out1 = ctx.keyswitch_hoisted(nact, d, evks, gals)
+    bound = _noise_bound(ctx, nact)
+    for r, g in enumerate(gals):
+        dg = np.stack([orc.ntt(_coeff_automorph(orc.intt(d[i], logN, ctx.q[i], ctx.psi_q[i]), g, ctx.q[i]),
+                               logN, ctx.q[i], ctx.psi_q[i]) for i in range(nact)])
+        e = _decrypt_noise(ctx, nact, dg, out0[r], out1[r], s, inputs.galois_secret(s, g))
+        assert max(abs(v) for v in e) <= bound, r
