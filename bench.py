@@ -133,6 +133,23 @@ def mixed_batch(P, keys, stream, timed, world, steps, seed, n_jobs=64):
             "mean_level": round(sum(levels) / n_jobs, 2)}
 
 
+def hoisted_rotations(P, keys, gals, d, stream, timed, world, steps):
+    """Rotations/s of R rotations of one ciphertext at the top level: the
+    hoisted call (one ModUp shared by all) against R independent key
+    switches (one batched call under KS_AUTO)."""
+    from paper_2311_01598_gb300 import ks
+    R = len(keys)
+    o0 = [ks.empty((NQ, N)) for _ in range(R)]
+    o1 = [ks.empty((NQ, N)) for _ in range(R)]
+    t_h = timed(lambda: P.switch_hoisted(keys, gals, NQ, d, o0, o1, stream), steps, 2)
+    jobs = [(keys[r], NQ, d, o0[r], o1[r]) for r in range(R)]
+    P.autotune(jobs, reps=2, stream=stream)
+    t_s = timed(lambda: P.switch_batch(jobs, "AUTO", stream), steps, 2)
+    return {"value": round(world * R * steps / (t_h / 1e3), 2), "unit": "rotations/s", "rotations": R,
+            "separate_key_switches": round(world * R * steps / (t_s / 1e3), 2),
+            "note": "hoisted: one ModUp, per rotation a permuted key product and a ModDown"}
+
+
 TABLE3 = [("BTS1", 17, 28, 28, 1), ("BTS2", 17, 40, 20, 2), ("BTS3", 17, 45, 15, 3),
           ("ARK", 16, 24, 6, 4), ("DPRIVE", 16, 26, 7, 3)]
 
@@ -358,6 +375,9 @@ def main():
     # by one of the 16 Galois keys (jobs of one key and level share key limbs)
     mixed = mixed_batch(P, keys, stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 7)
 
+    # ---- 8 rotations of one ciphertext: hoisted (one ModUp) vs 8 separate switches
+    hoisted = hoisted_rotations(P, keys[:8], gals[:8], d[0], stream, timed, world, steps=max(3, args.steps // 2))
+
     # ---- the paper's parameter sets (Table III): 4 ciphertexts a step, own keys
     table3 = table3_sets(stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 9)
 
@@ -438,6 +458,7 @@ def main():
             "oc_variants": variants,
             "mixed_batch": mixed,
             "table3_sets": table3,
+            "hoisted_rotations": hoisted,
             "schedule": {"tuned": list(tuned.as_tuple()), "fields": "dataflow, oc_variant, chunk, order",
                          "source": "fixed by --schedule" if args.schedule else "ks_autotune",
                          "candidates_ms": [round(x, 3) for x in tune_ms]},

@@ -127,6 +127,27 @@ int ks_switch(const ks_params *params, const ks_key *key, uint32_t level_towers,
               const uint64_t *d_in, uint64_t *d_out0, uint64_t *d_out1, ks_dataflow dataflow,
               ks_stream_t stream);
 
+/* Hoisted rotations (Sec. II-B: a rotation is the key switch of a Galois
+ * automorphism X -> X^g; hoisting shares one ModUp among several).
+ * For r < n_rot, with g_r = galois[r] (odd, < 2N) and keys[r] a key from
+ * s(X^g_r) to s:
+ *   (out0[r], out1[r]) = ModDown( sum_j phi_r(ModUp_j(d)) * evk_r,j )
+ * where phi_r permutes the evaluation slots as X -> X^g_r (slot k takes slot
+ * k' with 2brv(k')+1 = (2brv(k)+1) g_r mod 2N).  So out0[r] + out1[r]*s =
+ * phi_r(d)*s(X^g_r) + small noise: the key-switched second component of a
+ * ciphertext rotated by g_r (the caller applies phi_r to the first).  The
+ * digits of d are raised once for all rotations, so the result differs
+ * (within the same noise bound) from ks_switch of phi_r(d).  g_r = 1 gives
+ * ks_switch exactly.
+ *   level_towers, d_in : as ks_switch (device, evaluation form).
+ *   d_out0, d_out1     : host arrays of n_rot device pointers to [l+1][N];
+ *                        none may overlap d_in or one another.
+ * Scratch: the params object's per-stream workspace plus 2*(2l+2+K)*N words
+ * per rotation in flight (up to 64 at a time).  n_rot = 0 is a no-op. */
+int ks_switch_hoisted(const ks_params *params, uint32_t n_rot, const ks_key *const *keys, const uint64_t *galois,
+                      uint32_t level_towers, const uint64_t *d_in, uint64_t *const *d_out0, uint64_t *const *d_out1,
+                      ks_stream_t stream);
+
 /* One job of a batched key switch. */
 typedef struct {
     const ks_key *key;

@@ -78,6 +78,8 @@ struct Workspace {
     u64 *oc = nullptr;   // Output-Centric scratch of one job at the top level
     u64 *batch = nullptr;  // Output-Centric scratch of a batch
     size_t batch_words = 0;
+    u64 *rot = nullptr;    // c' and v of each hoisted rotation
+    size_t rot_words = 0;
 };
 
 static int ws_alloc(u64 **p, size_t words)
@@ -157,7 +159,7 @@ static void free_ws(ks_params *P)
     }
     for (auto &kv : P->ws) {
         Workspace *w = kv.second;
-        u64 *bufs[] = {w->y, w->D, w->cp, w->v, w->oc, w->batch};
+        u64 *bufs[] = {w->y, w->D, w->cp, w->v, w->oc, w->batch, w->rot};
         for (u64 *b : bufs)
             if (b) cudaFree(b);
         delete w;
@@ -219,6 +221,77 @@ static int run_mp(const ks_params *P, const ks_key *K, int nact, const u64 *d, u
     // P4 + P5: key product summed over digits.
     if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, K->d_evk, w->cp, false, st)) != KS_OK) return rc;
     return run_moddown(P, w, nact, 2, out0, out1, st);
+}
+
+// ------------------------------------------------------------------ hoisted rotations
+// One ModUp of d (as MP) shared by R rotations: rotation r's key product reads
+// the raised digits through X -> X^g_r, then the ModDowns of all rotations
+// run as batched launches (groups of kMaxBatch rotations).
+static int run_hoisted(ks_params *P, uint32_t R, const ks_key *const *keys, const uint64_t *gal, int nact,
+                       const u64 *d, u64 *const *out0, u64 *const *out1, cudaStream_t st)
+{
+    const Tables &T = P->tables;
+    const size_t N = P->N;
+    const int nt = nact + P->kp;
+    const int nd = active_digits(P, nact);
+    const int K = P->kp;
+    Workspace *w = nullptr;
+    int rc = get_ws(P, st, true, &w);
+    if (rc) return rc;
+    const uint32_t G = std::min<uint32_t>(R, kMaxBatch);
+    const size_t cp_words = 2 * (size_t)nt * N, v_words = 2 * (size_t)nact * N;
+    {
+        std::lock_guard<std::mutex> g(P->mu);
+        const size_t words = (size_t)G * (cp_words + v_words);
+        if (w->rot_words < words) {
+            if (w->rot) {
+                cudaStreamSynchronize(st);  // queued work may still use the old buffer
+                cudaFree(w->rot);
+                w->rot = nullptr;
+                w->rot_words = 0;
+            }
+            if ((rc = ws_alloc(&w->rot, words)) != KS_OK) return rc;
+            w->rot_words = words;
+        }
+    }
+    // ModUp P1-P3 once (digit towers are read from d by the key product).
+    LimbMap m1{d, w->y, pre_level(P, nact), nact, 0, 0, 0, nact, -1};
+    if ((rc = launch_ntt_inv(T, one_map(m1, nact), false, st)) != KS_OK) return rc;
+    BUpJobs bu;
+    bu.n = 0;
+    add_bup(bu, T, BUpJob{w->y, w->D, (size_t)nt * N, nact, 0, nt, 0, -1});
+    if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;
+    LimbMap mD{w->D, w->D, nullptr, nt, nt, 0, 0, nact, 0};
+    if ((rc = launch_ntt_fwd(T, one_map(mD, nd * nt), false, st)) != KS_OK) return rc;
+    for (uint32_t r0 = 0; r0 < R; r0 += G) {
+        const uint32_t g = std::min(G, R - r0);
+        u64 *cpr = w->rot, *vr = w->rot + (size_t)G * cp_words;
+        for (uint32_t i = 0; i < g; ++i)
+            if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, keys[r0 + i]->d_evk,
+                                       cpr + i * cp_words, false, st, gal[r0 + i])) != KS_OK)
+                return rc;
+        // ModDown of the g rotations: P1 iNTT, P2 BConv, P3 NTT, P4.
+        LimbMaps mP, mV;
+        mP.n = mV.n = 0;
+        BDnJobs bd;
+        bd.n = 0;
+        for (uint32_t i = 0; i < g; ++i) {
+            u64 *c = cpr + i * cp_words, *v = vr + i * v_words;
+            add_map(mP, LimbMap{c, c, nullptr, K, nt, nact, nact, nact, -1}, 2 * K);
+            add_bdn(bd, BDnJob{c, (size_t)nt * N, v, (size_t)nact * N, nact, 2});
+            add_map(mV, LimbMap{v, v, nullptr, nact, nact, 0, 0, nact, -1}, 2 * nact);
+        }
+        if ((rc = launch_ntt_inv(T, mP, false, st)) != KS_OK) return rc;
+        if ((rc = launch_bconv_down(T, bd, st)) != KS_OK) return rc;
+        if ((rc = launch_ntt_fwd(T, mV, false, st)) != KS_OK) return rc;
+        for (uint32_t i = 0; i < g; ++i) {
+            u64 *outs[2] = {out0[r0 + i], out1[r0 + i]};
+            if ((rc = launch_down_final(T, nact, 2, cpr + i * cp_words, (size_t)nt * N, vr + i * v_words,
+                                        (size_t)nact * N, outs, st)) != KS_OK)
+                return rc;
+        }
+    }
+    return KS_OK;
 }
 
 // ------------------------------------------------------------------ DC
@@ -562,6 +635,25 @@ int ks_switch(const ks_params *P, const ks_key *K, uint32_t level_towers, const 
     if ((rc = set_device(P)) != KS_OK) return rc;
     return switch_one(const_cast<ks_params *>(P), K, level_towers, d_in, d_out0, d_out1, dataflow,
                       (cudaStream_t)stream);
+}
+
+int ks_switch_hoisted(const ks_params *P, uint32_t n_rot, const ks_key *const *keys, const uint64_t *galois,
+                      uint32_t level_towers, const uint64_t *d_in, uint64_t *const *d_out0, uint64_t *const *d_out1,
+                      ks_stream_t stream)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (n_rot == 0) return KS_OK;
+    if (!keys || !galois || !d_out0 || !d_out1) return fail(KS_EINVAL, "ks_switch_hoisted: NULL array");
+    const uint64_t two_n = 2ull * P->N;
+    for (uint32_t r = 0; r < n_rot; ++r) {
+        if ((rc = check_job(P, keys[r], level_towers, d_in, d_out0[r], d_out1[r])) != KS_OK) return rc;
+        if (galois[r] % 2 == 0 || galois[r] >= two_n)
+            return fail(KS_EINVAL, "galois elements must be odd and below 2N");
+    }
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    return run_hoisted(const_cast<ks_params *>(P), n_rot, keys, galois, (int)level_towers, d_in, d_out0, d_out1,
+                       (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -109,9 +109,11 @@ __device__ __forceinline__ void bacc_zero(BAcc &A) { A.a0 = A.a1 = A.a2 = 0; }
 __device__ __forceinline__ void bacc_mac(BAcc &A, u32 y0, u32 y1, u64 csplit)
 {
     const u32 c0 = (u32)csplit, c1 = (u32)(csplit >> 32);
-    A.a0 += (u64)y0 * c0;
-    A.a2 += (u64)y1 * c1;
-    A.a1 += (u64)(y0 + y1) * (c0 + c1);
+    // one multiply-add of 32x32 bits into 64 bits each (mad.wide.u32): the
+    // C form of the same sums is not always compiled to it
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(A.a0) : "r"(y0), "r"(c0));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(A.a2) : "r"(y1), "r"(c1));
+    asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(A.a1) : "r"(y0 + y1), "r"(c0 + c1));
 }
 // Constants are stored times 2^64 (Montgomery form), so the accumulated value
 // S = a0 + a1*2^28 + a2*2^56 is reduced by one Montgomery reduction:

@@ -458,8 +458,18 @@ int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st)
 // ------------------------------------------------------------------ apply key
 // ModUp P4+P5 (single job): grid (N/256, nact+K).  The stored key carries the
 // folded factors and 2^64, so REDC of the 128-bit sum gives the folded c'.
+// With galois = g != 1 the raised digits are read through the automorphism
+// X -> X^g of the evaluation domain (slot n takes slot n' with
+// 2brv(n')+1 = (2brv(n)+1)g mod 2N): the key product of a hoisted rotation.
+__device__ __forceinline__ size_t galois_slot(size_t n, u64 g, int logN)
+{
+    const u64 two_n = 2ull << logN;
+    const u64 e = ((2ull * (__brev((unsigned)n) >> (32 - logN)) + 1) * g) & (two_n - 1);
+    return (size_t)(__brev((unsigned)((e - 1) >> 1)) >> (32 - logN));
+}
+
 __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, int j1, const u64 *d, const u64 *D,
-                                                   size_t dstride, const u64 *evk, u64 *cp, int accumulate)
+                                                   size_t dstride, const u64 *evk, u64 *cp, int accumulate, u64 galois)
 {
     const int t = blockIdx.y;
     const int nt = nact + T.kp;
@@ -467,11 +477,12 @@ __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, i
     const int tf = full_tower(t, nact, T.nq);
     const size_t N = (size_t)1 << T.logN;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t ns = galois == 1 ? n : galois_slot(n, galois, T.logN);
     const ModC &mc = T.modc[tf];
     U128 sb = {0, 0}, sa = {0, 0};
     for (int j = j0; j < j1; ++j) {
         const bool own = t < nact && t / T.alpha == j;
-        const u64 dv = own ? d[(size_t)t * N + n] : D[(size_t)(j - j0) * dstride + (size_t)t * N + n];
+        const u64 dv = own ? d[(size_t)t * N + ns] : D[(size_t)(j - j0) * dstride + (size_t)t * N + ns];
         const u64 kb = evk[(((size_t)j * 2 + 0) * nfull + tf) * N + n];
         const u64 ka = evk[(((size_t)j * 2 + 1) * nfull + tf) * N + n];
         mac128(sb, dv, kb);
@@ -491,12 +502,13 @@ __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, i
 }
 
 int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u64 *d, const u64 *D,
-                     size_t D_digit_stride, const u64 *evk, u64 *cp, bool accumulate, cudaStream_t st)
+                     size_t D_digit_stride, const u64 *evk, u64 *cp, bool accumulate, cudaStream_t st, uint64_t galois)
 {
     const size_t N = (size_t)1 << T.logN;
     dim3 g((unsigned)(N / 256), (unsigned)(nact + T.kp));
     KS_LAUNCH(st, "apply_key",
-              k_apply_key<<<g, 256, 0, st>>>(T, nact, j_begin, j_end, d, D, D_digit_stride, evk, cp, accumulate ? 1 : 0));
+              k_apply_key<<<g, 256, 0, st>>>(T, nact, j_begin, j_end, d, D, D_digit_stride, evk, cp, accumulate ? 1 : 0,
+                                             galois));
     return launch_status("apply-key launch");
 }
 

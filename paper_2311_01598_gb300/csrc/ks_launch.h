@@ -105,9 +105,11 @@ void add_bdn(BDnJobs &b, const BDnJob &j);
 int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st);
 
 // ModUp P4+P5 (single job): cp[x][t] = sum_j D_{j,t} * evk_{j,x,t}, D_{j,t} = d_t
-// inside digit j; D holds lazy NTT output.  accumulate: add to cp.
+// inside digit j; D holds lazy NTT output.  accumulate: add to cp.  galois
+// g != 1: every D_{j,t} (and d_t) is read through X -> X^g (hoisted rotation).
 int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u64 *d, const u64 *D,
-                     size_t D_digit_stride, const u64 *evk, u64 *cp, bool accumulate, cudaStream_t st);
+                     size_t D_digit_stride, const u64 *evk, u64 *cp, bool accumulate, cudaStream_t st,
+                     uint64_t galois = 1);
 // ModDown P4 (single job; P^-1 folded): out_x[i] = cp[x][i] - v[x][i] mod q_i,
 // v lazy NTT output.
 int launch_down_final(const Tables &T, int nact, int npoly, const u64 *cp, size_t cp_stride, const u64 *v,

@@ -1,8 +1,8 @@
 // ks_probe.cu -- arithmetic ceilings of this GPU for the two inner loops of
 // key switching, measured with the same device functions the kernels use:
 //   * the forward NTT butterfly (Shoup product by a twiddle, lazy sums),
-//   * the base-conversion multiply-accumulate (four 32x32->64 products into
-//     three 64-bit column sums).
+//   * the base-conversion multiply-accumulate (three 32x32->64 multiply-adds
+//     into three 64-bit column sums, Karatsuba form).
 // Each probe runs a register-only loop on every SM (no memory traffic inside
 // the timed loop), so its rate is what the integer pipes can sustain; the
 // benchmark divides the kernels' achieved rates by these to give a roofline

@@ -141,6 +141,9 @@ def lib():
         for name in ("ks_server_create", "ks_server_submit", "ks_server_wait", "ks_server_times", "ks_server_stats",
                      "ks_server_run_trace"):
             getattr(L, name).restype = ci
+        L.ks_switch_hoisted.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
+                                        ctypes.c_uint32, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        L.ks_switch_hoisted.restype = ci
         L.ks_probe_alu.argtypes = [ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.ks_probe_alu.restype = ci
         L.ks_kernel_launches.argtypes = []
@@ -267,6 +270,19 @@ class Params:
         df = DATAFLOWS[dataflow] if isinstance(dataflow, str) else dataflow
         check(lib().ks_switch(self.handle, key.handle, nact, _ptr(d), _ptr(out0), _ptr(out1), df,
                               _stream_handle(stream)))
+
+    def switch_hoisted(self, keys, galois, nact: int, d, outs0, outs1, stream=None) -> None:
+        """ks_switch_hoisted: key switches of the rotations X -> X^g (g in
+        galois, keys[r] the key of rotation r) of d with one shared ModUp;
+        outs0[r], outs1[r] receive rotation r."""
+        R = len(keys)
+        if not (len(galois) == len(outs0) == len(outs1) == R):
+            raise ValueError("keys, galois and outputs must have the same length")
+        ka = (ctypes.c_void_p * max(1, R))(*[k.handle for k in keys])
+        ga = (ctypes.c_uint64 * max(1, R))(*[int(g) for g in galois])
+        o0 = (ctypes.c_void_p * max(1, R))(*[_ptr(o).value for o in outs0])
+        o1 = (ctypes.c_void_p * max(1, R))(*[_ptr(o).value for o in outs1])
+        check(lib().ks_switch_hoisted(self.handle, R, ka, ga, nact, _ptr(d), o0, o1, _stream_handle(stream)))
 
     def switch_noalloc(self, key: Key, nact: int, d, out0, out1, stream=None) -> None:
         """ks_switch_noalloc: Output-Centric key switch using the library's
