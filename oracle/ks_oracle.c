@@ -602,20 +602,14 @@ void orc_sample_gauss(u64 seed, int n, i64 *out)
  * coefficient; stream seed^1 gives e_j (one integer polynomial per digit).
  * s: [N] in {-1,0,1}; sp: [N] signed coefficients of s'.
  * evk_out: [ndig][2][nq+kp][N] with index 0 = b, 1 = a. */
-void orc_keygen(const orc_ctx *c, const int8_t *s, const i64 *sp, u64 seed, u64 *evk_out)
+/* b_j = -a_j*s + e_j + [P g_j] s' on every tower, given a_j in the a-slots
+ * of evk_out and e_j drawn from stream seed^1 (digit, then coefficient). */
+static void keygen_b(const orc_ctx *c, const int8_t *s, const i64 *sp, u64 seed, u64 *evk_out)
 {
     u64 N = c->N;
     int nfull = c->nq + c->kp;
     int nd = c->ndig;
-    orc_rng ga = {seed ^ 0};
     orc_rng ge = {seed ^ 1};
-    /* a_j, drawn straight into the a-slot */
-    for (int j = 0; j < nd; j++)
-        for (int t = 0; t < nfull; t++) {
-            u64 r = tower_prime(c, c->nq, t);
-            u64 *dst = evk_out + (((size_t)j * 2 + 1) * nfull + t) * N;
-            for (u64 n = 0; n < N; n++) dst[n] = orc_uniform(&ga, r);
-        }
     i64 *e = (i64 *)malloc(sizeof(i64) * (size_t)nd * N);
     for (int j = 0; j < nd; j++)
         for (u64 n = 0; n < N; n++) e[(size_t)j * N + n] = orc_gauss(&ge);
@@ -649,6 +643,71 @@ void orc_keygen(const orc_ctx *c, const int8_t *s, const i64 *sp, u64 seed, u64 
         free(sh); free(sph); free(eh);
     }
     free(e);
+}
+
+/* Evaluation key for switching from s' to s (Han & Ki hybrid key):
+ *   b_j = -a_j * s + e_j + [P * g_j] * s'   (evaluation form, per tower),
+ * g_j the CRT idempotent of digit j: [P*g_j]_{q_i} = [P]_{q_i} if q_i is in
+ * digit j of the full level, 0 otherwise; 0 on the P towers.
+ * Draw order: stream seed^0 gives a_j for j, then tower in D_L order, then
+ * coefficient; stream seed^1 gives e_j (one integer polynomial per digit).
+ * s: [N] in {-1,0,1}; sp: [N] signed coefficients of s'.
+ * evk_out: [ndig][2][nq+kp][N] with index 0 = b, 1 = a. */
+void orc_keygen(const orc_ctx *c, const int8_t *s, const i64 *sp, u64 seed, u64 *evk_out)
+{
+    u64 N = c->N;
+    int nfull = c->nq + c->kp;
+    orc_rng ga = {seed ^ 0};
+    /* a_j, drawn straight into the a-slot */
+    for (int j = 0; j < c->ndig; j++)
+        for (int t = 0; t < nfull; t++) {
+            u64 r = tower_prime(c, c->nq, t);
+            u64 *dst = evk_out + (((size_t)j * 2 + 1) * nfull + t) * N;
+            for (u64 n = 0; n < N; n++) dst[n] = orc_uniform(&ga, r);
+        }
+    keygen_b(c, s, sp, seed, evk_out);
+}
+
+/* Compressed keys (Sec. IV-D: regenerating the key's uniform half from a
+ * seed halves the key's data movement; the sampling is reading R16).
+ * SplitMix64's state after k outputs is seed + k*0x9E3779B97F4A7C15, so
+ * output number c+1 of the stream is reached directly:
+ *   SM(x, c) = finaliser(x + (c+1)*0x9E3779B97F4A7C15).
+ * a_j at full tower t (q_0..q_L, p_0..p_{K-1}), slot n: the first of the
+ * draws v_m = SM(seed^2, ((j*nfull + t)*N + n)*64 + m) & mask(bitlen(r)),
+ * m = 0..63, with v_m < r; if all 64 reject (probability below 2^-64 for
+ * primes above 2^(bits-1)) the last one reduced mod r. */
+static u64 splitmix_at(u64 x, u64 c)
+{
+    orc_rng g = {x + c * 0x9E3779B97F4A7C15ULL};
+    return orc_rng_next(&g);
+}
+u64 orc_key_a_word(u64 seed, int j, int t, u64 n, int logN, int nfull, u64 r)
+{
+    int b = bitlen(r);
+    u64 mask = b >= 64 ? ~(u64)0 : (((u64)1 << b) - 1);
+    u64 base = (((u64)j * (u64)nfull + (u64)t) * ((u64)1 << logN) + n) * 64;
+    u64 v = 0;
+    for (int m = 0; m < 64; m++) {
+        v = splitmix_at(seed ^ 2, base + (u64)m) & mask;
+        if (v < r) return v;
+    }
+    return v % r;
+}
+/* The full evaluation key of a compressed key: a_j regenerated as above,
+ * e_j and b_j as orc_keygen.  Same layout as orc_keygen. */
+void orc_keygen_compressed(const orc_ctx *c, const int8_t *s, const i64 *sp, u64 seed, u64 *evk_out)
+{
+    u64 N = c->N;
+    int nfull = c->nq + c->kp;
+    for (int j = 0; j < c->ndig; j++)
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int t = 0; t < nfull; t++) {
+            u64 r = tower_prime(c, c->nq, t);
+            u64 *dst = evk_out + (((size_t)j * 2 + 1) * nfull + t) * N;
+            for (u64 n = 0; n < N; n++) dst[n] = orc_key_a_word(seed, j, t, n, c->logN, nfull, r);
+        }
+    keygen_b(c, s, sp, seed, evk_out);
 }
 
 /* Negacyclic schoolbook product mod q (a*b mod X^N+1): pins the NTT. */

@@ -91,6 +91,10 @@ def _load():
         lib.orc_automorph_eval.restype = None
         lib.orc_keyswitch_hoisted.argtypes = [vp, ci, u64p, ci, u64p, u64p, u64p, u64p]
         lib.orc_keyswitch_hoisted.restype = None
+        lib.orc_keygen_compressed.argtypes = [vp, i8p, i64p, ctypes.c_uint64, u64p]
+        lib.orc_keygen_compressed.restype = None
+        lib.orc_key_a_word.argtypes = [ctypes.c_uint64, ci, ci, ctypes.c_uint64, ci, ci, ctypes.c_uint64]
+        lib.orc_key_a_word.restype = ctypes.c_uint64
         lib.orc_keygen.argtypes = [vp, i8p, i64p, ctypes.c_uint64, u64p]
         lib.orc_keygen.restype = None
         lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ci, u64p]
@@ -293,6 +297,19 @@ class Ctx:
         evk = np.zeros((self.ndig, 2, self.nq + self.kp, self.N), dtype=np.uint64)
         _lib.orc_keygen(self._h, _p(s), _p(sp), seed & (2**64 - 1), _p(evk))
         return evk
+
+    def keygen_compressed(self, s, sp, seed: int) -> np.ndarray:
+        """Full evaluation key of a compressed key (a_j regenerated from the
+        seed, see orc_keygen_compressed); same layout as keygen."""
+        s = np.ascontiguousarray(s, dtype=np.int8)
+        sp = np.ascontiguousarray(sp, dtype=np.int64)
+        evk = np.zeros((self.ndig, 2, self.nq + self.kp, self.N), dtype=np.uint64)
+        _lib.orc_keygen_compressed(self._h, _p(s), _p(sp), seed & (2**64 - 1), _p(evk))
+        return evk
+
+    def key_a_word(self, seed: int, j: int, t: int, n: int) -> int:
+        r = (self.q + self.p)[t]
+        return int(_lib.orc_key_a_word(seed & (2**64 - 1), j, t, n, self.logN, self.nq + self.kp, r))
 
     def evk_bytes(self) -> int:
         return self.ndig * 2 * (self.nq + self.kp) * self.N * 8

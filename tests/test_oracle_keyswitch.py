@@ -308,3 +308,62 @@ def test_hoisted_rotations_decrypt(logN, nq, kp, dnum, nact):
                                logN, ctx.q[i], ctx.psi_q[i]) for i in range(nact)])
         e = _decrypt_noise(ctx, nact, dg, out0[r], out1[r], s, inputs.galois_secret(s, g))
         assert max(abs(v) for v in e) <= bound, r
+
+
+# ------------------------------------------------------------------ compressed keys
+def test_key_a_word_is_the_splitmix_stream_at_its_counter():
+    """The compressed key's a-words read SplitMix64 at a computed counter:
+    word (j, t, n) is the first draw, masked to bitlen(r), below r among
+    stream outputs ((j*nfull + t)*N + n)*64 + m of seed^2 -- checked against
+    the sequential generator, itself pinned to published outputs."""
+    ctx = orc.Ctx(4, 3, 2, 2, bits=54)
+    N, nfull, seed = ctx.N, 5, 0x5EED
+    primes = ctx.q + ctx.p
+    for (j, t, n) in [(0, 0, 0), (0, 4, 15), (1, 2, 7), (1, 4, 3)]:
+        base = ((j * nfull + t) * N + n) * 64
+        stream = orc.splitmix64(seed ^ 2, base + 64)[base:]
+        mask = (1 << primes[t].bit_length()) - 1
+        want = next(int(v) & mask for v in stream if (int(v) & mask) < primes[t])
+        assert ctx.key_a_word(seed, j, t, n) == want
+
+
+@pytest.mark.parametrize("logN,nq,kp,dnum", [(4, 3, 1, 3), (5, 5, 2, 2)])
+def test_compressed_keygen_relation_and_uniformity(logN, nq, kp, dnum):
+    """A compressed key satisfies the key relation b_j + a_j*s = e_j +
+    [P g_j] s' with one small e_j per digit, and its a-words are uniform
+    residues (mean within 5 sigma of r/2 on every tower)."""
+    ctx = orc.Ctx(logN, nq, kp, dnum, bits=54)
+    N = ctx.N
+    s = inputs.ternary_secret(N, seed=logN + 40)
+    sp = inputs.galois_secret(s, 5)
+    evk = ctx.keygen_compressed(s, sp, seed=77)
+    primes = ctx.q + ctx.p
+    P = prod(ctx.p)
+    s_int, sp_int = [int(v) for v in s], [int(v) for v in sp]
+    for j in range(ctx.ndig):
+        e_ref = None
+        for t, r in enumerate(primes):
+            assert ctx.key_a_word(77, j, t, 3) == int(evk[j, 1, t, 3])
+            psi = (ctx.psi_q + ctx.psi_p)[t]
+            b = orc.intt(evk[j, 0, t], logN, r, psi)
+            a = orc.intt(evk[j, 1, t], logN, r, psi)
+            a_s = negacyclic_schoolbook([int(v) for v in a], s_int)
+            g = P % r if (t < nq and t // ctx.alpha == j) else 0
+            e = [centre(int(bv) + asv - g * spv, r) for bv, asv, spv in zip(b, a_s, sp_int)]
+            assert max(abs(v) for v in e) <= 19
+            e_ref = e if e_ref is None else e_ref
+            assert e == e_ref
+    words = evk[:, 1].astype(np.float64) / np.array(primes, dtype=np.float64)[None, :, None]
+    sd = (1 / 12) ** 0.5 / (ctx.ndig * N) ** 0.5
+    assert np.all(np.abs(words.mean(axis=(0, 2)) - 0.5) < 5 * sd)
+
+
+def test_compressed_key_switch_decrypts():
+    ctx = orc.Ctx(6, 7, 3, 3, bits=54)
+    s = inputs.ternary_secret(ctx.N, seed=81)
+    sp = inputs.galois_secret(s, 5)
+    evk = ctx.keygen_compressed(s, sp, seed=82)
+    d = inputs.uniform_towers(ctx.q, ctx.N, seed=83)
+    out0, out1 = ctx.keyswitch(7, d, evk)
+    e = _decrypt_noise(ctx, 7, d, out0, out1, s, sp)
+    assert max(abs(v) for v in e) <= _noise_bound(ctx, 7)
