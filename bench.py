@@ -378,6 +378,17 @@ def main():
     # ---- 8 rotations of one ciphertext: hoisted (one ModUp) vs 8 separate switches
     hoisted = hoisted_rotations(P, keys[:8], gals[:8], d[0], stream, timed, world, steps=max(3, args.steps // 2))
 
+    # ---- the same 16-ciphertext step with compressed keys (a regenerated on chip)
+    ckeys = [P.keygen_compressed(s, inputs.galois_secret(s, g), seed=inputs.SEED_BASE + 100 + i)
+             for i, g in enumerate(gals)]
+    cjobs = [(ckeys[i], NQ, d[i], o0[i], o1[i]) for i in range(B)]
+    ctuned, _ = P.autotune(cjobs, reps=2, stream=stream)
+    t_c = timed(lambda: P.switch_batch_sched(cjobs, ctuned, stream), args.steps, 2)
+    compressed = {"value": round(world * B * args.steps / (t_c / 1e3), 2), "unit": UNIT,
+                  "key_bytes": ckeys[0].nbytes, "full_key_bytes": keys[0].nbytes,
+                  "schedule": list(ctuned.as_tuple())}
+    del cjobs, ckeys
+
     # ---- the paper's parameter sets (Table III): 4 ciphertexts a step, own keys
     table3 = table3_sets(stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 9)
 
@@ -459,6 +470,7 @@ def main():
             "mixed_batch": mixed,
             "table3_sets": table3,
             "hoisted_rotations": hoisted,
+            "compressed_keys": compressed,
             "schedule": {"tuned": list(tuned.as_tuple()), "fields": "dataflow, oc_variant, chunk, order",
                          "source": "fixed by --schedule" if args.schedule else "ks_autotune",
                          "candidates_ms": [round(x, 3) for x in tune_ms]},

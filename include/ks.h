@@ -104,6 +104,21 @@ int ks_params_info(const ks_params *params, uint64_t *h_q, uint64_t *h_p,
 int ks_keygen_upload(const ks_params *params, const int8_t *h_s, const int64_t *h_s_prime,
                      uint64_t seed, ks_stream_t stream, ks_key **out);
 
+/* Compressed key (Sec. IV-D: regenerating a key's uniform half from a seed
+ * halves the key's data movement).  Same relation and e_j stream as
+ * ks_keygen_upload, but a_j is defined by counter-addressed SplitMix64 so it
+ * can be regenerated anywhere:  a-word (j, t, n) (t the full tower index
+ * q_0..q_L, p_0..p_{K-1}) is the first draw
+ *   SM(seed^2, ((j*(n_q+k_p) + t)*N + n)*64 + m) & mask(bitlen(r_t)),
+ * m = 0..63, below r_t (if all 64 reject, the last one mod r_t), where
+ * SM(x, c) is output c (from 0) of the SplitMix64 stream seeded with x.
+ * Only b_j is stored (half the device memory of a full key); the kernels
+ * regenerate a_j while they form the key product.  A compressed key works
+ * with every entry point; Output-Centric schedules asking for the fused
+ * variant run the split variant for batches that contain one. */
+int ks_keygen_upload_compressed(const ks_params *params, const int8_t *h_s, const int64_t *h_s_prime,
+                                uint64_t seed, ks_stream_t stream, ks_key **out);
+
 /* Upload a key given in the canonical layout
  *   evk[digit j < n_digits][b=0 / a=1][tower q_0..q_L, p_0..p_{K-1}][N]
  * (evaluation form, canonical).  h_evk is host memory. */

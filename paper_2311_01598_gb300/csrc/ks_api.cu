@@ -219,7 +219,7 @@ static int run_mp(const ks_params *P, const ks_key *K, int nact, const u64 *d, u
     LimbMap mD{w->D, w->D, nullptr, nt, nt, 0, 0, nact, 0};
     if ((rc = launch_ntt_fwd(T, one_map(mD, nd * nt), false, st)) != KS_OK) return rc;
     // P4 + P5: key product summed over digits.
-    if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, K->d_evk, w->cp, false, st)) != KS_OK) return rc;
+    if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, key_view(K), w->cp, false, st)) != KS_OK) return rc;
     return run_moddown(P, w, nact, 2, out0, out1, st);
 }
 
@@ -267,7 +267,7 @@ static int run_hoisted(ks_params *P, uint32_t R, const ks_key *const *keys, cons
         const uint32_t g = std::min(G, R - r0);
         u64 *cpr = w->rot, *vr = w->rot + (size_t)G * cp_words;
         for (uint32_t i = 0; i < g; ++i)
-            if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, keys[r0 + i]->d_evk,
+            if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, key_view(keys[r0 + i]),
                                        cpr + i * cp_words, false, st, gal[r0 + i])) != KS_OK)
                 return rc;
         // ModDown of the g rotations: P1 iNTT, P2 BConv, P3 NTT, P4.
@@ -315,7 +315,7 @@ static int run_dc(const ks_params *P, const ks_key *K, int nact, const u64 *d, u
         if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;
         LimbMap mD{w->D, w->D, nullptr, nt, nt, 0, 0, nact, j};
         if ((rc = launch_ntt_fwd(T, one_map(mD, nt), false, st)) != KS_OK) return rc;
-        if ((rc = launch_apply_key(T, nact, j, j + 1, d, w->D, 0, K->d_evk, w->cp, j > 0, st)) != KS_OK) return rc;
+        if ((rc = launch_apply_key(T, nact, j, j + 1, d, w->D, 0, key_view(K), w->cp, j > 0, st)) != KS_OK) return rc;
     }
     return run_moddown(P, w, nact, 2, out0, out1, st);
 }
@@ -329,7 +329,7 @@ static OcJob oc_job(const ks_params *P, const ks_key *K, int nact, const u64 *d,
     J.d = d;
     J.out0 = out0;
     J.out1 = out1;
-    J.evk = K->d_evk;
+    J.key = key_view(K);
     J.y = scratch;
     J.tmp = J.y + (size_t)nact * N;
     J.cp = J.tmp + ((size_t)nd * (nact + P->kp) + 2 * (size_t)nact) * N;
@@ -517,10 +517,42 @@ int64_t gauss(SplitMix &g)
         if (e >= -19 && e <= 19) return e;
     }
 }
+// a-word (j, t, n) of a compressed key: the first SplitMix64 draw of stream
+// seed^2 at counters ((j*nfull + t)*N + n)*64 + m, masked to bitlen(r), that
+// is below r (output c of a stream is reached by starting its state at
+// seed^2 + c*gamma); the same definition the kernels regenerate.
+uint64_t key_a_word_host(uint64_t seed, int j, int t, size_t n, int logN, int nfull, uint64_t r)
+{
+    const int b = 64 - __builtin_clzll(r);
+    const uint64_t mask = b >= 64 ? ~0ull : ((1ull << b) - 1);
+    const uint64_t base = ((((uint64_t)j * nfull + t) << logN) + n) * 64;
+    uint64_t v = 0;
+    for (int m = 0; m < 64; ++m) {
+        SplitMix g{(seed ^ 2) + (base + m) * 0x9E3779B97F4A7C15ULL};
+        v = g.next() & mask;
+        if (v < r) return v;
+    }
+    return v % r;
+}
 }  // namespace
+
+static int keygen_impl(const ks_params *P, const int8_t *h_s, const int64_t *h_s_prime, uint64_t seed,
+                       bool compressed, ks_stream_t stream, ks_key **out);
 
 int ks_keygen_upload(const ks_params *P, const int8_t *h_s, const int64_t *h_s_prime, uint64_t seed,
                      ks_stream_t stream, ks_key **out)
+{
+    return keygen_impl(P, h_s, h_s_prime, seed, false, stream, out);
+}
+
+int ks_keygen_upload_compressed(const ks_params *P, const int8_t *h_s, const int64_t *h_s_prime, uint64_t seed,
+                                ks_stream_t stream, ks_key **out)
+{
+    return keygen_impl(P, h_s, h_s_prime, seed, true, stream, out);
+}
+
+static int keygen_impl(const ks_params *P, const int8_t *h_s, const int64_t *h_s_prime, uint64_t seed,
+                       bool compressed, ks_stream_t stream, ks_key **out)
 {
     int rc = check_params(P);
     if (rc) return rc;
@@ -541,7 +573,10 @@ int ks_keygen_upload(const ks_params *P, const int8_t *h_s, const int64_t *h_s_p
         for (int t = 0; t < nfull; ++t) {
             const u64 r = t < P->nq ? P->q[t] : P->p[t - P->nq];
             u64 *dst = evk_h.data() + (((size_t)j * 2 + 1) * nfull + t) * N;
-            for (size_t n = 0; n < N; ++n) dst[n] = uniform_mod(ga, r);
+            if (compressed)
+                for (size_t n = 0; n < N; ++n) dst[n] = key_a_word_host(seed, j, t, n, P->logN, nfull, r);
+            else
+                for (size_t n = 0; n < N; ++n) dst[n] = uniform_mod(ga, r);
         }
     std::vector<int64_t> vecs((2 + (size_t)P->ndig) * N);
     for (size_t n = 0; n < N; ++n) {
@@ -580,6 +615,26 @@ int ks_keygen_upload(const ks_params *P, const int8_t *h_s, const int64_t *h_s_p
         rc = launch_keygen_combine(P->tables, d_res, d_res + (size_t)nfull * N, d_res + 2 * (size_t)nfull * N, d_pmod,
                                    K->d_evk, st);
     if (rc == KS_OK) rc = launch_key_convert(P->tables, K->d_evk, st);
+    if (rc == KS_OK && compressed) {
+        // keep the b halves only; the a halves are regenerated by the kernels
+        u64 *b_only = nullptr;
+        const size_t half = (size_t)nfull * N;
+        rc = cuda_check(cudaMalloc((void **)&b_only, (size_t)P->ndig * half * 8), "key allocation");
+        for (int j = 0; j < P->ndig && rc == KS_OK; ++j)
+            rc = cuda_check(cudaMemcpyAsync(b_only + (size_t)j * half, K->d_evk + (size_t)2 * j * half, half * 8,
+                                            cudaMemcpyDeviceToDevice, st),
+                            "key compaction");
+        if (rc == KS_OK) rc = cuda_check(cudaStreamSynchronize(st), "keygen sync");
+        if (rc == KS_OK) {
+            cudaFree(K->d_evk);
+            K->d_evk = b_only;
+            K->bytes = (size_t)P->ndig * half * 8;
+            K->compressed = 1;
+            K->a_seed = seed;
+        } else if (b_only) {
+            cudaFree(b_only);
+        }
+    }
     if (rc == KS_OK) rc = cuda_check(cudaStreamSynchronize(st), "keygen sync");
     cudaFree(d_vecs);
     cudaFree(d_res);

@@ -96,6 +96,60 @@ __device__ __forceinline__ u64 redc(U128 T, u64 q, u64 mont)
     u64 m = T.lo * mont;
     return T.hi + __umul64hi(m, q) + (T.lo != 0 ? 1 : 0);
 }
+// Canonical key product of the a half from its 128-bit sum (see key_a).
+template <bool CK>
+__device__ __forceinline__ u64 key_a_finish(const KeyView &K, U128 sa, const ModC &mc, const ulonglong2 *fold, int t)
+{
+    u64 x = redc(sa, mc.q, mc.mont);
+    if (CK && K.comp) x = shoup_lazy(x, fold[t].x, fold[t].y, mc.q);
+    return reduce_any(x, mc.q, mc.one_sh);
+}
+
+// ------------------------------------------------------------------ keys
+// Compressed keys store b_j ([digit][tower][N], stored form) and regenerate
+// a_j (canonical, evaluation form) from a seed.  a-word (j, t, n), t the full
+// tower index, is the first of the draws
+//   v_m = SM(seed ^ 2, ((j*nfull + t)*N + n)*64 + m) & mask(bitlen(r)),
+// m = 0..63, with v_m < r (the last one mod r if all reject, probability
+// below 2^-64), where SM(x, c) is output c (from 0) of the SplitMix64 stream
+// seeded with x (Steele, Lea & Flood 2014): the stream's state after c+1
+// steps is x + (c+1)*0x9E3779B97F4A7C15, so any output is reached directly.
+__device__ __forceinline__ u64 splitmix_out(u64 x, u64 c)
+{
+    u64 z = x + (c + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ u64 key_a_word(u64 seed, int j, int t, size_t n, int logN, int nfull, u64 r)
+{
+    const int b = 64 - __clzll((long long)r);
+    const u64 mask = b >= 64 ? ~0ull : ((1ull << b) - 1);
+    const u64 base = (((((u64)j * (u64)nfull + (u64)t) << logN) + (u64)n) * 64);
+    u64 v = 0;
+    for (int m = 0; m < 64; ++m) {
+        v = splitmix_out(seed ^ 2, base + (u64)m) & mask;
+        if (v < r) return v;
+    }
+    return v % r;
+}
+// Key words of digit j, full tower t, slot n.  Full keys hold both halves
+// times the tower's fold factor and 2^64; a compressed key's a-word is
+// canonical, so its sum of products is multiplied by that factor once per
+// output (key_a_finish).
+// CK: the launch may contain compressed keys (otherwise every key is full
+// and the regeneration code is left out of the kernel).
+template <bool CK>
+__device__ __forceinline__ u64 key_b(const KeyView &K, int j, int t, size_t n, int nfull, int logN)
+{
+    return K.evk[(((size_t)((CK && K.comp) ? j : 2 * j) * nfull + t) << logN) + n];
+}
+template <bool CK>
+__device__ __forceinline__ u64 key_a(const KeyView &K, int j, int t, size_t n, int nfull, int logN, u64 r)
+{
+    if (CK && K.comp) return key_a_word(K.a_seed, j, t, n, logN, nfull, r);
+    return K.evk[(((size_t)(2 * j + 1) * nfull + t) << logN) + n];
+}
 
 // Base-conversion accumulator: sum of y*c with y, c < 2^56 split at 28 bits.
 struct BAcc {

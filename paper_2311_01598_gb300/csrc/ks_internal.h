@@ -52,6 +52,14 @@ struct ModC {
 };
 
 // Device tables of one parameter set, passed to kernels by value.
+// A key as the kernels read it: a full key, or a compressed one (b stored,
+// a regenerated from a_seed; see key_a_word in ks_device.cuh).
+struct KeyView {
+    const u64 *evk;
+    u64 a_seed;
+    int comp;
+};
+
 struct Tables {
     const ModC *modc;
     const ulonglong2 *tw;
@@ -108,9 +116,17 @@ struct ks_params {
 
 struct ks_key {
     const ks_params *params = nullptr;
-    uint64_t *d_evk = nullptr;  // [ndig][2][nq+kp][N], Montgomery form with key_sc folded in
+    // full key: [ndig][2][nq+kp][N]; compressed: [ndig][nq+kp][N] (b only);
+    // Montgomery form with key_sc folded in
+    uint64_t *d_evk = nullptr;
     size_t bytes = 0;
+    int compressed = 0;
+    uint64_t a_seed = 0;  // compressed: seed of the regenerated a half
 };
+
+namespace ks {
+inline KeyView key_view(const ks_key *K) { return KeyView{K->d_evk, K->a_seed, K->compressed}; }
+}  // namespace ks
 
 namespace ks {
 

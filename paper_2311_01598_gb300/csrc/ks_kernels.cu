@@ -468,8 +468,9 @@ __device__ __forceinline__ size_t galois_slot(size_t n, u64 g, int logN)
     return (size_t)(__brev((unsigned)((e - 1) >> 1)) >> (32 - logN));
 }
 
+template <bool CK>
 __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, int j1, const u64 *d, const u64 *D,
-                                                   size_t dstride, const u64 *evk, u64 *cp, int accumulate, u64 galois)
+                                                   size_t dstride, KeyView key, u64 *cp, int accumulate, u64 galois)
 {
     const int t = blockIdx.y;
     const int nt = nact + T.kp;
@@ -483,14 +484,12 @@ __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, i
     for (int j = j0; j < j1; ++j) {
         const bool own = t < nact && t / T.alpha == j;
         const u64 dv = own ? d[(size_t)t * N + ns] : D[(size_t)(j - j0) * dstride + (size_t)t * N + ns];
-        const u64 kb = evk[(((size_t)j * 2 + 0) * nfull + tf) * N + n];
-        const u64 ka = evk[(((size_t)j * 2 + 1) * nfull + tf) * N + n];
-        mac128(sb, dv, kb);
-        mac128(sa, dv, ka);
+        mac128(sb, dv, key_b<CK>(key, j, tf, n, nfull, T.logN));
+        mac128(sa, dv, key_a<CK>(key, j, tf, n, nfull, T.logN, mc.q));
     }
     // D below 40q: the REDC result is below q + 40*nd*q^2/2^64, reduced fully.
     u64 rb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    u64 ra = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+    u64 ra = key_a_finish<CK>(key, sa, mc, T.key_sc, tf);
     u64 *cb = cp + (size_t)t * N + n;
     u64 *ca = cp + ((size_t)nt + t) * N + n;
     if (accumulate) {
@@ -502,13 +501,19 @@ __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, i
 }
 
 int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u64 *d, const u64 *D,
-                     size_t D_digit_stride, const u64 *evk, u64 *cp, bool accumulate, cudaStream_t st, uint64_t galois)
+                     size_t D_digit_stride, const KeyView &key, u64 *cp, bool accumulate, cudaStream_t st,
+                     uint64_t galois)
 {
     const size_t N = (size_t)1 << T.logN;
     dim3 g((unsigned)(N / 256), (unsigned)(nact + T.kp));
-    KS_LAUNCH(st, "apply_key",
-              k_apply_key<<<g, 256, 0, st>>>(T, nact, j_begin, j_end, d, D, D_digit_stride, evk, cp, accumulate ? 1 : 0,
-                                             galois));
+    if (key.comp)
+        KS_LAUNCH(st, "apply_key",
+                  k_apply_key<true><<<g, 256, 0, st>>>(T, nact, j_begin, j_end, d, D, D_digit_stride, key, cp,
+                                                       accumulate ? 1 : 0, galois));
+    else
+        KS_LAUNCH(st, "apply_key",
+                  k_apply_key<false><<<g, 256, 0, st>>>(T, nact, j_begin, j_end, d, D, D_digit_stride, key, cp,
+                                                        accumulate ? 1 : 0, galois));
     return launch_status("apply-key launch");
 }
 

@@ -108,7 +108,7 @@ int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st);
 // inside digit j; D holds lazy NTT output.  accumulate: add to cp.  galois
 // g != 1: every D_{j,t} (and d_t) is read through X -> X^g (hoisted rotation).
 int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u64 *d, const u64 *D,
-                     size_t D_digit_stride, const u64 *evk, u64 *cp, bool accumulate, cudaStream_t st,
+                     size_t D_digit_stride, const KeyView &key, u64 *cp, bool accumulate, cudaStream_t st,
                      uint64_t galois = 1);
 // ModDown P4 (single job; P^-1 folded): out_x[i] = cp[x][i] - v[x][i] mod q_i,
 // v lazy NTT output.
@@ -132,7 +132,7 @@ int launch_signed_to_towers(const Tables &T, const int64_t *v, int nvec, u64 *ou
 struct OcJob {
     const u64 *d;
     u64 *out0, *out1;
-    const u64 *evk;
+    KeyView key;  // the fused variant reads full keys only (launch_oc)
     u64 *y;    // [nact][N]
     u64 *tmp;  // [nd*(nact+K) + 2*nact][N]
     u64 *cp;   // [2][nact+K][N]

@@ -94,7 +94,7 @@ extern "C" int ks_switch_noalloc(const ks_params *P, const ks_key *K, uint32_t l
     J.d = d_in;
     J.out0 = d_out0;
     J.out1 = d_out1;
-    J.evk = K->d_evk;
+    J.key = key_view(K);
     J.y = base;
     J.tmp = J.y + (size_t)nact * N;
     J.cp = J.tmp + ((size_t)nd * (nact + P->kp) + 2 * (size_t)nact) * N;

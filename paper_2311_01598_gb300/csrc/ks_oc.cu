@@ -130,15 +130,15 @@ __global__ void __launch_bounds__(S::THREADS_B) k_oc_rowP(Tables T, OcJobs oj)
     constexpr uint32_t BLK = S::ROWS * (1 << S::LB) * 8;
     auto prefetch_digit = [&](int j) {
         prefetch_l2(J.tmp + ((size_t)(j * K + k) << S::LOGN) + brow, BLK);
-        prefetch_l2(J.evk + ((size_t)((j * 2 + 0) * nfull + tf) << S::LOGN) + brow, BLK);
-        prefetch_l2(J.evk + ((size_t)((j * 2 + 1) * nfull + tf) << S::LOGN) + brow, BLK);
+        prefetch_l2(J.key.evk + ((size_t)((j * 2 + 0) * nfull + tf) << S::LOGN) + brow, BLK);
+        prefetch_l2(J.key.evk + ((size_t)((j * 2 + 1) * nfull + tf) << S::LOGN) + brow, BLK);
     };
     if (threadIdx.x == 0) prefetch_digit(0);
     for (int j = 0; j < J.nd; ++j) {
         if (threadIdx.x == 0 && j + 1 < J.nd) prefetch_digit(j + 1);
         oc_digit<S>(J.tmp + ((size_t)(j * K + k) << S::LOGN) + rowoff, 1, twt, G, srow, tau,
-                    J.evk + ((size_t)((j * 2 + 0) * nfull + tf) << S::LOGN) + rowoff,
-                    J.evk + ((size_t)((j * 2 + 1) * nfull + tf) << S::LOGN) + rowoff, ab, aa, j == 0, mc.q, mc.mont);
+                    J.key.evk + ((size_t)((j * 2 + 0) * nfull + tf) << S::LOGN) + rowoff,
+                    J.key.evk + ((size_t)((j * 2 + 1) * nfull + tf) << S::LOGN) + rowoff, ab, aa, j == 0, mc.q, mc.mont);
     }
     const ulonglong2 *itwt = T.itw + ((size_t)tf << S::LOGN);
     oc_inv_store<S>(ab, itwt, G, srow, tau, J.cp + ((size_t)t << S::LOGN) + rowoff, mc.q);
@@ -174,8 +174,8 @@ __global__ void __launch_bounds__(S::THREADS_B) k_oc_rowQ(Tables T, OcJobs oj)
     auto prefetch_digit = [&](int j) {
         const u64 *src = j == j0 ? J.d + ((size_t)t << S::LOGN) : J.tmp + ((size_t)(j * nact + t) << S::LOGN);
         prefetch_l2(src + brow, BLK);
-        prefetch_l2(J.evk + ((size_t)((j * 2 + 0) * nfull + t) << S::LOGN) + brow, BLK);
-        prefetch_l2(J.evk + ((size_t)((j * 2 + 1) * nfull + t) << S::LOGN) + brow, BLK);
+        prefetch_l2(J.key.evk + ((size_t)((j * 2 + 0) * nfull + t) << S::LOGN) + brow, BLK);
+        prefetch_l2(J.key.evk + ((size_t)((j * 2 + 1) * nfull + t) << S::LOGN) + brow, BLK);
     };
     if (threadIdx.x == 0) prefetch_digit(0);
     for (int j = 0; j < J.nd; ++j) {
@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(S::THREADS_B) k_oc_rowQ(Tables T, OcJobs oj)
         }
         const u64 *gin = j == j0 ? J.d + ((size_t)t << S::LOGN) + rowoff
                                  : J.tmp + ((size_t)(j * nact + t) << S::LOGN) + rowoff;
-        oc_digit<S>(gin, j != j0, twt, G, srow, tau, J.evk + ((size_t)((j * 2 + 0) * nfull + t) << S::LOGN) + rowoff,
-                    J.evk + ((size_t)((j * 2 + 1) * nfull + t) << S::LOGN) + rowoff, ab, aa, j == 0, mc.q, mc.mont);
+        oc_digit<S>(gin, j != j0, twt, G, srow, tau, J.key.evk + ((size_t)((j * 2 + 0) * nfull + t) << S::LOGN) + rowoff,
+                    J.key.evk + ((size_t)((j * 2 + 1) * nfull + t) << S::LOGN) + rowoff, ab, aa, j == 0, mc.q, mc.mont);
     }
     for (int xp = 0; xp < 2; ++xp)
         oc_down_store<S>(J.tmp + ((size_t)((J.nd + xp) * nact + t) << S::LOGN) + rowoff, twt, G, srow, tau,
@@ -241,8 +241,16 @@ static int oc_rows(const Tables &T, const OcJobs &oj, bool p_section, cudaStream
 // resident warps per SM than the fused row kernels, at the price of one more
 // round trip of the section's limbs through L2/HBM.
 
+static bool any_compressed(const OcJobs &oj)
+{
+    for (int i = 0; i < oj.n; ++i)
+        if (oj.job[i].key.comp) return true;
+    return false;
+}
+
 // P section combine: c'_{x,p_k} = sum_j NTT(z_{j,p_k}) * evk_{j,x,p_k} for
 // every coefficient, written canonical to cp.  grid (N/256, jobs*K).
+template <bool CK>
 __global__ void __launch_bounds__(256) k_oc_comb_p(Tables T, OcJobs oj)
 {
     const int K = T.kp;
@@ -258,16 +266,17 @@ __global__ void __launch_bounds__(256) k_oc_comb_p(Tables T, OcJobs oj)
     U128 sb = {0, 0}, sa = {0, 0};
     for (int j = 0; j < J.nd; ++j) {
         const u64 x = J.tmp[(size_t)(j * K + k) * N + n];
-        mac128(sb, x, J.evk[((size_t)(j * 2 + 0) * nfull + tf) * N + n]);
-        mac128(sa, x, J.evk[((size_t)(j * 2 + 1) * nfull + tf) * N + n]);
+        mac128(sb, x, key_b<CK>(J.key, j, tf, n, nfull, T.logN));
+        mac128(sa, x, key_a<CK>(J.key, j, tf, n, nfull, T.logN, mc.q));
     }
     J.cp[(size_t)t * N + n] = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    J.cp[(size_t)(nt + t) * N + n] = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+    J.cp[(size_t)(nt + t) * N + n] = key_a_finish<CK>(J.key, sa, mc, T.key_sc, tf);
 }
 
 // Q section combine: out_x = sum_j D_j * evk_{j,x} - NTT(v_x), D_j the
 // transformed ModUp limb or the input tower for the own digit.
 // grid (N/256, sum of nact over jobs).
+template <bool CK>
 __global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
 {
     const int jb = find_slot(oj.pre, oj.n, blockIdx.y);
@@ -282,12 +291,12 @@ __global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
     U128 sb = {0, 0}, sa = {0, 0};
     for (int j = 0; j < J.nd; ++j) {
         const u64 x = j == j0 ? J.d[(size_t)t * N + n] : J.tmp[(size_t)(j * nact + t) * N + n];
-        mac128(sb, x, J.evk[((size_t)(j * 2 + 0) * nfull + t) * N + n]);
-        mac128(sa, x, J.evk[((size_t)(j * 2 + 1) * nfull + t) * N + n]);
+        mac128(sb, x, key_b<CK>(J.key, j, t, n, nfull, T.logN));
+        mac128(sa, x, key_a<CK>(J.key, j, t, n, nfull, T.logN, mc.q));
     }
     const u64 q40 = 40 * mc.q;
     const u64 cb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    const u64 ca = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+    const u64 ca = key_a_finish<CK>(J.key, sa, mc, T.key_sc, t);
     const u64 vb = J.tmp[(size_t)(J.nd * nact + t) * N + n];
     const u64 va = J.tmp[(size_t)((J.nd + 1) * nact + t) * N + n];
     J.out0[(size_t)t * N + n] = reduce_any(cb + q40 - vb, mc.q, mc.one_sh);
@@ -297,10 +306,18 @@ __global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
 static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
-    if (p_section)
-        KS_LAUNCH(st, "oc_comb_p", k_oc_comb_p<<<dim3((unsigned)(N / 256), oj.n * T.kp), 256, 0, st>>>(T, oj));
-    else
-        KS_LAUNCH(st, "oc_comb_q", k_oc_comb_q<<<dim3((unsigned)(N / 256), oj.pre[oj.n]), 256, 0, st>>>(T, oj));
+    const dim3 gp((unsigned)(N / 256), oj.n * T.kp), gq((unsigned)(N / 256), oj.pre[oj.n]);
+    if (p_section) {
+        if (any_compressed(oj))
+            KS_LAUNCH(st, "oc_comb_p", k_oc_comb_p<true><<<gp, 256, 0, st>>>(T, oj));
+        else
+            KS_LAUNCH(st, "oc_comb_p", k_oc_comb_p<false><<<gp, 256, 0, st>>>(T, oj));
+    } else {
+        if (any_compressed(oj))
+            KS_LAUNCH(st, "oc_comb_q", k_oc_comb_q<true><<<gq, 256, 0, st>>>(T, oj));
+        else
+            KS_LAUNCH(st, "oc_comb_q", k_oc_comb_q<false><<<gq, 256, 0, st>>>(T, oj));
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(KS_ECUDA, std::string("OC combine launch: ") + cudaGetErrorString(e));
     return KS_OK;
@@ -316,6 +333,7 @@ size_t oc_scratch_words(const Tables &T, int nact)
 
 // Whole-basis variant: tmp holds D [nd][nact+K] then v [2][nact].
 // P-tower combine of this layout: c'_{x,p_k} from D rows at tower nact+k.
+template <bool CK>
 __global__ void __launch_bounds__(256) k_oc_comb_pw(Tables T, OcJobs oj)
 {
     const int K = T.kp;
@@ -331,14 +349,15 @@ __global__ void __launch_bounds__(256) k_oc_comb_pw(Tables T, OcJobs oj)
     U128 sb = {0, 0}, sa = {0, 0};
     for (int j = 0; j < J.nd; ++j) {
         const u64 x = J.tmp[((size_t)j * nt + t) * N + n];
-        mac128(sb, x, J.evk[((size_t)(j * 2 + 0) * nfull + tf) * N + n]);
-        mac128(sa, x, J.evk[((size_t)(j * 2 + 1) * nfull + tf) * N + n]);
+        mac128(sb, x, key_b<CK>(J.key, j, tf, n, nfull, T.logN));
+        mac128(sa, x, key_a<CK>(J.key, j, tf, n, nfull, T.logN, mc.q));
     }
     J.cp[(size_t)t * N + n] = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    J.cp[(size_t)(nt + t) * N + n] = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+    J.cp[(size_t)(nt + t) * N + n] = key_a_finish<CK>(J.key, sa, mc, T.key_sc, tf);
 }
 
 // Q-tower combine of the whole-basis layout.  grid (N/256, sum of nact).
+template <bool CK>
 __global__ void __launch_bounds__(256) k_oc_comb_qw(Tables T, OcJobs oj)
 {
     const int jb = find_slot(oj.pre, oj.n, blockIdx.y);
@@ -354,13 +373,13 @@ __global__ void __launch_bounds__(256) k_oc_comb_qw(Tables T, OcJobs oj)
     U128 sb = {0, 0}, sa = {0, 0};
     for (int j = 0; j < J.nd; ++j) {
         const u64 x = j == j0 ? J.d[(size_t)t * N + n] : J.tmp[((size_t)j * nt + t) * N + n];
-        mac128(sb, x, J.evk[((size_t)(j * 2 + 0) * nfull + t) * N + n]);
-        mac128(sa, x, J.evk[((size_t)(j * 2 + 1) * nfull + t) * N + n]);
+        mac128(sb, x, key_b<CK>(J.key, j, t, n, nfull, T.logN));
+        mac128(sa, x, key_a<CK>(J.key, j, t, n, nfull, T.logN, mc.q));
     }
     const u64 *v = J.tmp + (size_t)J.nd * nt * N;
     const u64 q40 = 40 * mc.q;
     const u64 cb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    const u64 ca = reduce_any(redc(sa, mc.q, mc.mont), mc.q, mc.one_sh);
+    const u64 ca = key_a_finish<CK>(J.key, sa, mc, T.key_sc, t);
     J.out0[(size_t)t * N + n] = reduce_any(cb + q40 - v[(size_t)t * N + n], mc.q, mc.one_sh);
     J.out1[(size_t)t * N + n] = reduce_any(ca + q40 - v[(size_t)(nact + t) * N + n], mc.q, mc.one_sh);
 }
@@ -395,11 +414,19 @@ static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream
     if ((rc = launch_ntt_inv(T, m1, false, st)) != KS_OK) return rc;   // ModUp P1
     if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;          // P2, every tower
     if ((rc = launch_ntt_fwd(T, mD, false, st)) != KS_OK) return rc;    // P3
-    KS_LAUNCH(st, "oc_comb_p", k_oc_comb_pw<<<dim3((unsigned)(N / 256), n * K), 256, 0, st>>>(T, oj));  // P4+P5, P towers
+    const bool ck = any_compressed(oj);
+    const dim3 gp((unsigned)(N / 256), n * K), gq((unsigned)(N / 256), oj.pre[n]);
+    if (ck)  // P4+P5, P towers
+        KS_LAUNCH(st, "oc_comb_p", k_oc_comb_pw<true><<<gp, 256, 0, st>>>(T, oj));
+    else
+        KS_LAUNCH(st, "oc_comb_p", k_oc_comb_pw<false><<<gp, 256, 0, st>>>(T, oj));
     if ((rc = launch_ntt_inv(T, mw, false, st)) != KS_OK) return rc;    // ModDown P1
     if ((rc = launch_bconv_down(T, bd, st)) != KS_OK) return rc;        // ModDown P2
     if ((rc = launch_ntt_fwd(T, mv, false, st)) != KS_OK) return rc;    // ModDown P3
-    KS_LAUNCH(st, "oc_comb_q", k_oc_comb_qw<<<dim3((unsigned)(N / 256), oj.pre[n]), 256, 0, st>>>(T, oj));  // P4+P5 Q, ModDown P4
+    if (ck)  // P4+P5 Q, ModDown P4
+        KS_LAUNCH(st, "oc_comb_q", k_oc_comb_qw<true><<<gq, 256, 0, st>>>(T, oj));
+    else
+        KS_LAUNCH(st, "oc_comb_q", k_oc_comb_qw<false><<<gq, 256, 0, st>>>(T, oj));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(KS_ECUDA, std::string("OC whole-basis launch: ") + cudaGetErrorString(e));
     return KS_OK;
@@ -473,6 +500,14 @@ static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int varian
 
 int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st)
 {
+    // The fused row kernels read the key's a half from memory: batches with
+    // a compressed key run the split variant instead.
+    if (variant == KS_OC_FUSED)
+        for (int i = 0; i < njobs; ++i)
+            if (jobs[i].key.comp) {
+                variant = KS_OC_SPLIT;
+                break;
+            }
     for (int i0 = 0; i0 < njobs; i0 += kMaxBatch) {
         int rc = launch_oc_chunk(T, std::min(kMaxBatch, njobs - i0), jobs + i0, variant, st);
         if (rc != KS_OK) return rc;

@@ -174,7 +174,7 @@ static void scheduler(ks_server *S)
                 J.d = r.d;
                 J.out0 = r.o0;
                 J.out1 = r.o1;
-                J.evk = r.K->d_evk;
+                J.key = key_view(r.K);
                 J.y = (u64 *)(S->pool_mem + r.off);
                 J.tmp = J.y + (size_t)nact * P0->N;
                 J.cp = J.tmp + ((size_t)nd * (nact + P0->kp) + 2 * (size_t)nact) * P0->N;

@@ -84,6 +84,7 @@ def lib():
         L.ks_params_destroy.restype = None
         L.ks_params_info.argtypes = [vp, vp, vp, ctypes.POINTER(u32), ctypes.POINTER(u32)]
         L.ks_keygen_upload.argtypes = [vp, vp, vp, u64, vp, pvp]
+        L.ks_keygen_upload_compressed.argtypes = [vp, vp, vp, u64, vp, pvp]
         L.ks_key_upload_raw.argtypes = [vp, vp, vp, pvp]
         L.ks_key_destroy.argtypes = [vp]
         L.ks_key_destroy.restype = None
@@ -152,7 +153,8 @@ def lib():
         L.ks_profile_enable.restype = None
         L.ks_profile_collect.argtypes = [u32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                          ctypes.POINTER(u32), ctypes.POINTER(u32)]
-        for name in ("ks_params_create", "ks_params_info", "ks_keygen_upload", "ks_key_upload_raw", "ks_switch",
+        for name in ("ks_params_create", "ks_params_info", "ks_keygen_upload", "ks_keygen_upload_compressed",
+                     "ks_key_upload_raw", "ks_switch",
                      "ks_switch_batch", "ks_ntt", "ks_modup", "ks_moddown", "ks_switch_batch_host",
                      "ks_profile_collect"):
             getattr(L, name).restype = ci
@@ -256,6 +258,16 @@ class Params:
         h = ctypes.c_void_p()
         check(lib().ks_keygen_upload(self.handle, _ptr(s), _ptr(sp), seed & (2**64 - 1), _stream_handle(stream),
                                      ctypes.byref(h)))
+        return Key(self, h.value)
+
+    def keygen_compressed(self, s, s_prime, seed: int, stream=None) -> Key:
+        """ks_keygen_upload_compressed: b_j stored, a_j regenerated by the
+        kernels from the seed (half the key's device memory and traffic)."""
+        s = np.ascontiguousarray(s, dtype=np.int8)
+        sp = np.ascontiguousarray(s_prime, dtype=np.int64)
+        h = ctypes.c_void_p()
+        check(lib().ks_keygen_upload_compressed(self.handle, _ptr(s), _ptr(sp), seed & (2**64 - 1),
+                                                _stream_handle(stream), ctypes.byref(h)))
         return Key(self, h.value)
 
     def upload_key(self, evk: np.ndarray, stream=None) -> Key:
