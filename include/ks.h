@@ -142,7 +142,7 @@ int ks_switch(const ks_params *params, const ks_key *key, uint32_t level_towers,
               const uint64_t *d_in, uint64_t *d_out0, uint64_t *d_out1, ks_dataflow dataflow,
               ks_stream_t stream);
 
-/* Hoisted rotations (Sec. II-B: a rotation is the key switch of a Galois
+/* Hoisted rotations (Sec. II: a rotation needs the key switch of a Galois
  * automorphism X -> X^g; hoisting shares one ModUp among several).
  * For r < n_rot, with g_r = galois[r] (odd, < 2N) and keys[r] a key from
  * s(X^g_r) to s:

@@ -493,7 +493,7 @@ void orc_keyswitch(const orc_ctx *c, int nact, const u64 *d, const u64 *evk, u64
 }
 
 /* ------------------------------------------------------------------ */
-/* Rotations with hoisting (Sec. II-B names rotations as the key switches */
+/* Rotations with hoisting (Sec. II: a rotation needs the key switch of a  */
 /* of Galois automorphisms; hoisting shares one ModUp among them).      */
 /* ------------------------------------------------------------------ */
 
