@@ -493,8 +493,8 @@ void orc_keyswitch(const orc_ctx *c, int nact, const u64 *d, const u64 *evk, u64
 }
 
 /* ------------------------------------------------------------------ */
-/* Rotations with hoisting (Sec. II: a rotation needs the key switch of a  */
-/* of Galois automorphisms; hoisting shares one ModUp among them).      */
+/* Rotations with hoisting (Sec. II: every rotation needs the key switch */
+/* of a Galois automorphism; hoisting shares one ModUp among them).     */
 /* ------------------------------------------------------------------ */
 
 /* X -> X^g on an evaluation-form tower.  Slot k holds a(psi^e_k) with
