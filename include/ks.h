@@ -92,6 +92,22 @@ void ks_params_destroy(ks_params *params);
 int ks_params_info(const ks_params *params, uint64_t *h_q, uint64_t *h_p,
                    uint32_t *alpha, uint32_t *n_digits);
 
+/* Implementation options of a parameter set (none changes any result).
+ *   KS_OPT_BCONV_TENSOR (default 1): run the fast base conversions (ModUp P2,
+ *     ModDown P2) on the tensor cores (tcgen05, exact bf16 byte slices)
+ *     wherever at most 9 source towers meet N >= 2^9; 0 selects the CUDA-core
+ *     kernels everywhere.
+ * Returns KS_EINVAL for an unknown option or value.  Not thread-safe with
+ * concurrent calls on the same params object. */
+enum { KS_OPT_BCONV_TENSOR = 1 };
+int ks_params_set_option(ks_params *params, int option, int value);
+
+/* Device-side status of the library on the params object's GPU: bit 0 is set
+ * when a tensor-core kernel gave up waiting for its MMAs (bounded wait) since
+ * the last call with clear = 1; its outputs are then not valid.  Returns
+ * KS_OK, or KS_ECUDA if the flag cannot be read. */
+int ks_device_status(const ks_params *params, int clear, uint32_t *flags);
+
 /* Generate and upload an evaluation key switching s' -> s (hybrid key):
  *   b_j = -a_j*s + e_j + [P*g_j]*s',  a_j uniform, e_j rounded Gaussian
  *   (sigma 3.2, |e| <= 19), g_j the CRT idempotent of digit j.

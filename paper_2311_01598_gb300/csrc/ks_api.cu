@@ -692,6 +692,30 @@ int ks_switch(const ks_params *P, const ks_key *K, uint32_t level_towers, const 
                       (cudaStream_t)stream);
 }
 
+int ks_params_set_option(ks_params *P, int option, int value)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (option != KS_OPT_BCONV_TENSOR || (value != 0 && value != 1)) return fail(KS_EINVAL, "unknown option or value");
+    std::lock_guard<std::mutex> g(P->mu);
+    P->bconv_tensor = value;
+    P->tables.up_tc = value ? P->d_up_tc : nullptr;
+    P->tables.dn_tc = value ? P->d_dn_tc : nullptr;
+    return KS_OK;
+}
+
+int ks_device_status(const ks_params *P, int clear, uint32_t *flags)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (!flags) return fail(KS_EINVAL, "flags is NULL");
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    const int v = tc_error_flag(clear != 0);
+    if (v < 0) return fail(KS_ECUDA, "device status unreadable");
+    *flags = v ? 1u : 0u;
+    return KS_OK;
+}
+
 int ks_switch_hoisted(const ks_params *P, uint32_t n_rot, const ks_key *const *keys, const uint64_t *galois,
                       uint32_t level_towers, const uint64_t *d_in, uint64_t *const *d_out0, uint64_t *const *d_out1,
                       ks_stream_t stream)

@@ -1,0 +1,536 @@
+// ks_bconv_tc.cu -- fast base conversion (ModUp P2, ModDown P2) on the
+// 5th-generation tensor cores (tcgen05, accumulators in tensor memory).
+//
+// The conversion z_t = sum_i y_i c_{i,t} is a product of a [coefficients x
+// sources] matrix by a [sources x targets] matrix of constants below 2^56.
+// Exactness with f16 operands: y_i (canonical, < 2^56) is cut into 7 bytes
+// y_{i,a} and each constant into 7 bytes c_{i,t,b}; then
+//   sum_i y_i c_{i,t} = sum_{s=0}^{12} 2^(8s) P_{t,s},
+//   P_{t,s} = sum_i sum_{a+b=s} y_{i,a} c_{i,t,b},
+// and every P_{t,s} (at most 9 sources x 7 byte pairs x 255^2 < 2^22) is an
+// exact integer in the fp32 accumulator.  One MMA of M=128 coefficients,
+// K = 7*(sources) padded to 64, N = 16 per target (13 shifts used) computes
+// all P_{t,s} of 16 targets: the A tile holds the byte slices of y (built by
+// the CTA from the source limbs), the B tile the per-target slabs
+// B[s][7i+a] = c_{i,t,s-a} (precomputed on the host, 2 KB each).  The
+// epilogue reads P_{t,s} from tensor memory, recombines the 128-bit sum and
+// reduces it with one Montgomery reduction (constants carry 2^64), giving the
+// same lazy [0, 2r) output as the CUDA-core kernels.
+//
+// Operand layout: the canonical K-major layout without swizzle: 8x16-byte
+// core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row
+// groups 1024 bytes apart (SBO); B slabs of 16 rows concatenate.
+#include <cstdio>
+
+#include "ks_device.cuh"
+#include "ks_launch.h"
+
+namespace ks {
+
+namespace {
+
+constexpr int TC_M = 128;            // coefficients per MMA tile
+constexpr int TC_K = 64;             // padded K (7 x up to 9 sources)
+constexpr int TC_TB = 16;            // targets per CTA
+constexpr uint32_t TC_LBO = 128;
+constexpr uint32_t TC_SBO = (TC_K / 8) * 128;
+constexpr int TC_SLAB = 16 * TC_K * 2;  // bytes of one target slab
+constexpr int TC_WAIT_LIMIT = 1 << 24;  // mbarrier polls before giving up
+
+__device__ int g_tc_error;  // set when an MMA completion wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of this architecture; no swizzle
+    return d;
+}
+// kind::f16 instruction descriptor: D f32, A and B f16, both K-major.
+__device__ __forceinline__ uint32_t tc_idesc(int n)
+{
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+__host__ __device__ __forceinline__ uint32_t tc_off(int r, int k)
+{
+    return (uint32_t)((r / 8) * TC_SBO + (k / 8) * TC_LBO + (r % 8) * 16 + (k % 8) * 2);
+}
+// Two bytes as an exact f16 pair: byte a0 of word x (low half) and byte a1 of
+// word y (high half).  0x6400 | b is the f16 of 1024 + b (b < 1024), so one
+// byte permute, one logic op and one packed subtraction of 1024 give (b0, b1).
+// The selector is a constant once the callers' loops are unrolled.
+__device__ __forceinline__ uint32_t f16x2_bytes(uint32_t x, uint32_t y, uint32_t a0, uint32_t a1)
+{
+    const uint32_t sel = a0 | ((4u + a1) << 8);  // x.byte[a0] -> byte 0, y.byte[a1] -> byte 2
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(x), "r"(y), "r"(sel));
+    d = (d & 0x00FF00FFu) | 0x64006400u;
+    uint32_t r;
+    asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(d), "r"(0x64006400u));
+    return r;
+}
+
+// 128-bit sum of the 13 shifted partial sums of one target, Montgomery-reduced.
+// v[s] are the raw accumulator bits 0x4B000000 + P_s (bias column); the bias
+// is removed once per 64-bit group.
+__device__ __forceinline__ u64 tc_reduce(const uint32_t (&v)[16], u64 q, u64 mont)
+{
+    constexpr u64 B = 0x4B000000ull;
+    u64 a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) a0 += (u64)v[s] << (8 * s);
+#pragma unroll
+    for (int s = 5; s < 10; ++s) a1 += (u64)v[s] << (8 * (s - 5));
+#pragma unroll
+    for (int s = 10; s < 13; ++s) a2 += (u64)v[s] << (8 * (s - 10));
+    a0 -= B * 0x0101010101ull;  // B * (1 + 2^8 + ... + 2^32)
+    a1 -= B * 0x0101010101ull;
+    a2 -= B * 0x010101ull;
+    // S = a0 + a1*2^40 + a2*2^80
+    const u64 t1 = a1 << 40;
+    const u64 lo = a0 + t1;
+    const u64 hi = (a1 >> 24) + (a2 << 16) + (lo < t1 ? 1 : 0);
+    return redc(U128{lo, hi}, q, mont);
+}
+
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+    return done != 0;
+}
+
+// One unit of work: a tile of 128 coefficients for one block of <= 16
+// targets of one (job, digit) (ModUp) or (job, polynomial) (ModDown).
+struct TcItem {
+    const u64 *src;     // source tower 0 at the tile's first coefficient; tower i at + i*N
+    int nsrc;           // source towers (<= 9)
+    int G;              // targets (0: nothing to do)
+    int key;            // (job block, target block): the B slabs and targets change with it
+    int sbase;          // slab index base (ModUp: of the digit at this level)
+    int t_first, ov_at, ov, nact, t_base;  // target numbering (ModUp)
+    u64 *dst0;          // output base: target t at dst0 + (t - t_base)*N
+};
+
+template <int MODE>
+__device__ __forceinline__ TcItem tc_item(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int item, int XT,
+                                          int TBN)
+{
+    const size_t N = (size_t)1 << T.logN;
+    const int xt = item % XT, r = item / XT, tb = r % TBN, z = r / TBN;
+    TcItem it;
+    it.key = r;
+    if (MODE == 0) {
+        const int jb = find_slot(bu.zpre, bu.n, z);
+        const BUpJob &J = bu.job[jb];
+        const int j = J.jsel >= 0 ? J.jsel : z - bu.zpre[jb];
+        const int lo = j * T.alpha, hi = min(lo + T.alpha, J.nact);
+        const int olo = max(lo, J.t_begin), ohi = min(hi, J.t_end);
+        it.ov = ohi > olo ? ohi - olo : 0;
+        it.ov_at = olo;
+        const int nb = (J.t_end - J.t_begin) - it.ov;
+        const int u0 = tb * TC_TB;
+        it.G = max(0, min(TC_TB, nb - u0));
+        it.t_first = J.t_begin + u0;
+        it.nact = J.nact;
+        it.t_base = J.t_base;
+        it.nsrc = hi - lo;
+        it.src = J.y + (size_t)lo * N + (size_t)xt * TC_M;
+        it.sbase = T.up_tc_lvl[(size_t)(J.nact - 1) * T.ndig + j];
+        it.dst0 = J.D + (size_t)(J.jsel >= 0 ? 0 : j) * J.dstride + (size_t)xt * TC_M;
+    } else {
+        const int jb = find_slot(bd.zpre, bd.n, z);
+        const BDnJob &J = bd.job[jb];
+        const int x = z - bd.zpre[jb];
+        const int i0 = tb * TC_TB;
+        it.G = max(0, min(TC_TB, J.nact - i0));
+        it.t_first = i0;
+        it.ov = 0;
+        it.ov_at = 0;
+        it.nact = J.nact;
+        it.t_base = 0;
+        it.nsrc = T.kp;
+        it.src = J.cp + (size_t)x * J.cp_stride + (size_t)J.nact * N + (size_t)xt * TC_M;
+        it.sbase = 0;
+        it.dst0 = J.v + (size_t)x * J.v_stride + (size_t)xt * TC_M;
+    }
+    return it;
+}
+
+// target g of an item: compact tower, full tower, slab
+template <int MODE>
+__device__ __forceinline__ void tc_target(const Tables &T, const TcItem &it, int g, int &t, int &tf, int &slab)
+{
+    if (MODE == 0) {
+        t = it.t_first + g;
+        if (it.ov > 0 && t >= it.ov_at) t += it.ov;
+        tf = full_tower(t, it.nact, T.nq);
+        slab = it.sbase + tf;
+    } else {
+        t = it.t_first + g;
+        tf = t;
+        slab = t;
+    }
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// OR of a flag over the 128 producer threads (named barrier 1 with reduction).
+__device__ __forceinline__ bool producers_or(bool f)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)f)
+        : "memory");
+    return r != 0;
+}
+
+constexpr int TC_PROD = 128;                  // producer threads (warps 0-3)
+constexpr int TC_CONS_WARPS = 16;             // consumer warps: 4 lane quarters x 4 target groups
+constexpr int TC_PIPE_THREADS = TC_PROD + 32 * TC_CONS_WARPS;
+constexpr uint32_t TC_PIPE_COLS = 512;        // two accumulators of 256 columns
+
+// Walks a CTA's contiguous run of items: (xt, r) advance without divisions and
+// the item is decoded again only when its (job block, target block) changes.
+template <int MODE>
+struct TcCursor {
+    int xt, r, XT, TBN;
+    TcItem it;
+    __device__ __forceinline__ void start(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int item, int XT_,
+                                          int TBN_)
+    {
+        XT = XT_;
+        TBN = TBN_;
+        xt = item % XT;
+        r = item / XT;
+        it = tc_item<MODE>(T, bu, bd, item, XT, TBN);
+    }
+    __device__ __forceinline__ void next(const Tables &T, const BUpJobs &bu, const BDnJobs &bd)
+    {
+        if (++xt == XT) {
+            xt = 0;
+            ++r;
+            it = tc_item<MODE>(T, bu, bd, r * XT, XT, TBN);
+        } else {
+            it.src += TC_M;
+            it.dst0 += TC_M;
+        }
+    }
+};
+
+// Persistent pipelined base conversion: each CTA (one per SM) takes a
+// contiguous run of items.  Producer warps load the next item's sources into
+// registers while they build the current A tile, then one thread issues the
+// MMAs into the accumulator buffer of the item (two buffers alternate) and
+// commits them to acc_full; consumer warps wait on acc_full, run the
+// epilogue and release the buffer through acc_empty.  Every wait is bounded:
+// on timeout the kernel sets g_tc_error and its threads leave their loops.
+template <int MODE>
+__global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJobs bu, BDnJobs bd, const uint4 *slabs,
+                                                                int XT, int TBN, int items)
+{
+    extern __shared__ unsigned char tc_dyn[];
+    unsigned char *sa0 = tc_dyn + ((128 - (smem_u32(tc_dyn) & 127)) & 127);
+    unsigned char *sb = sa0 + 2 * TC_M * TC_K * 2;
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
+    __shared__ uint32_t tbase_s;
+    __shared__ u64 *s_dst[2][TC_TB];
+    __shared__ u64 s_q[2][TC_TB], s_mont[2][TC_TB];
+    __shared__ int s_G[2];
+    const int per = (items + gridDim.x - 1) / gridDim.x;
+    const int i0 = blockIdx.x * per, i1 = min(items, i0 + per);
+    if (i0 >= i1) return;
+    const size_t N = (size_t)1 << T.logN;
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]), 2);              // MMA commit + producer release of the targets
+            mbar_init(smem_u32(&acc_empty[b]), TC_CONS_WARPS);  // one arrival per consumer warp
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase_s)),
+                     "r"(TC_PIPE_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tbase = tbase_s;
+
+    if (tid < TC_PROD) {
+        // ------------------------------------------------------------ producers
+        const int m = tid;
+        int k = 0, cur_r = -1;
+        TcCursor<MODE> cur, nxt;
+        nxt.start(T, bu, bd, i0, XT, TBN);
+        u64 y[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) y[i] = (nxt.it.G > 0 && i < nxt.it.nsrc) ? nxt.it.src[(size_t)i * N + m] : 0;
+        bool ok = true;
+        for (int item = i0; item < i1; ++item) {
+            cur = nxt;
+            u64 yc[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) yc[i] = y[i];
+            if (item + 1 < i1) {  // the next item's sources are in flight while this one is built
+                nxt.next(T, bu, bd);
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    y[i] = (nxt.it.G > 0 && i < nxt.it.nsrc) ? nxt.it.src[(size_t)i * N + m] : 0;
+            }
+            const TcItem &it = cur.it;
+            if (it.G == 0) continue;
+            const int buf = k & 1;
+            const bool restage = cur.r != cur_r;
+            bool bad = false;
+            // the accumulator and A tile of this buffer were last used by item k-2
+            if (k >= 2) bad = !tc_wait(smem_u32(&acc_empty[buf]), (uint32_t)(((k >> 1) - 1) & 1));
+            // new targets: every earlier MMA must be done with the B slabs
+            if (!bad && restage && k >= 1) bad = !tc_wait(smem_u32(&acc_empty[buf ^ 1]), (uint32_t)(((k - 1) >> 1) & 1));
+            if (producers_or(bad)) {
+                ok = false;
+                break;
+            }
+            if (restage) {
+                constexpr int W = TC_SLAB / 16;
+                for (int idx = m; idx < it.G * W; idx += TC_PROD) {
+                    const int g = idx / W, w = idx % W;
+                    int t, tf, slab;
+                    tc_target<MODE>(T, it, g, t, tf, slab);
+                    reinterpret_cast<uint4 *>(sb)[idx] = slabs[(size_t)slab * W + w];
+                }
+                cur_r = cur.r;
+            }
+            unsigned char *sa = sa0 + buf * (TC_M * TC_K * 2);
+            // A tile: row m, columns 7i+a = byte a of source i (f16); column 63 =
+            // 2048, the bias with the slabs' 4096 there.  Sources past nsrc are 0.
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                if (i >= it.nsrc) yc[i] = 0;
+            uint32_t wd[18];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                wd[2 * i] = (uint32_t)yc[i];
+                wd[2 * i + 1] = (uint32_t)(yc[i] >> 32);
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 8; e += 2) {
+                    const int k0 = 8 * c + e, k1 = k0 + 1;
+                    const int i0s = k0 / 7, a0 = k0 % 7, i1s = k1 / 7, a1 = k1 % 7;
+                    if (k1 == 63)  // byte 6 of source 8, then the bias 2048 (f16 0x6800)
+                        w[e / 2] = (f16x2_bytes(wd[17], 0u, 2u, 0u) & 0xFFFFu) | 0x68000000u;
+                    else
+                        w[e / 2] = f16x2_bytes(wd[2 * i0s + a0 / 4], wd[2 * i1s + a1 / 4], (uint32_t)(a0 % 4),
+                                               (uint32_t)(a1 % 4));
+                }
+                *reinterpret_cast<uint4 *>(sa + tc_off(m, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+            if (m < it.G) {
+                int t, tf, slab;
+                tc_target<MODE>(T, it, m, t, tf, slab);
+                s_dst[buf][m] = it.dst0 + (size_t)(t - it.t_base) * N;
+                s_q[buf][m] = T.modc[tf].q;
+                s_mont[buf][m] = T.modc[tf].mont;
+            }
+            if (m == 0) s_G[buf] = it.G;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            producers_sync();
+            if (m == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t idesc = tc_idesc(16 * it.G);
+                const uint32_t dcol = tbase + (uint32_t)(buf * 256);
+#pragma unroll
+                for (int kk = 0; kk < TC_K / 16; ++kk) {
+                    const uint64_t ad = tc_desc(smem_u32(sa) + kk * 2 * TC_LBO);
+                    const uint64_t bdsc = tc_desc(smem_u32(sb) + kk * 2 * TC_LBO);
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dcol),
+                        "l"(ad), "l"(bdsc), "r"(idesc), "r"((uint32_t)kk));
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&acc_full[buf]))
+                             : "memory");
+                mbar_arrive(smem_u32(&acc_full[buf]));  // releases s_dst/s_q/s_mont/s_G of this buffer
+            }
+            ++k;
+        }
+        if (!ok && tid == 0) {
+            atomicExch(&g_tc_error, 1);
+            // once more, bounded, for the last MMAs still in flight before the memory is freed
+            if (k >= 1) tc_wait(smem_u32(&acc_full[(k - 1) & 1]), (uint32_t)(((k - 1) >> 1) & 1));
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int cw = warp - TC_PROD / 32, quarter = cw % 4, part = cw / 4;
+        const int row = quarter * 32 + lane;
+        int k = 0;
+        bool ok = true;
+        TcCursor<MODE> cur;
+        cur.start(T, bu, bd, i0, XT, TBN);
+        for (int item = i0; item < i1; ++item) {
+            if (item > i0) cur.next(T, bu, bd);
+            if (cur.it.G == 0) continue;
+            const int buf = k & 1;
+            const bool got = tc_wait(smem_u32(&acc_full[buf]), (uint32_t)((k >> 1) & 1));
+            if (__any_sync(0xffffffffu, !got)) {  // the warp's lanes agree (tcgen05.ld is warp-collective)
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int G = s_G[buf];
+            const int g_end = min(G, 4 * part + 4);
+            for (int g = 4 * part; g < g_end; ++g) {
+                uint32_t v[16];
+                const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + 16 * g);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                s_dst[buf][g][row] = tc_reduce(v, s_q[buf][g], s_mont[buf][g]);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&acc_empty[buf]));
+            ++k;
+        }
+        if (!ok && lane == 0) atomicExch(&g_tc_error, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(TC_PIPE_COLS));
+}
+
+// Dynamic shared memory: two A tiles (16 KB each) and up to 16 B slabs
+// (32 KB), padded so that one CTA holds an SM (it takes all 512 columns of
+// tensor memory).
+constexpr int TC_PIPE_SMEM = 120 * 1024;
+static_assert(TC_PIPE_SMEM >= 2 * TC_M * TC_K * 2 + TC_TB * TC_SLAB + 128, "tile space");
+
+}  // namespace
+
+bool bconv_tc_supported(const Tables &T, int nsrc)
+{
+    return nsrc <= 9 && (((size_t)1 << T.logN) % (size_t)TC_M) == 0;
+}
+
+static int sm_count()
+{
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            n = 1;
+        }
+    }
+    return n;
+}
+
+template <int MODE>
+static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int TBN, int Z, const uint4 *slabs,
+                     cudaStream_t st, const char *name)
+{
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_bconv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PIPE_SMEM);
+        attr = true;
+    }
+    const int XT = (int)(((size_t)1 << T.logN) / TC_M);
+    const long long items = (long long)XT * TBN * Z;
+    if (items <= 0) return KS_OK;
+    const int grid = (int)std::min<long long>(items, sm_count());
+    KS_LAUNCH(st, name, k_bconv_tc<MODE><<<grid, TC_PIPE_THREADS, TC_PIPE_SMEM, st>>>(T, bu, bd, slabs, XT, TBN,
+                                                                                        (int)items));
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? KS_OK : fail(KS_ECUDA, std::string(name) + " (tensor cores) launch: " + cudaGetErrorString(e));
+}
+
+int launch_bconv_up_tc(const Tables &T, const BUpJobs &b, const uint4 *slabs, const int *, cudaStream_t st)
+{
+    int span = 0;
+    for (int i = 0; i < b.n; ++i) span = std::max(span, b.job[i].t_end - b.job[i].t_begin);
+    if (span <= 0) return KS_OK;
+    BDnJobs none;
+    none.n = 0;
+    Tables Tt = T;
+    Tt.up_tc = slabs;
+    return launch_tc<0>(Tt, b, none, (span + TC_TB - 1) / TC_TB, b.zpre[b.n], slabs, st, "bconv_up");
+}
+
+int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, cudaStream_t st)
+{
+    int span = 0;
+    for (int i = 0; i < b.n; ++i) span = std::max(span, b.job[i].nact);
+    if (span <= 0) return KS_OK;
+    BUpJobs none;
+    none.n = 0;
+    return launch_tc<1>(T, none, b, (span + TC_TB - 1) / TC_TB, b.zpre[b.n], slabs, st, "bconv_down");
+}
+
+int tc_error_flag(bool clear)
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_tc_error, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (clear && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_tc_error, &z, sizeof(int));
+    }
+    return v;
+}
+
+// Host: the B slab of one target: rows s = 0..15 (shift; 13..15 zero),
+// columns k = 7i + a (source i, byte a of y): byte s - a of constant c_i.
+void tc_slab(const std::vector<u64> &c, uint16_t *slab)
+{
+    for (int r = 0; r < 16; ++r)
+        for (int k = 0; k < TC_K; ++k) {
+            const int i = k / 7, a = k % 7, b = r - a;
+            uint32_t byte = 0;
+            if (i < (int)c.size() && b >= 0 && b <= 6) byte = (uint32_t)((c[i] >> (8 * b)) & 0xFF);
+            // f16 of an integer below 256
+            uint16_t bits = 0;
+            if (byte) {
+                int e = 31 - __builtin_clz(byte);                 // exponent
+                uint32_t mant = (byte << (10 - e)) & 0x3FF;        // 10 fraction bits
+                bits = (uint16_t)(((15 + e) << 10) | mant);
+            }
+            slab[tc_off(r, k) / 2] = bits;
+        }
+    // column 63 (never a slice: 9 sources use 0..62) holds 4096 in the 13 used
+    // shift rows; times the A tile's 2048 there it adds 2^23, so the fp32
+    // accumulator of P (< 2^22) reads 2^23 + P: its bits are 0x4B000000 + P
+    for (int r = 0; r < 13; ++r) slab[tc_off(r, 63) / 2] = (uint16_t)((15 + 12) << 10);
+}
+
+}  // namespace ks

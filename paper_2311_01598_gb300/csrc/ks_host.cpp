@@ -8,6 +8,7 @@
 #include <cstring>
 
 #include "ks_internal.h"
+#include "ks_launch.h"
 
 namespace ks {
 
@@ -233,6 +234,45 @@ int build_tables(ks_params *P)
         for (int i = 0; i < P->nq; ++i)
             dn[(size_t)k * P->nq + i] = split28(to_mont(invmod_h(P->p[k] % P->q[i], P->q[i]), P->q[i]));
 
+    // tensor-core base conversion: one B slab per (digit j, active towers a,
+    // full tower t) for ModUp and per Q tower for ModDown (<= 9 sources)
+    std::vector<uint16_t> up_tc, dn_tc;
+    std::vector<int> up_tc_lvl((size_t)P->nq * P->ndig, 0);
+    constexpr size_t SLAB = 16 * 64;
+    if (A <= 9) {
+        std::vector<int> off((size_t)P->ndig * (A + 1), -1);
+        for (int j = 0; j < P->ndig; ++j) {
+            int lo = j * A;
+            int full = std::min(A, P->nq - lo);
+            for (int a = 1; a <= full; ++a) {
+                off[j * (A + 1) + a] = (int)(up_tc.size() / SLAB);
+                for (int t = 0; t < nt; ++t) {
+                    u64 r = prim[t];
+                    std::vector<u64> c(a);
+                    for (int i = 0; i < a; ++i) {
+                        u64 hat = 1;
+                        for (int k = 0; k < a; ++k)
+                            if (k != i) hat = mulmod_h(hat, prim[lo + k] % r, r);
+                        c[i] = to_mont(hat, r);
+                    }
+                    up_tc.resize(up_tc.size() + SLAB);
+                    tc_slab(c, up_tc.data() + up_tc.size() - SLAB);
+                }
+            }
+        }
+        for (int nact = 1; nact <= P->nq; ++nact)
+            for (int j = 0; j * A < nact; ++j)
+                up_tc_lvl[(size_t)(nact - 1) * P->ndig + j] = off[j * (A + 1) + std::min(A, nact - j * A)];
+    }
+    if (P->kp <= 9) {
+        dn_tc.resize((size_t)P->nq * SLAB);
+        for (int i = 0; i < P->nq; ++i) {
+            std::vector<u64> c(P->kp);
+            for (int k = 0; k < P->kp; ++k) c[k] = to_mont(invmod_h(P->p[k] % P->q[i], P->q[i]), P->q[i]);
+            tc_slab(c, dn_tc.data() + (size_t)i * SLAB);
+        }
+    }
+
     // factors folded into the stored key
     std::vector<ulonglong2> ksc(nt), psc(nt);
     for (int t = 0; t < nt; ++t) {
@@ -265,6 +305,17 @@ int build_tables(ks_params *P)
     if ((rc = upload(&P->d_dn_mat, dn)) != KS_OK) return rc;
     if ((rc = upload(&P->d_key_sc, ksc)) != KS_OK) return rc;
     if ((rc = upload(&P->d_plain_sc, psc)) != KS_OK) return rc;
+    if (!up_tc.empty()) {
+        uint16_t *d = nullptr;
+        if ((rc = upload(&d, up_tc)) != KS_OK) return rc;
+        P->d_up_tc = reinterpret_cast<uint4 *>(d);  // 256-byte aligned allocation
+        if ((rc = upload(&P->d_up_tc_lvl, up_tc_lvl)) != KS_OK) return rc;
+    }
+    if (!dn_tc.empty()) {
+        uint16_t *d = nullptr;
+        if ((rc = upload(&d, dn_tc)) != KS_OK) return rc;
+        P->d_dn_tc = reinterpret_cast<uint4 *>(d);
+    }
 
     Tables &T = P->tables;
     T.modc = P->d_modc;
@@ -276,6 +327,9 @@ int build_tables(ks_params *P)
     T.key_sc = P->d_key_sc;
     T.plain_sc = P->d_plain_sc;
     T.up_mat_lvl = P->d_up_mat_lvl;
+    T.up_tc = P->bconv_tensor ? P->d_up_tc : nullptr;
+    T.up_tc_lvl = P->d_up_tc_lvl;
+    T.dn_tc = P->bconv_tensor ? P->d_dn_tc : nullptr;
     T.logN = P->logN;
     T.nq = P->nq;
     T.kp = P->kp;
@@ -286,14 +340,17 @@ int build_tables(ks_params *P)
 
 void free_tables(ks_params *P)
 {
-    void *ptrs[] = {P->d_modc,   P->d_tw,     P->d_itw,    P->d_up_pre,   P->d_up_pre_lvl,
-                    P->d_up_mat, P->d_dn_mat, P->d_key_sc, P->d_plain_sc, P->d_up_mat_lvl};
+    void *ptrs[] = {P->d_modc,   P->d_tw,     P->d_itw,    P->d_up_pre,   P->d_up_pre_lvl, P->d_up_mat,
+                    P->d_dn_mat, P->d_key_sc, P->d_plain_sc, P->d_up_mat_lvl, P->d_up_tc,      P->d_up_tc_lvl,
+                    P->d_dn_tc};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     P->d_modc = nullptr;
     P->d_tw = P->d_itw = P->d_up_pre = P->d_up_pre_lvl = P->d_key_sc = P->d_plain_sc = nullptr;
     P->d_up_mat = P->d_dn_mat = nullptr;
     P->d_up_mat_lvl = nullptr;
+    P->d_up_tc = P->d_dn_tc = nullptr;
+    P->d_up_tc_lvl = nullptr;
 }
 
 }  // namespace ks

@@ -70,6 +70,11 @@ struct Tables {
     const ulonglong2 *key_sc;   // Montgomery-form fold factors (see header)
     const ulonglong2 *plain_sc; // the same factors without 2^64
     const int *up_mat_lvl;    // ModUp matrix offset of digit j at level nact: [(nact-1)*ndig + j]
+    // tensor-core base conversion: per-target B slabs (null when unsupported
+    // or switched off) and the ModUp slab base of digit j at level nact
+    const uint4 *up_tc;
+    const int *up_tc_lvl;
+    const uint4 *dn_tc;
     int logN;
     int nq, kp, alpha, ndig;
 };
@@ -98,6 +103,9 @@ struct ks_params {
     ulonglong2 *d_up_pre = nullptr;
     ulonglong2 *d_up_pre_lvl = nullptr;  // [nq levels][nq]: ModUp P1 factor per level
     int *d_up_mat_lvl = nullptr;         // [nq levels][ndig]: ModUp matrix offsets per level
+    uint4 *d_up_tc = nullptr, *d_dn_tc = nullptr;  // tensor-core BConv slabs
+    int *d_up_tc_lvl = nullptr;
+    int bconv_tensor = 1;                // use the tensor-core BConv where supported
     uint64_t *d_up_mat = nullptr;
     uint64_t *d_dn_mat = nullptr;
     ulonglong2 *d_key_sc = nullptr, *d_plain_sc = nullptr;

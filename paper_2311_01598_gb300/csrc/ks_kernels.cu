@@ -380,6 +380,7 @@ __global__ void __launch_bounds__(BC_THREADS, 4) k_bconv_up(Tables T, BUpJobs bj
 int launch_bconv_up(const Tables &T, const BUpJobs &b, cudaStream_t st)
 {
     if (b.n == 0) return KS_OK;
+    if (T.up_tc && bconv_tc_supported(T, T.alpha)) return launch_bconv_up_tc(T, b, T.up_tc, T.up_tc_lvl, st);
     int span = 0;
     for (int i = 0; i < b.n; ++i) span = std::max(span, b.job[i].t_end - b.job[i].t_begin);
     if (span <= 0) return KS_OK;
@@ -447,6 +448,7 @@ __global__ void __launch_bounds__(BC_THREADS, 4) k_bconv_down(Tables T, BDnJobs 
 int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st)
 {
     if (b.n == 0) return KS_OK;
+    if (T.dn_tc && bconv_tc_supported(T, T.kp)) return launch_bconv_down_tc(T, b, T.dn_tc, st);
     int span = 0;
     for (int i = 0; i < b.n; ++i) span = std::max(span, b.job[i].nact);
     const size_t N = (size_t)1 << T.logN;

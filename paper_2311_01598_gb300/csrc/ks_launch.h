@@ -5,6 +5,8 @@
 // covers the limbs of every job of a batch; a single key switch is a batch of
 // one.  Blocks find their job by a search over per-launch prefix counts.
 #pragma once
+#include <vector>
+
 #include "ks_internal.h"
 
 namespace ks {
@@ -103,6 +105,18 @@ struct BDnJobs {
 };
 void add_bdn(BDnJobs &b, const BDnJob &j);
 int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st);
+
+// Tensor-core base conversion (ks_bconv_tc.cu): same jobs and outputs as the
+// CUDA-core kernels; used by launch_bconv_up/down when the tables are present
+// and the shape is supported (at most 9 sources, N a multiple of 512).
+bool bconv_tc_supported(const Tables &T, int nsrc);
+int launch_bconv_up_tc(const Tables &T, const BUpJobs &b, const uint4 *slabs, const int *slab_lvl, cudaStream_t st);
+int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, cudaStream_t st);
+// Host: one 2 KB B slab (16 shift rows x 64 slice columns, bf16, canonical
+// layout) for the constants c[0..nsrc) of one target.
+void tc_slab(const std::vector<u64> &c, uint16_t *slab);
+// Device flag set by a tensor-core kernel whose MMA wait gave up (-1: unreadable).
+int tc_error_flag(bool clear);
 
 // ModUp P4+P5 (single job): cp[x][t] = sum_j D_{j,t} * evk_{j,x,t}, D_{j,t} = d_t
 // inside digit j; D holds lazy NTT output.  accumulate: add to cp.  galois

@@ -142,6 +142,10 @@ def lib():
         for name in ("ks_server_create", "ks_server_submit", "ks_server_wait", "ks_server_times", "ks_server_stats",
                      "ks_server_run_trace"):
             getattr(L, name).restype = ci
+        L.ks_params_set_option.argtypes = [vp, ci, ci]
+        L.ks_params_set_option.restype = ci
+        L.ks_device_status.argtypes = [vp, ci, ctypes.POINTER(u32)]
+        L.ks_device_status.restype = ci
         L.ks_switch_hoisted.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.c_uint32, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         L.ks_switch_hoisted.restype = ci
@@ -282,6 +286,17 @@ class Params:
         df = DATAFLOWS[dataflow] if isinstance(dataflow, str) else dataflow
         check(lib().ks_switch(self.handle, key.handle, nact, _ptr(d), _ptr(out0), _ptr(out1), df,
                               _stream_handle(stream)))
+
+    def set_bconv_tensor(self, on: bool) -> None:
+        """KS_OPT_BCONV_TENSOR: base conversions on the tensor cores (default)
+        or on the CUDA cores."""
+        check(lib().ks_params_set_option(self.handle, 1, 1 if on else 0))
+
+    def device_status(self, clear: bool = True) -> int:
+        """ks_device_status: bit 0 = a tensor-core kernel's bounded MMA wait gave up."""
+        f = ctypes.c_uint32()
+        check(lib().ks_device_status(self.handle, 1 if clear else 0, ctypes.byref(f)))
+        return int(f.value)
 
     def switch_hoisted(self, keys, galois, nact: int, d, outs0, outs1, stream=None) -> None:
         """ks_switch_hoisted: key switches of the rotations X -> X^g (g in
