@@ -122,7 +122,7 @@ struct TcItem {
 
 template <int MODE>
 __device__ __forceinline__ TcItem tc_item(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int item, int XT,
-                                          int TBN)
+                                          int TBN, int TB)
 {
     const size_t N = (size_t)1 << T.logN;
     const int xt = item % XT, r = item / XT, tb = r % TBN, z = r / TBN;
@@ -137,8 +137,8 @@ __device__ __forceinline__ TcItem tc_item(const Tables &T, const BUpJobs &bu, co
         it.ov = ohi > olo ? ohi - olo : 0;
         it.ov_at = olo;
         const int nb = (J.t_end - J.t_begin) - it.ov;
-        const int u0 = tb * TC_TB;
-        it.G = max(0, min(TC_TB, nb - u0));
+        const int u0 = tb * TB;
+        it.G = max(0, min(TB, nb - u0));
         it.t_first = J.t_begin + u0;
         it.nact = J.nact;
         it.t_base = J.t_base;
@@ -150,8 +150,8 @@ __device__ __forceinline__ TcItem tc_item(const Tables &T, const BUpJobs &bu, co
         const int jb = find_slot(bd.zpre, bd.n, z);
         const BDnJob &J = bd.job[jb];
         const int x = z - bd.zpre[jb];
-        const int i0 = tb * TC_TB;
-        it.G = max(0, min(TC_TB, J.nact - i0));
+        const int i0 = tb * TB;
+        it.G = max(0, min(TB, J.nact - i0));
         it.t_first = i0;
         it.ov = 0;
         it.ov_at = 0;
@@ -189,45 +189,73 @@ __device__ __forceinline__ void mbar_arrive(uint32_t a)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
 }
-__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
-// OR of a flag over the 128 producer threads (named barrier 1 with reduction).
+__device__ __forceinline__ void producers_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+// OR of a flag over the 256 producer threads (named barrier 1 with reduction).
 __device__ __forceinline__ bool producers_or(bool f)
 {
     uint32_t r;
     asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}"
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 256, p;\n selp.u32 %0, 1, 0, q;\n}"
         : "=r"(r)
         : "r"((uint32_t)f)
         : "memory");
     return r != 0;
 }
 
-constexpr int TC_PROD = 128;                  // producer threads (warps 0-3)
+constexpr int TC_PROD = 256;                  // producer threads (warps 0-7): two per tile row
 constexpr int TC_CONS_WARPS = 16;             // consumer warps: 4 lane quarters x 4 target groups
 constexpr int TC_PIPE_THREADS = TC_PROD + 32 * TC_CONS_WARPS;
 constexpr uint32_t TC_PIPE_COLS = 512;        // two accumulators of 256 columns
+
+// Half H of A-tile row m: K chunks 4H..4H+3 from sources 4H..4H+4 (y[u] =
+// source 4H+u, zero past the item's sources).
+template <int H>
+__device__ __forceinline__ void tc_build_half(unsigned char *sa, int m, const u64 (&y)[5])
+{
+    uint32_t wd[10];
+#pragma unroll
+    for (int u = 0; u < 5; ++u) {
+        wd[2 * u] = (uint32_t)y[u];
+        wd[2 * u + 1] = (uint32_t)(y[u] >> 32);
+    }
+#pragma unroll
+    for (int c = 4 * H; c < 4 * H + 4; ++c) {
+        uint32_t w[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            const int k0 = 8 * c + e, k1 = k0 + 1;
+            const int u0 = k0 / 7 - 4 * H, a0 = k0 % 7, u1 = k1 / 7 - 4 * H, a1 = k1 % 7;
+            if (k1 == 63)  // byte 6 of source 8, then the bias 2048 (f16 0x6800)
+                w[e / 2] = (f16x2_bytes(wd[2 * 4 + 1], 0u, 2u, 0u) & 0xFFFFu) | 0x68000000u;
+            else
+                w[e / 2] = f16x2_bytes(wd[2 * u0 + a0 / 4], wd[2 * u1 + a1 / 4], (uint32_t)(a0 % 4), (uint32_t)(a1 % 4));
+        }
+        *reinterpret_cast<uint4 *>(sa + tc_off(m, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
 
 // Walks a CTA's contiguous run of items: (xt, r) advance without divisions and
 // the item is decoded again only when its (job block, target block) changes.
 template <int MODE>
 struct TcCursor {
-    int xt, r, XT, TBN;
+    int xt, r, XT, TBN, TB;
     TcItem it;
     __device__ __forceinline__ void start(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int item, int XT_,
-                                          int TBN_)
+                                          int TBN_, int TB_)
     {
         XT = XT_;
         TBN = TBN_;
+        TB = TB_;
         xt = item % XT;
         r = item / XT;
-        it = tc_item<MODE>(T, bu, bd, item, XT, TBN);
+        it = tc_item<MODE>(T, bu, bd, item, XT, TBN, TB);
     }
     __device__ __forceinline__ void next(const Tables &T, const BUpJobs &bu, const BDnJobs &bd)
     {
         if (++xt == XT) {
             xt = 0;
             ++r;
-            it = tc_item<MODE>(T, bu, bd, r * XT, XT, TBN);
+            it = tc_item<MODE>(T, bu, bd, r * XT, XT, TBN, TB);
         } else {
             it.src += TC_M;
             it.dst0 += TC_M;
@@ -244,7 +272,7 @@ struct TcCursor {
 // on timeout the kernel sets g_tc_error and its threads leave their loops.
 template <int MODE>
 __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJobs bu, BDnJobs bd, const uint4 *slabs,
-                                                                int XT, int TBN, int items)
+                                                                int XT, int TBN, int TB, int items)
 {
     extern __shared__ unsigned char tc_dyn[];
     unsigned char *sa0 = tc_dyn + ((128 - (smem_u32(tc_dyn) & 127)) & 127);
@@ -278,24 +306,25 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
 
     if (tid < TC_PROD) {
         // ------------------------------------------------------------ producers
-        const int m = tid;
+        const int m = tid % TC_M, h = tid / TC_M;  // row m, K chunks 4h..4h+3 (sources 4h..4h+4)
         int k = 0, cur_r = -1;
         TcCursor<MODE> cur, nxt;
-        nxt.start(T, bu, bd, i0, XT, TBN);
-        u64 y[9];
+        nxt.start(T, bu, bd, i0, XT, TBN, TB);
+        u64 y[5];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) y[i] = (nxt.it.G > 0 && i < nxt.it.nsrc) ? nxt.it.src[(size_t)i * N + m] : 0;
+        for (int u = 0; u < 5; ++u)
+            y[u] = (nxt.it.G > 0 && 4 * h + u < nxt.it.nsrc) ? nxt.it.src[(size_t)(4 * h + u) * N + m] : 0;
         bool ok = true;
         for (int item = i0; item < i1; ++item) {
             cur = nxt;
-            u64 yc[9];
+            u64 yc[5];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) yc[i] = y[i];
+            for (int u = 0; u < 5; ++u) yc[u] = y[u];
             if (item + 1 < i1) {  // the next item's sources are in flight while this one is built
                 nxt.next(T, bu, bd);
 #pragma unroll
-                for (int i = 0; i < 9; ++i)
-                    y[i] = (nxt.it.G > 0 && i < nxt.it.nsrc) ? nxt.it.src[(size_t)i * N + m] : 0;
+                for (int u = 0; u < 5; ++u)
+                    y[u] = (nxt.it.G > 0 && 4 * h + u < nxt.it.nsrc) ? nxt.it.src[(size_t)(4 * h + u) * N + m] : 0;
             }
             const TcItem &it = cur.it;
             if (it.G == 0) continue;
@@ -312,7 +341,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
             }
             if (restage) {
                 constexpr int W = TC_SLAB / 16;
-                for (int idx = m; idx < it.G * W; idx += TC_PROD) {
+                for (int idx = tid; idx < it.G * W; idx += TC_PROD) {
                     const int g = idx / W, w = idx % W;
                     int t, tf, slab;
                     tc_target<MODE>(T, it, g, t, tf, slab);
@@ -323,41 +352,21 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
             unsigned char *sa = sa0 + buf * (TC_M * TC_K * 2);
             // A tile: row m, columns 7i+a = byte a of source i (f16); column 63 =
             // 2048, the bias with the slabs' 4096 there.  Sources past nsrc are 0.
-#pragma unroll
-            for (int i = 0; i < 9; ++i)
-                if (i >= it.nsrc) yc[i] = 0;
-            uint32_t wd[18];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                wd[2 * i] = (uint32_t)yc[i];
-                wd[2 * i + 1] = (uint32_t)(yc[i] >> 32);
-            }
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                uint32_t w[4];
-#pragma unroll
-                for (int e = 0; e < 8; e += 2) {
-                    const int k0 = 8 * c + e, k1 = k0 + 1;
-                    const int i0s = k0 / 7, a0 = k0 % 7, i1s = k1 / 7, a1 = k1 % 7;
-                    if (k1 == 63)  // byte 6 of source 8, then the bias 2048 (f16 0x6800)
-                        w[e / 2] = (f16x2_bytes(wd[17], 0u, 2u, 0u) & 0xFFFFu) | 0x68000000u;
-                    else
-                        w[e / 2] = f16x2_bytes(wd[2 * i0s + a0 / 4], wd[2 * i1s + a1 / 4], (uint32_t)(a0 % 4),
-                                               (uint32_t)(a1 % 4));
-                }
-                *reinterpret_cast<uint4 *>(sa + tc_off(m, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
-            }
-            if (m < it.G) {
+            if (h == 0)
+                tc_build_half<0>(sa, m, yc);
+            else
+                tc_build_half<1>(sa, m, yc);
+            if (h == 0 && m < it.G) {
                 int t, tf, slab;
                 tc_target<MODE>(T, it, m, t, tf, slab);
                 s_dst[buf][m] = it.dst0 + (size_t)(t - it.t_base) * N;
                 s_q[buf][m] = T.modc[tf].q;
                 s_mont[buf][m] = T.modc[tf].mont;
             }
-            if (m == 0) s_G[buf] = it.G;
+            if (tid == 0) s_G[buf] = it.G;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             producers_sync();
-            if (m == 0) {
+            if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t idesc = tc_idesc(16 * it.G);
                 const uint32_t dcol = tbase + (uint32_t)(buf * 256);
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
         int k = 0;
         bool ok = true;
         TcCursor<MODE> cur;
-        cur.start(T, bu, bd, i0, XT, TBN);
+        cur.start(T, bu, bd, i0, XT, TBN, TB);
         for (int item = i0; item < i1; ++item) {
             if (item > i0) cur.next(T, bu, bd);
             if (cur.it.G == 0) continue;
@@ -401,8 +410,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int G = s_G[buf];
-            const int g_end = min(G, 4 * part + 4);
-            for (int g = 4 * part; g < g_end; ++g) {
+            for (int g = part; g < G; g += 4) {  // targets strided over the four warps of a lane quarter
                 uint32_t v[16];
                 const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + 16 * g);
                 asm volatile(
@@ -455,9 +463,12 @@ static int sm_count()
 }
 
 template <int MODE>
-static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int TBN, int Z, const uint4 *slabs,
+static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int span, int Z, const uint4 *slabs,
                      cudaStream_t st, const char *name)
 {
+    // target blocks of equal size (at most 16): 24 targets run as 12 + 12
+    const int TBN = (span + TC_TB - 1) / TC_TB;
+    const int TB = (span + TBN - 1) / TBN;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_bconv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PIPE_SMEM);
@@ -467,7 +478,7 @@ static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int 
     const long long items = (long long)XT * TBN * Z;
     if (items <= 0) return KS_OK;
     const int grid = (int)std::min<long long>(items, sm_count());
-    KS_LAUNCH(st, name, k_bconv_tc<MODE><<<grid, TC_PIPE_THREADS, TC_PIPE_SMEM, st>>>(T, bu, bd, slabs, XT, TBN,
+    KS_LAUNCH(st, name, k_bconv_tc<MODE><<<grid, TC_PIPE_THREADS, TC_PIPE_SMEM, st>>>(T, bu, bd, slabs, XT, TBN, TB,
                                                                                         (int)items));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KS_OK : fail(KS_ECUDA, std::string(name) + " (tensor cores) launch: " + cudaGetErrorString(e));
@@ -475,14 +486,22 @@ static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int 
 
 int launch_bconv_up_tc(const Tables &T, const BUpJobs &b, const uint4 *slabs, const int *, cudaStream_t st)
 {
-    int span = 0;
-    for (int i = 0; i < b.n; ++i) span = std::max(span, b.job[i].t_end - b.job[i].t_begin);
+    int span = 0;  // most targets of any (job, digit): the range minus the digit's own towers
+    for (int i = 0; i < b.n; ++i) {
+        const BUpJob &J = b.job[i];
+        const int nd = (J.nact + T.alpha - 1) / T.alpha;
+        for (int j = (J.jsel >= 0 ? J.jsel : 0); j < (J.jsel >= 0 ? J.jsel + 1 : nd); ++j) {
+            const int lo = j * T.alpha, hi = std::min(lo + T.alpha, J.nact);
+            const int olo = std::max(lo, J.t_begin), ohi = std::min(hi, J.t_end);
+            span = std::max(span, (J.t_end - J.t_begin) - std::max(0, ohi - olo));
+        }
+    }
     if (span <= 0) return KS_OK;
     BDnJobs none;
     none.n = 0;
     Tables Tt = T;
     Tt.up_tc = slabs;
-    return launch_tc<0>(Tt, b, none, (span + TC_TB - 1) / TC_TB, b.zpre[b.n], slabs, st, "bconv_up");
+    return launch_tc<0>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up");
 }
 
 int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, cudaStream_t st)
@@ -492,7 +511,7 @@ int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, 
     if (span <= 0) return KS_OK;
     BUpJobs none;
     none.n = 0;
-    return launch_tc<1>(T, none, b, (span + TC_TB - 1) / TC_TB, b.zpre[b.n], slabs, st, "bconv_down");
+    return launch_tc<1>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down");
 }
 
 int tc_error_flag(bool clear)
