@@ -96,6 +96,16 @@ __device__ __forceinline__ u64 tc_reduce(const uint32_t (&v)[16], u64 q, u64 mon
     return redc(U128{lo, hi}, q, mont);
 }
 
+// 16 consecutive accumulator columns of this warp's 32 lanes (no wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
 __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase)
 {
     uint32_t done = 0;
@@ -410,18 +420,17 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int G = s_G[buf];
-            for (int g = part; g < G; g += 4) {  // targets strided over the four warps of a lane quarter
-                uint32_t v[16];
+            // targets strided over the four warps of a lane quarter, two
+            // tensor-memory loads in flight per wait
+            for (int g = part; g < G; g += 8) {
+                const bool two = g + 4 < G;
+                uint32_t v[16], w[16];
                 const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + 16 * g);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                      "=r"(v[15])
-                    : "r"(taddr));
+                tmem_ld16(taddr, v);
+                if (two) tmem_ld16(taddr + 64, w);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 s_dst[buf][g][row] = tc_reduce(v, s_q[buf][g], s_mont[buf][g]);
+                if (two) s_dst[buf][g + 4][row] = tc_reduce(w, s_q[buf][g + 4], s_mont[buf][g + 4]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
