@@ -381,7 +381,7 @@ def main():
     # ---- the same 16-ciphertext step with compressed keys (a regenerated on chip)
     ckeys = [P.keygen_compressed(s, inputs.galois_secret(s, g), seed=inputs.SEED_BASE + 100 + i)
              for i, g in enumerate(gals)]
-    cjobs = [(ckeys[i], NQ, d[i], o0[i], o1[i]) for i in range(B)]
+    cjobs = [(ckeys[i], NQ, d[i], ks.empty((NQ, N)), ks.empty((NQ, N))) for i in range(B)]  # own outputs
     ctuned, _ = P.autotune(cjobs, reps=2, stream=stream)
     t_c = timed(lambda: P.switch_batch_sched(cjobs, ctuned, stream), args.steps, 2)
     compressed = {"value": round(world * B * args.steps / (t_c / 1e3), 2), "unit": UNIT,

@@ -6,7 +6,8 @@ launches inside it ("launch_window").  Given the CSV of
 `ncu --metrics gpu__time_duration.sum --csv --log-file …` over the same
 command and that window, this prints per kernel its launches, total time
 and share of the window, as a markdown table.  Library kernels are the ones
-named k_*; other launches (PyTorch's) are ignored.
+named k_* (namespace qualifiers allowed); other launches (PyTorch's) are
+ignored.
 
     python -m paper_2311_01598_gb300.launch_summary launches.csv --first F --count C
 
@@ -65,7 +66,7 @@ def read_launches(path):
         if r.get("Metric Name") != "gpu__time_duration.sum":
             continue
         name = r["Kernel Name"]
-        m = re.match(r"(?:void )?(k_[A-Za-z0-9_]+(?:<[^()]*>)?)", name)
+        m = re.search(r"\b(k_[A-Za-z0-9_]+(?:<[^()]*>)?)", name)
         if not m:
             continue
         ns = float(r["Metric Value"].replace(",", ""))
@@ -99,8 +100,18 @@ def to_markdown(table, total, n):
 # library launch names (KS_LAUNCH) of the device kernels
 LIB_NAMES = {"k_fwd_row": "ntt_fwd_row", "k_fwd_col": "ntt_fwd_col", "k_inv_row": "ntt_inv_row",
              "k_inv_col": "ntt_inv_col", "k_bconv_up": "bconv_up", "k_bconv_down": "bconv_down",
+             "k_bconv_tc<0>": "bconv_up", "k_bconv_tc<1>": "bconv_down",
              "k_oc_comb_qw": "oc_comb_q", "k_oc_comb_pw": "oc_comb_p", "k_oc_comb_q": "oc_comb_q",
              "k_oc_comb_p": "oc_comb_p"}
+
+
+def lib_name(kernel_name):
+    """Library launch name of an ncu kernel name, or None."""
+    m = re.search(r"\b(k_[A-Za-z0-9_]+)(<[^()]*>)?", kernel_name)
+    if not m:
+        return None
+    full = m.group(1) + (m.group(2) or "")
+    return LIB_NAMES.get(full, LIB_NAMES.get(m.group(1)))
 
 
 def traffic_from_report(rep, key_switches):
@@ -115,13 +126,12 @@ def traffic_from_report(rep, key_switches):
     scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
     per = {}
     for r in rows[2:]:
-        m = re.match(r"(?:void )?(k_[A-Za-z0-9_]+)", r[ix["Kernel Name"]])
-        if not m or m.group(1) not in LIB_NAMES:
+        lib = lib_name(r[ix["Kernel Name"]])
+        if lib is None:
             continue
         b = 0.0
         for name in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             b += float(r[ix[name]].replace(",", "")) * scale[units[ix[name]]]
-        lib = LIB_NAMES[m.group(1)]
         c, t = per.get(lib, (0, 0.0))
         per[lib] = (c + 1, t + b)
     return {k: {"launches": c, "dram_bytes_per_ks": t / key_switches} for k, (c, t) in per.items()}
