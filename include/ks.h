@@ -94,12 +94,17 @@ int ks_params_info(const ks_params *params, uint64_t *h_q, uint64_t *h_p,
 
 /* Implementation options of a parameter set (none changes any result).
  *   KS_OPT_BCONV_TENSOR (default 1): run the fast base conversions (ModUp P2,
- *     ModDown P2) on the tensor cores (tcgen05, exact bf16 byte slices)
- *     wherever at most 9 source towers meet N >= 2^9; 0 selects the CUDA-core
+ *     ModDown P2) on the tensor cores (tcgen05, exact f16 byte slices)
+ *     wherever at most 9 source towers meet N >= 2^7; 0 selects the CUDA-core
  *     kernels everywhere.
+ *   KS_OPT_BATCH_LANES (default 2, 1..4): an Output-Centric batch of at least
+ *     4 jobs per lane is split over that many library streams, forked from
+ *     and joined back to the caller's stream (the memory-bound combine
+ *     kernels of one part then overlap the integer-bound passes of another);
+ *     1 keeps every launch on the caller's stream.
  * Returns KS_EINVAL for an unknown option or value.  Not thread-safe with
  * concurrent calls on the same params object. */
-enum { KS_OPT_BCONV_TENSOR = 1 };
+enum { KS_OPT_BCONV_TENSOR = 1, KS_OPT_BATCH_LANES = 2 };
 int ks_params_set_option(ks_params *params, int option, int value);
 
 /* Device-side status of the library on the params object's GPU: bit 0 is set
@@ -402,6 +407,14 @@ int ks_server_run_trace(ks_server *server, uint32_t n, const ks_request *reqs, c
  * forward NTT butterflies per second and base-conversion multiply-
  * accumulates per second.  iters: loop trips per thread (e.g. 4096). */
 int ks_probe_alu(int iters, double *bfly_per_s, double *mac_per_s);
+
+/* Issue rates of single integer instructions on this GPU, in lanes per SM
+ * per clock (all SMs, 8 independent chains per thread, the device's clock
+ * attribute): out[0] mad.lo.u32, [1] mad.wide.u32 (64-bit accumulate),
+ * [2] mul.lo.u64, [3] mul.hi.u64, [4] add.u32.  n >= 5.  The multiply-pipe
+ * cost of the kernels' modular products follows from these (a Shoup product
+ * is two mul.lo.u64 and one mul.hi.u64). */
+int ks_probe_int_pipes(double *lanes_per_clk_sm, int n);
 
 /* Number of kernels this library has launched since it was loaded. */
 uint64_t ks_kernel_launches(void);

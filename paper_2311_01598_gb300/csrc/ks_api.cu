@@ -141,6 +141,16 @@ static int get_stage(ks_params *P, HostStage **out)
 
 static void free_ws(ks_params *P)
 {
+    for (int l = 0; l < 4; ++l)
+        if (P->lane_st[l]) {
+            cudaStreamDestroy(P->lane_st[l]);
+            P->lane_st[l] = nullptr;
+        }
+    for (int e = 0; e < 5; ++e)
+        if (P->lane_ev[e]) {
+            cudaEventDestroy(P->lane_ev[e]);
+            P->lane_ev[e] = nullptr;
+        }
     if (P->stage) {
         HostStage *h = P->stage;
         if (h->scratch) cudaFree(h->scratch);
@@ -696,12 +706,18 @@ int ks_params_set_option(ks_params *P, int option, int value)
 {
     int rc = check_params(P);
     if (rc) return rc;
-    if (option != KS_OPT_BCONV_TENSOR || (value != 0 && value != 1)) return fail(KS_EINVAL, "unknown option or value");
     std::lock_guard<std::mutex> g(P->mu);
-    P->bconv_tensor = value;
-    P->tables.up_tc = value ? P->d_up_tc : nullptr;
-    P->tables.dn_tc = value ? P->d_dn_tc : nullptr;
-    return KS_OK;
+    if (option == KS_OPT_BCONV_TENSOR && (value == 0 || value == 1)) {
+        P->bconv_tensor = value;
+        P->tables.up_tc = value ? P->d_up_tc : nullptr;
+        P->tables.dn_tc = value ? P->d_dn_tc : nullptr;
+        return KS_OK;
+    }
+    if (option == KS_OPT_BATCH_LANES && value >= 1 && value <= 4) {
+        P->batch_lanes = value;
+        return KS_OK;
+    }
+    return fail(KS_EINVAL, "unknown option or value");
 }
 
 int ks_device_status(const ks_params *P, int clear, uint32_t *flags)
@@ -749,6 +765,26 @@ int check_schedule(const ks_schedule *sc)
     return KS_OK;
 }
 
+static int run_oc_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st);
+constexpr uint32_t kLaneJobs = 4;  // fewest jobs worth a lane of their own
+
+static int lane_streams(ks_params *P)
+{
+    std::lock_guard<std::mutex> g(P->mu);
+    if (P->lane_st[0]) return KS_OK;
+    for (int l = 0; l < 4; ++l)
+        if (cudaStreamCreateWithFlags(&P->lane_st[l], cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(KS_ECUDA, "lane stream creation failed");
+        }
+    for (int e = 0; e < 5; ++e)
+        if (cudaEventCreateWithFlags(&P->lane_ev[e], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(KS_ECUDA, "lane event creation failed");
+        }
+    return KS_OK;
+}
+
 // Run a validated batch under a schedule.
 int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st)
 {
@@ -769,7 +805,39 @@ int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &s
         return KS_OK;
     }
     // Output-Centric: every stage launch covers a group of sc.chunk jobs, each
-    // with its own scratch.
+    // with its own scratch.  A large batch is split over internal streams
+    // (at least kLaneJobs jobs each) forked from and joined back to st, so the
+    // memory-bound combine kernels of one part overlap the integer-bound
+    // passes of another.
+    const int lanes = std::min<int>(P->batch_lanes, (int)(n / kLaneJobs));
+    if (lanes > 1) {
+        std::vector<ks_job> sorted(n);
+        for (uint32_t i = 0; i < n; ++i) sorted[i] = jobs[idx[i]];
+        if ((rc = lane_streams(P)) != KS_OK) return rc;
+        std::lock_guard<std::mutex> lg(P->lane_mu);  // the fork event and lanes are shared
+        if ((rc = cuda_check(cudaEventRecord(P->lane_ev[4], st), "lane fork")) != KS_OK) return rc;
+        ks_schedule one = sc;
+        one.order = 0;  // already ordered
+        uint32_t at = 0;
+        for (int l = 0; l < lanes; ++l) {
+            const uint32_t cnt = n / lanes + ((uint32_t)l < n % lanes ? 1 : 0);
+            if ((rc = cuda_check(cudaStreamWaitEvent(P->lane_st[l], P->lane_ev[4], 0), "lane fork")) != KS_OK) return rc;
+            if ((rc = run_oc_batch(P, cnt, sorted.data() + at, one, P->lane_st[l])) != KS_OK) return rc;
+            if ((rc = cuda_check(cudaEventRecord(P->lane_ev[l], P->lane_st[l]), "lane join")) != KS_OK) return rc;
+            if ((rc = cuda_check(cudaStreamWaitEvent(st, P->lane_ev[l], 0), "lane join")) != KS_OK) return rc;
+            at += cnt;
+        }
+        return KS_OK;
+    }
+    std::vector<ks_job> sorted(n);
+    for (uint32_t i = 0; i < n; ++i) sorted[i] = jobs[idx[i]];
+    return run_oc_batch(P, n, sorted.data(), sc, st);
+}
+
+// Output-Centric batch in the given order on one stream.
+static int run_oc_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st)
+{
+    int rc;
     Workspace *w = nullptr;
     if ((rc = get_ws(P, st, false, &w)) != KS_OK) return rc;
     size_t words = 0;
@@ -791,7 +859,7 @@ int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &s
     std::vector<OcJob> oj(n);
     size_t off = 0;
     for (uint32_t k = 0; k < n; ++k) {
-        const ks_job &j = jobs[idx[k]];
+        const ks_job &j = jobs[k];
         const int nact = (int)j.level_towers;
         oj[k] = oc_job(P, j.key, nact, j.d_in, j.d_out0, j.d_out1, w->batch + off);
         off += oc_scratch_words(P->tables, nact);

@@ -106,6 +106,10 @@ struct ks_params {
     uint4 *d_up_tc = nullptr, *d_dn_tc = nullptr;  // tensor-core BConv slabs
     int *d_up_tc_lvl = nullptr;
     int bconv_tensor = 1;                // use the tensor-core BConv where supported
+    int batch_lanes = 2;                 // internal streams a large Output-Centric batch is split over
+    cudaStream_t lane_st[4] = {};        // created on first use
+    cudaEvent_t lane_ev[5] = {};
+    std::mutex lane_mu;                  // one batch at a time enqueues on the lanes
     uint64_t *d_up_mat = nullptr;
     uint64_t *d_dn_mat = nullptr;
     ulonglong2 *d_key_sc = nullptr, *d_plain_sc = nullptr;

@@ -54,9 +54,89 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_bmac(u64 *out, u64 c, i
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// Throughput of single integer instructions (the building blocks of the
+// kernels' modular arithmetic): 8 independent chains per thread.
+constexpr int kPipeIters = 2048;
+template <int OP>
+__global__ void __launch_bounds__(kProbeThreads) k_probe_pipe(u64 *out, u64 b0)
+{
+    u64 acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = threadIdx.x + c;
+    for (int it = 0; it < kPipeIters; ++it) {
+        const u64 b = b0 + it;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (OP == 0) {  // mad.lo.u32
+                uint32_t a = (uint32_t)acc[c];
+                asm volatile("mad.lo.u32 %0, %0, %1, %2;" : "+r"(a) : "r"((uint32_t)b), "r"((uint32_t)b0));
+                acc[c] = a;
+            } else if (OP == 1) {  // mad.wide.u32 (64-bit accumulate)
+                asm volatile("mad.wide.u32 %0, %1, %2, %0;" : "+l"(acc[c]) : "r"((uint32_t)acc[c]), "r"((uint32_t)b));
+            } else if (OP == 2) {  // mul.lo.u64
+                asm volatile("mul.lo.u64 %0, %0, %1;" : "+l"(acc[c]) : "l"(b));
+            } else if (OP == 3) {  // mul.hi.u64
+                asm volatile("mul.hi.u64 %0, %0, %1;" : "+l"(acc[c]) : "l"(b | 0x100000000ull));
+            } else {  // add.u32
+                uint32_t a = (uint32_t)acc[c];
+                asm volatile("add.u32 %0, %0, %1;" : "+r"(a) : "r"((uint32_t)b));
+                acc[c] = a;
+            }
+        }
+    }
+    u64 s = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += acc[c];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 }  // namespace ks
 
 using namespace ks;
+
+extern "C" int ks_probe_int_pipes(double *lanes_per_clk_sm, int n)
+{
+    if (!lanes_per_clk_sm || n < 5) return fail(KS_EINVAL, "ks_probe_int_pipes: need room for 5 rates");
+    int dev = 0, sms = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "ks_probe_int_pipes: device query failed");
+    }
+    u64 *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc((void **)&out, sizeof(u64) * kProbeBlocks * kProbeThreads) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        if (out) cudaFree(out);
+        return fail(KS_ECUDA, "ks_probe_int_pipes: setup failed");
+    }
+    const double ops = (double)kProbeBlocks * kProbeThreads * kPipeIters * 8;
+    for (int op = 0; op < 5; ++op) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0);
+            switch (op) {
+            case 0: k_probe_pipe<0><<<kProbeBlocks, kProbeThreads>>>(out, 3); break;
+            case 1: k_probe_pipe<1><<<kProbeBlocks, kProbeThreads>>>(out, 3); break;
+            case 2: k_probe_pipe<2><<<kProbeBlocks, kProbeThreads>>>(out, 3); break;
+            case 3: k_probe_pipe<3><<<kProbeBlocks, kProbeThreads>>>(out, 0x123456789abcdefull); break;
+            default: k_probe_pipe<4><<<kProbeBlocks, kProbeThreads>>>(out, 3); break;
+            }
+            cudaEventRecord(e1);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0 && ms < best) best = ms;  // first repetition warms up
+        }
+        lanes_per_clk_sm[op] = ops / (best * 1e-3) / ((double)sms * khz * 1e3);
+    }
+    const bool bad = cudaGetLastError() != cudaSuccess;
+    cudaFree(out);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return bad ? fail(KS_ECUDA, "ks_probe_int_pipes: kernel failed") : KS_OK;
+}
 
 extern "C" int ks_probe_alu(int iters, double *bfly_per_s, double *mac_per_s)
 {

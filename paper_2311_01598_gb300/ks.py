@@ -149,6 +149,8 @@ def lib():
         L.ks_switch_hoisted.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.c_uint32, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         L.ks_switch_hoisted.restype = ci
+        L.ks_probe_int_pipes.argtypes = [ctypes.POINTER(ctypes.c_double), ci]
+        L.ks_probe_int_pipes.restype = ci
         L.ks_probe_alu.argtypes = [ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.ks_probe_alu.restype = ci
         L.ks_kernel_launches.argtypes = []
@@ -291,6 +293,10 @@ class Params:
         """KS_OPT_BCONV_TENSOR: base conversions on the tensor cores (default)
         or on the CUDA cores."""
         check(lib().ks_params_set_option(self.handle, 1, 1 if on else 0))
+
+    def set_batch_lanes(self, lanes: int) -> None:
+        """KS_OPT_BATCH_LANES: library streams a large Output-Centric batch is split over."""
+        check(lib().ks_params_set_option(self.handle, 2, int(lanes)))
 
     def device_status(self, clear: bool = True) -> int:
         """ks_device_status: bit 0 = a tensor-core kernel's bounded MMA wait gave up."""
@@ -519,6 +525,13 @@ class Mlp:
 # -- measurement hooks ---------------------------------------------------------------
 def kernel_launches() -> int:
     return int(lib().ks_kernel_launches())
+
+
+def probe_int_pipes() -> dict:
+    """ks_probe_int_pipes: lanes per SM per clock of single integer instructions."""
+    out = (ctypes.c_double * 5)()
+    check(lib().ks_probe_int_pipes(out, 5))
+    return dict(zip(("mad.lo.u32", "mad.wide.u32", "mul.lo.u64", "mul.hi.u64", "add.u32"), [round(x, 2) for x in out]))
 
 
 def probe_alu(iters: int = 4096) -> tuple[float, float]:

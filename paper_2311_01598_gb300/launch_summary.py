@@ -32,9 +32,9 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TRAFFIC_PATH = os.path.join(HERE, "data", "ncu_traffic_gb300.json")
-# the files whose change invalidates recorded per-kernel DRAM traffic
-KERNEL_SOURCES = ("csrc/ks_kernels.cu", "csrc/ks_oc.cu", "csrc/ks_device.cuh", "csrc/ks_ntt_core.cuh",
-                  "csrc/ks_launch.h", "csrc/ks_api.cu")
+# the device-code files whose change invalidates recorded per-kernel DRAM traffic
+KERNEL_SOURCES = ("csrc/ks_kernels.cu", "csrc/ks_oc.cu", "csrc/ks_bconv_tc.cu", "csrc/ks_device.cuh",
+                  "csrc/ks_ntt_core.cuh", "csrc/ks_launch.h")
 
 
 def kernel_sources_sha() -> str:
