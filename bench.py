@@ -396,12 +396,22 @@ def main():
     # ---- the paper's parameter sets (Table III): 4 ciphertexts a step, own keys
     table3 = table3_sets(stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 9)
 
-    # ---- the plain single-ciphertext paths beside it
+    # ---- the plain single-ciphertext paths beside it, and the Output-Centric
+    # one replayed from a CUDA graph (launch gaps matter at this size)
     singles = {}
     for df in ("MP", "DC", "OC"):
         f = lambda df=df: P.switch(keys[0], NQ, d[0], o0[0], o1[0], df, stream)  # noqa: E731
         t = timed(f, args.steps, 3)
         singles[df] = world * args.steps / (t / 1e3)
+    gs = torch.cuda.Stream()  # capture needs a stream of its own; warm it (scratch) first
+    with torch.cuda.stream(gs):
+        P.switch(keys[0], NQ, d[0], o0[0], o1[0], "OC", gs)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=gs):
+        P.switch(keys[0], NQ, d[0], o0[0], o1[0], "OC", gs)
+    t = timed(graph.replay, args.steps, 3)  # replays on the timing stream
+    singles["OC_graph"] = world * args.steps / (t / 1e3)
 
     # ---- end to end through the host-buffer entry point
     hin = [torch.empty((NQ, N), dtype=torch.int64, pin_memory=True) for _ in range(B)]

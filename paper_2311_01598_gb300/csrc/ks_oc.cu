@@ -241,6 +241,49 @@ static int oc_rows(const Tables &T, const OcJobs &oj, bool p_section, cudaStream
 // resident warps per SM than the fused row kernels, at the price of one more
 // round trip of the section's limbs through L2/HBM.
 
+// V consecutive coefficients per thread (V = 2: 16-byte loads and stores;
+// limb bases and even coefficient indices keep them aligned).
+template <int V>
+__device__ __forceinline__ void ldv(const u64 *p, u64 (&o)[V])
+{
+    if constexpr (V == 2) {
+        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p);
+        o[0] = t.x;
+        o[1] = t.y;
+    } else {
+        o[0] = *p;
+    }
+}
+template <int V>
+__device__ __forceinline__ void stv(u64 *p, const u64 (&v)[V])
+{
+    if constexpr (V == 2)
+        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(v[0], v[1]);
+    else
+        *p = v[0];
+}
+// key product of V coefficients: x * b_j and x * a_j added into sb, sa
+template <bool CK, int V>
+__device__ __forceinline__ void key_macv(const KeyView &K, int j, int t, size_t n, int nfull, int logN, u64 q,
+                                         const u64 (&x)[V], U128 (&sb)[V], U128 (&sa)[V])
+{
+    const size_t N = (size_t)1 << logN;
+    u64 kb[V], ka[V];
+    if (CK && K.comp) {
+        ldv<V>(K.evk + ((size_t)j * nfull + t) * N + n, kb);
+#pragma unroll
+        for (int c = 0; c < V; ++c) ka[c] = key_a_word(K.a_seed, j, t, n + c, logN, nfull, q);
+    } else {
+        ldv<V>(K.evk + ((size_t)(2 * j) * nfull + t) * N + n, kb);
+        ldv<V>(K.evk + ((size_t)(2 * j + 1) * nfull + t) * N + n, ka);
+    }
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        mac128(sb[c], x[c], kb[c]);
+        mac128(sa[c], x[c], ka[c]);
+    }
+}
+
 static bool any_compressed(const OcJobs &oj)
 {
     for (int i = 0; i < oj.n; ++i)
@@ -249,8 +292,8 @@ static bool any_compressed(const OcJobs &oj)
 }
 
 // P section combine: c'_{x,p_k} = sum_j NTT(z_{j,p_k}) * evk_{j,x,p_k} for
-// every coefficient, written canonical to cp.  grid (N/256, jobs*K).
-template <bool CK>
+// every coefficient, written canonical to cp.  grid (N/(256V), jobs*K).
+template <bool CK, int V>
 __global__ void __launch_bounds__(256) k_oc_comb_p(Tables T, OcJobs oj)
 {
     const int K = T.kp;
@@ -261,22 +304,30 @@ __global__ void __launch_bounds__(256) k_oc_comb_p(Tables T, OcJobs oj)
     const int nt = J.nact + K;
     const int nfull = T.nq + K;
     const size_t N = (size_t)1 << T.logN;
-    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
     const ModC &mc = T.modc[tf];
-    U128 sb = {0, 0}, sa = {0, 0};
+    U128 sb[V], sa[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) sb[c] = sa[c] = U128{0, 0};
     for (int j = 0; j < J.nd; ++j) {
-        const u64 x = J.tmp[(size_t)(j * K + k) * N + n];
-        mac128(sb, x, key_b<CK>(J.key, j, tf, n, nfull, T.logN));
-        mac128(sa, x, key_a<CK>(J.key, j, tf, n, nfull, T.logN, mc.q));
+        u64 x[V];
+        ldv<V>(J.tmp + (size_t)(j * K + k) * N + n, x);
+        key_macv<CK, V>(J.key, j, tf, n, nfull, T.logN, mc.q, x, sb, sa);
     }
-    J.cp[(size_t)t * N + n] = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    J.cp[(size_t)(nt + t) * N + n] = key_a_finish<CK>(J.key, sa, mc, T.key_sc, tf);
+    u64 ob[V], oa[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        ob[c] = reduce_any(redc(sb[c], mc.q, mc.mont), mc.q, mc.one_sh);
+        oa[c] = key_a_finish<CK>(J.key, sa[c], mc, T.key_sc, tf);
+    }
+    stv<V>(J.cp + (size_t)t * N + n, ob);
+    stv<V>(J.cp + (size_t)(nt + t) * N + n, oa);
 }
 
 // Q section combine: out_x = sum_j D_j * evk_{j,x} - NTT(v_x), D_j the
 // transformed ModUp limb or the input tower for the own digit.
-// grid (N/256, sum of nact over jobs).
-template <bool CK>
+// grid (N/(256V), sum of nact over jobs).
+template <bool CK, int V>
 __global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
 {
     const int jb = find_slot(oj.pre, oj.n, blockIdx.y);
@@ -286,37 +337,47 @@ __global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
     const int j0 = t / T.alpha;
     const int nfull = T.nq + T.kp;
     const size_t N = (size_t)1 << T.logN;
-    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
     const ModC &mc = T.modc[t];
-    U128 sb = {0, 0}, sa = {0, 0};
+    U128 sb[V], sa[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) sb[c] = sa[c] = U128{0, 0};
     for (int j = 0; j < J.nd; ++j) {
-        const u64 x = j == j0 ? J.d[(size_t)t * N + n] : J.tmp[(size_t)(j * nact + t) * N + n];
-        mac128(sb, x, key_b<CK>(J.key, j, t, n, nfull, T.logN));
-        mac128(sa, x, key_a<CK>(J.key, j, t, n, nfull, T.logN, mc.q));
+        u64 x[V];
+        ldv<V>(j == j0 ? J.d + (size_t)t * N + n : J.tmp + (size_t)(j * nact + t) * N + n, x);
+        key_macv<CK, V>(J.key, j, t, n, nfull, T.logN, mc.q, x, sb, sa);
     }
+    u64 vb[V], va[V], o0[V], o1[V];
+    ldv<V>(J.tmp + (size_t)(J.nd * nact + t) * N + n, vb);
+    ldv<V>(J.tmp + (size_t)((J.nd + 1) * nact + t) * N + n, va);
     const u64 q40 = 40 * mc.q;
-    const u64 cb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    const u64 ca = key_a_finish<CK>(J.key, sa, mc, T.key_sc, t);
-    const u64 vb = J.tmp[(size_t)(J.nd * nact + t) * N + n];
-    const u64 va = J.tmp[(size_t)((J.nd + 1) * nact + t) * N + n];
-    J.out0[(size_t)t * N + n] = reduce_any(cb + q40 - vb, mc.q, mc.one_sh);
-    J.out1[(size_t)t * N + n] = reduce_any(ca + q40 - va, mc.q, mc.one_sh);
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        const u64 cb = reduce_any(redc(sb[c], mc.q, mc.mont), mc.q, mc.one_sh);
+        const u64 ca = key_a_finish<CK>(J.key, sa[c], mc, T.key_sc, t);
+        o0[c] = reduce_any(cb + q40 - vb[c], mc.q, mc.one_sh);
+        o1[c] = reduce_any(ca + q40 - va[c], mc.q, mc.one_sh);
+    }
+    stv<V>(J.out0 + (size_t)t * N + n, o0);
+    stv<V>(J.out1 + (size_t)t * N + n, o1);
 }
 
 static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
-    const dim3 gp((unsigned)(N / 256), oj.n * T.kp), gq((unsigned)(N / 256), oj.pre[oj.n]);
+    // Q towers: two coefficients a thread (16-byte accesses); the P-tower
+    // combine has few rows and keeps one (measured faster)
+    const dim3 gp((unsigned)(N / 256), oj.n * T.kp), gq((unsigned)(N / 512), oj.pre[oj.n]);
     if (p_section) {
         if (any_compressed(oj))
-            KS_LAUNCH(st, "oc_comb_p", k_oc_comb_p<true><<<gp, 256, 0, st>>>(T, oj));
+            KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_p<true, 1><<<gp, 256, 0, st>>>(T, oj)));
         else
-            KS_LAUNCH(st, "oc_comb_p", k_oc_comb_p<false><<<gp, 256, 0, st>>>(T, oj));
+            KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_p<false, 1><<<gp, 256, 0, st>>>(T, oj)));
     } else {
         if (any_compressed(oj))
-            KS_LAUNCH(st, "oc_comb_q", k_oc_comb_q<true><<<gq, 256, 0, st>>>(T, oj));
+            KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_q<true, 2><<<gq, 256, 0, st>>>(T, oj)));
         else
-            KS_LAUNCH(st, "oc_comb_q", k_oc_comb_q<false><<<gq, 256, 0, st>>>(T, oj));
+            KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_q<false, 2><<<gq, 256, 0, st>>>(T, oj)));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(KS_ECUDA, std::string("OC combine launch: ") + cudaGetErrorString(e));
@@ -333,7 +394,8 @@ size_t oc_scratch_words(const Tables &T, int nact)
 
 // Whole-basis variant: tmp holds D [nd][nact+K] then v [2][nact].
 // P-tower combine of this layout: c'_{x,p_k} from D rows at tower nact+k.
-template <bool CK>
+// grid (N/(256V), jobs*K).
+template <bool CK, int V>
 __global__ void __launch_bounds__(256) k_oc_comb_pw(Tables T, OcJobs oj)
 {
     const int K = T.kp;
@@ -344,20 +406,28 @@ __global__ void __launch_bounds__(256) k_oc_comb_pw(Tables T, OcJobs oj)
     const int nt = J.nact + K;
     const int nfull = T.nq + K;
     const size_t N = (size_t)1 << T.logN;
-    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
     const ModC &mc = T.modc[tf];
-    U128 sb = {0, 0}, sa = {0, 0};
+    U128 sb[V], sa[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) sb[c] = sa[c] = U128{0, 0};
     for (int j = 0; j < J.nd; ++j) {
-        const u64 x = J.tmp[((size_t)j * nt + t) * N + n];
-        mac128(sb, x, key_b<CK>(J.key, j, tf, n, nfull, T.logN));
-        mac128(sa, x, key_a<CK>(J.key, j, tf, n, nfull, T.logN, mc.q));
+        u64 x[V];
+        ldv<V>(J.tmp + ((size_t)j * nt + t) * N + n, x);
+        key_macv<CK, V>(J.key, j, tf, n, nfull, T.logN, mc.q, x, sb, sa);
     }
-    J.cp[(size_t)t * N + n] = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    J.cp[(size_t)(nt + t) * N + n] = key_a_finish<CK>(J.key, sa, mc, T.key_sc, tf);
+    u64 ob[V], oa[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        ob[c] = reduce_any(redc(sb[c], mc.q, mc.mont), mc.q, mc.one_sh);
+        oa[c] = key_a_finish<CK>(J.key, sa[c], mc, T.key_sc, tf);
+    }
+    stv<V>(J.cp + (size_t)t * N + n, ob);
+    stv<V>(J.cp + (size_t)(nt + t) * N + n, oa);
 }
 
-// Q-tower combine of the whole-basis layout.  grid (N/256, sum of nact).
-template <bool CK>
+// Q-tower combine of the whole-basis layout.  grid (N/(256V), sum of nact).
+template <bool CK, int V>
 __global__ void __launch_bounds__(256) k_oc_comb_qw(Tables T, OcJobs oj)
 {
     const int jb = find_slot(oj.pre, oj.n, blockIdx.y);
@@ -368,20 +438,30 @@ __global__ void __launch_bounds__(256) k_oc_comb_qw(Tables T, OcJobs oj)
     const int j0 = t / T.alpha;
     const int nfull = T.nq + T.kp;
     const size_t N = (size_t)1 << T.logN;
-    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t n = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
     const ModC &mc = T.modc[t];
-    U128 sb = {0, 0}, sa = {0, 0};
+    U128 sb[V], sa[V];
+#pragma unroll
+    for (int c = 0; c < V; ++c) sb[c] = sa[c] = U128{0, 0};
     for (int j = 0; j < J.nd; ++j) {
-        const u64 x = j == j0 ? J.d[(size_t)t * N + n] : J.tmp[((size_t)j * nt + t) * N + n];
-        mac128(sb, x, key_b<CK>(J.key, j, t, n, nfull, T.logN));
-        mac128(sa, x, key_a<CK>(J.key, j, t, n, nfull, T.logN, mc.q));
+        u64 x[V];
+        ldv<V>(j == j0 ? J.d + (size_t)t * N + n : J.tmp + ((size_t)j * nt + t) * N + n, x);
+        key_macv<CK, V>(J.key, j, t, n, nfull, T.logN, mc.q, x, sb, sa);
     }
     const u64 *v = J.tmp + (size_t)J.nd * nt * N;
+    u64 vb[V], va[V], o0[V], o1[V];
+    ldv<V>(v + (size_t)t * N + n, vb);
+    ldv<V>(v + (size_t)(nact + t) * N + n, va);
     const u64 q40 = 40 * mc.q;
-    const u64 cb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
-    const u64 ca = key_a_finish<CK>(J.key, sa, mc, T.key_sc, t);
-    J.out0[(size_t)t * N + n] = reduce_any(cb + q40 - v[(size_t)t * N + n], mc.q, mc.one_sh);
-    J.out1[(size_t)t * N + n] = reduce_any(ca + q40 - v[(size_t)(nact + t) * N + n], mc.q, mc.one_sh);
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        const u64 cb = reduce_any(redc(sb[c], mc.q, mc.mont), mc.q, mc.one_sh);
+        const u64 ca = key_a_finish<CK>(J.key, sa[c], mc, T.key_sc, t);
+        o0[c] = reduce_any(cb + q40 - vb[c], mc.q, mc.one_sh);
+        o1[c] = reduce_any(ca + q40 - va[c], mc.q, mc.one_sh);
+    }
+    stv<V>(J.out0 + (size_t)t * N + n, o0);
+    stv<V>(J.out1 + (size_t)t * N + n, o1);
 }
 
 static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream_t st)
@@ -415,18 +495,19 @@ static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream
     if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;          // P2, every tower
     if ((rc = launch_ntt_fwd(T, mD, false, st)) != KS_OK) return rc;    // P3
     const bool ck = any_compressed(oj);
-    const dim3 gp((unsigned)(N / 256), n * K), gq((unsigned)(N / 256), oj.pre[n]);
+    // Q towers two coefficients a thread, P towers one (as in oc_combine)
+    const dim3 gp((unsigned)(N / 256), n * K), gq((unsigned)(N / 512), oj.pre[n]);
     if (ck)  // P4+P5, P towers
-        KS_LAUNCH(st, "oc_comb_p", k_oc_comb_pw<true><<<gp, 256, 0, st>>>(T, oj));
+        KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_pw<true, 1><<<gp, 256, 0, st>>>(T, oj)));
     else
-        KS_LAUNCH(st, "oc_comb_p", k_oc_comb_pw<false><<<gp, 256, 0, st>>>(T, oj));
+        KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_pw<false, 1><<<gp, 256, 0, st>>>(T, oj)));
     if ((rc = launch_ntt_inv(T, mw, false, st)) != KS_OK) return rc;    // ModDown P1
     if ((rc = launch_bconv_down(T, bd, st)) != KS_OK) return rc;        // ModDown P2
     if ((rc = launch_ntt_fwd(T, mv, false, st)) != KS_OK) return rc;    // ModDown P3
     if (ck)  // P4+P5 Q, ModDown P4
-        KS_LAUNCH(st, "oc_comb_q", k_oc_comb_qw<true><<<gq, 256, 0, st>>>(T, oj));
+        KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qw<true, 2><<<gq, 256, 0, st>>>(T, oj)));
     else
-        KS_LAUNCH(st, "oc_comb_q", k_oc_comb_qw<false><<<gq, 256, 0, st>>>(T, oj));
+        KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qw<false, 2><<<gq, 256, 0, st>>>(T, oj)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(KS_ECUDA, std::string("OC whole-basis launch: ") + cudaGetErrorString(e));
     return KS_OK;
