@@ -338,12 +338,18 @@ typedef struct {
 
 /* End-to-end batched key switch from host memory: copy the inputs to the
  * device, key switch (results as ks_switch gives them), copy both outputs
- * back.  Jobs run in chunks of 4 (batched launches under KS_OC/KS_AUTO); the
- * copies of the next and previous chunk run on two library-owned streams
- * while a chunk computes (double-buffered device staging owned by the params
- * object), and everything is ordered before work later queued on `stream`.
- * Host buffers should be page-locked for the copies to overlap.  Returns
- * after queueing; synchronise `stream` before reading outputs. */
+ * back.  Jobs run in equal chunks of at most 8, each chunk one device batch
+ * (ks_switch_batch with the same dataflow; KS_AUTO uses the tuned schedule of
+ * the chunk's shape).  Copies in, compute and copies out run on three
+ * library-owned streams over double-buffered device staging owned by the
+ * params object, so chunk c computes while chunk c+1 is copied in and chunk
+ * c-1 is copied out, and consecutive calls overlap the same way.  The call's
+ * device work does NOT wait for work queued earlier on `stream` (the jobs read
+ * only host memory and keys, which are complete when created); `stream` is
+ * made to wait for every copy-out.  Host buffers should be page-locked for
+ * the copies to overlap.  Calls on one params object are serialised on the
+ * host.  Returns after queueing; synchronise `stream` before reading or
+ * reusing the host buffers. */
 int ks_switch_batch_host(const ks_params *params, uint32_t n, const ks_host_job *h_jobs,
                          ks_dataflow dataflow, ks_stream_t stream);
 

@@ -105,14 +105,14 @@ static int get_ws(ks_params *P, cudaStream_t st, bool need_D, Workspace **out)
 }
 
 // Double-buffered device staging of the host-memory batch path: jobs run in
-// chunks of kHostChunk; chunk c computes while chunk c+1 is copied in and
-// chunk c-1 is copied out.
-constexpr int kHostChunk = 4;
+// chunks of at most kHostChunk; chunk c computes while chunk c+1 is copied in
+// and chunk c-1 is copied out.
+constexpr int kHostChunk = 8;
 struct HostStage {
     u64 *din[2] = {nullptr, nullptr}, *dout0[2] = {nullptr, nullptr}, *dout1[2] = {nullptr, nullptr};
-    u64 *scratch = nullptr;  // Output-Centric scratch of one chunk
-    cudaStream_t s_in = nullptr, s_out = nullptr;
+    cudaStream_t s_in = nullptr, s_out = nullptr, s_comp = nullptr;
     cudaEvent_t h2d[2] = {}, comp[2] = {}, d2h[2] = {};
+    int next = 0;  // slot of the next chunk (alternation continues across calls)
 };
 
 static int get_stage(ks_params *P, HostStage **out)
@@ -130,9 +130,10 @@ static int get_stage(ks_params *P, HostStage **out)
             if (rc == KS_OK) rc = cuda_check(cudaEventCreateWithFlags(&h->comp[i], cudaEventDisableTiming), "event");
             if (rc == KS_OK) rc = cuda_check(cudaEventCreateWithFlags(&h->d2h[i], cudaEventDisableTiming), "event");
         }
-        if (rc == KS_OK) rc = ws_alloc(&h->scratch, (size_t)kHostChunk * oc_scratch_words(P->tables, P->nq));
+
         if (rc == KS_OK) rc = cuda_check(cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking), "stream");
         if (rc == KS_OK) rc = cuda_check(cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking), "stream");
+        if (rc == KS_OK) rc = cuda_check(cudaStreamCreateWithFlags(&h->s_comp, cudaStreamNonBlocking), "stream");
         if (rc != KS_OK) return rc;
     }
     *out = P->stage;
@@ -153,7 +154,6 @@ static void free_ws(ks_params *P)
         }
     if (P->stage) {
         HostStage *h = P->stage;
-        if (h->scratch) cudaFree(h->scratch);
         for (int i = 0; i < 2; ++i) {
             u64 *bufs[] = {h->din[i], h->dout0[i], h->dout1[i]};
             for (u64 *b : bufs)
@@ -164,6 +164,7 @@ static void free_ws(ks_params *P)
         }
         if (h->s_in) cudaStreamDestroy(h->s_in);
         if (h->s_out) cudaStreamDestroy(h->s_out);
+        if (h->s_comp) cudaStreamDestroy(h->s_comp);
         delete h;
         P->stage = nullptr;
     }
@@ -932,6 +933,28 @@ int ks_set_default_schedule(ks_params *P, const ks_schedule *schedule)
     return KS_OK;
 }
 
+}  // extern "C"
+
+namespace ks {
+// Chunk sizes of a host batch of n jobs.
+static std::vector<uint32_t> host_chunks(uint32_t n)
+{
+    std::vector<uint32_t> out;
+    uint32_t left = n;
+    while (left > 0) {
+        // equal chunks of at most kHostChunk (consecutive calls pipeline, so
+        // the copies at a call's ends are hidden behind the neighbours' work)
+        const uint32_t k = (left + kHostChunk - 1) / kHostChunk;
+        const uint32_t c = (left + k - 1) / k;
+        out.push_back(c);
+        left -= c;
+    }
+    return out;
+}
+}  // namespace ks
+
+extern "C" {
+
 int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs, ks_dataflow dataflow,
                          ks_stream_t stream)
 {
@@ -950,14 +973,19 @@ int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs
     std::lock_guard<std::mutex> g(PP->host_mu);
     HostStage *h = nullptr;
     if ((rc = get_stage(PP, &h)) != KS_OK) return rc;
-    cudaStream_t cs = (cudaStream_t)stream;
+    // The chunks compute on the stage's own stream: host-buffer jobs read no
+    // device data of the caller (keys are complete when their constructors
+    // return), so they need not wait for earlier work on the caller's stream, and consecutive calls pipeline (the next call's
+    // copy-in and compute overlap this call's copy-out).  The caller's stream
+    // waits for every copy-out at the end.
+    cudaStream_t cs = h->s_comp, caller = (cudaStream_t)stream;
     const size_t N = P->N;
     const size_t slot_words = (size_t)P->nq * N;
-    const size_t scr = oc_scratch_words(P->tables, P->nq);
-    int c = 0;
-    for (uint32_t i0 = 0; i0 < n; i0 += kHostChunk, ++c) {
-        const int s = c & 1;
-        const uint32_t m = std::min<uint32_t>(kHostChunk, n - i0);
+    const std::vector<uint32_t> chunks = host_chunks(n);
+    uint32_t i0 = 0;
+    for (size_t c = 0; c < chunks.size(); i0 += chunks[c], ++c) {
+        const int s = (int)((h->next + c) & 1);
+        const uint32_t m = chunks[c];
         // copy the chunk in once the chunk that last used this slot is computed
         rc = cuda_check(cudaStreamWaitEvent(h->s_in, h->comp[s], 0), "wait");
         for (uint32_t k = 0; k < m && rc == KS_OK; ++k) {
@@ -971,21 +999,23 @@ int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs
         if (rc == KS_OK) rc = cuda_check(cudaStreamWaitEvent(cs, h->h2d[s], 0), "wait");
         if (rc == KS_OK) rc = cuda_check(cudaStreamWaitEvent(cs, h->d2h[s], 0), "wait");
         if (rc == KS_OK) {
-            if (dataflow == KS_MP || dataflow == KS_DC) {
-                for (uint32_t k = 0; k < m && rc == KS_OK; ++k) {
-                    const ks_host_job &j = jobs[i0 + k];
-                    rc = switch_one(PP, j.key, j.level_towers, h->din[s] + k * slot_words,
-                                    h->dout0[s] + k * slot_words, h->dout1[s] + k * slot_words, dataflow, cs);
-                }
-            } else {
-                OcJob oj[kHostChunk];
-                for (uint32_t k = 0; k < m; ++k) {
-                    const ks_host_job &j = jobs[i0 + k];
-                    oj[k] = oc_job(P, j.key, (int)j.level_towers, h->din[s] + k * slot_words,
-                                   h->dout0[s] + k * slot_words, h->dout1[s] + k * slot_words, h->scratch + k * scr);
-                }
-                rc = launch_oc(P->tables, (int)m, oj, P->sched.oc_variant, cs);
+            // the chunk as a device batch (its schedule: tuned for KS_AUTO)
+            ks_job dj[kHostChunk];
+            uint64_t lv = 0;
+            for (uint32_t k = 0; k < m; ++k) {
+                const ks_host_job &j = jobs[i0 + k];
+                dj[k] = ks_job{j.key, j.level_towers, h->din[s] + k * slot_words, h->dout0[s] + k * slot_words,
+                               h->dout1[s] + k * slot_words};
+                lv += j.level_towers;
             }
+            ks_schedule sc = P->sched;
+            if (dataflow == KS_MP || dataflow == KS_DC) sc.dataflow = dataflow;
+            if (dataflow == KS_OC) sc.dataflow = KS_OC;
+            if (dataflow == KS_AUTO) {
+                auto it = P->tune.find(tune_signature(m, (uint32_t)(lv / m)));
+                if (it != P->tune.end()) sc = it->second;
+            }
+            rc = run_batch(PP, m, dj, sc, cs);
         }
         if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->comp[s], cs), "record");
         // copy out
@@ -1002,9 +1032,10 @@ int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs
         if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->d2h[s], h->s_out), "record");
         if (rc) return rc;
     }
+    h->next = (int)((h->next + chunks.size()) & 1);
     // later work on the caller's stream is ordered after every copy-out
     for (int s = 0; s < 2; ++s)
-        if ((rc = cuda_check(cudaStreamWaitEvent(cs, h->d2h[s], 0), "wait")) != KS_OK) return rc;
+        if ((rc = cuda_check(cudaStreamWaitEvent(caller, h->d2h[s], 0), "wait")) != KS_OK) return rc;
     return KS_OK;
 }
 
