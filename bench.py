@@ -94,6 +94,8 @@ def class_work(nact=NQ):
         "ntt_inv_col": ("bfly", inv_limbs * half * LA, 2 * inv_limbs * LIMB),
         "ntt_fwd_col": ("bfly", fwd_limbs * half * LA, 2 * fwd_limbs * LIMB),
         "ntt_fwd_row": ("bfly", fwd_limbs * half * LB, 2 * fwd_limbs * LIMB),
+        "ntt_inv_cl": ("bfly", inv_limbs * half * LOGN, 2 * inv_limbs * LIMB),
+        "ntt_fwd_cl": ("bfly", fwd_limbs * half * LOGN, 2 * fwd_limbs * LIMB),
         "bconv_up": ("mac", sum(a * (K + nact - a) for a in al) * N, (2 * nact + nd * K + q_modup) * LIMB),
         "bconv_down": ("mac", 2 * K * nact * N, (2 * K + 2 * nact) * LIMB),
         "oc_comb_p": ("hbm", 2 * nd * K * N, (3 * nd * K + 2 * K) * LIMB),
@@ -124,11 +126,11 @@ def mixed_batch(P, keys, stream, timed, world, steps, seed, n_jobs=64):
         jobs.append((keys[k], lv, d, ks.empty((lv, N)), ks.empty((lv, N))))
     tuned, _ = P.autotune(jobs, reps=2, stream=stream)
     t_auto = timed(lambda: P.switch_batch(jobs, "AUTO", stream), steps, 2)
-    by_key = ks.Schedule(tuned.dataflow, tuned.oc_variant, tuned.chunk, 2)
+    by_key = ks.Schedule(tuned.dataflow, tuned.oc_variant, tuned.chunk, 2, tuned.ntt, tuned.bconv)
     t_key = timed(lambda: P.switch_batch_sched(jobs, by_key, stream), steps, 2)
     return {"value": round(world * n_jobs * steps / (t_auto / 1e3), 2), "unit": "key-switches/s",
             "jobs": n_jobs, "levels": "uniform 4..24 of 24", "keys": len(keys),
-            "schedule": list(tuned.as_tuple()),
+            "schedule": list(tuned.as_tuple() + tuned.impl()),
             "grouped_by_key": round(world * n_jobs * steps / (t_key / 1e3), 2),
             "mean_level": round(sum(levels) / n_jobs, 2)}
 
@@ -172,7 +174,7 @@ def table3_sets(stream, timed, world, steps, seed, batch=4):
         t = timed(lambda: P3.switch_batch(jobs3, "AUTO", stream), steps, 2)
         out[name] = {"value": round(world * batch * steps / (t / 1e3), 2), "unit": "key-switches/s",
                      "logN": logN, "q_towers": nq, "p_towers": kp, "dnum": dnum, "batch": batch,
-                     "schedule": list(tuned3.as_tuple())}
+                     "schedule": list(tuned3.as_tuple() + tuned3.impl())}
         del jobs3, keys3, P3
         torch.cuda.empty_cache()
     return out
@@ -336,8 +338,11 @@ def main():
     if args.schedule:
         tuned, tune_ms = ks.Schedule(*[int(x) for x in args.schedule.split(",")]), []
         P.tune_cache_put(B, NQ, tuned)
+        impl_ms = []
     else:
         tuned, tune_ms = P.autotune(jobs, reps=2, stream=stream)
+        # the second stage's timings of the winning structure, for the record
+        _, impl_ms = P.autotune_impl(jobs, tuned, reps=2, stream=stream)
     if args.dataflow == "OC":
         step = lambda: P.switch_batch(jobs, "AUTO", stream)  # noqa: E731
     else:
@@ -390,7 +395,7 @@ def main():
     t_c = timed(lambda: P.switch_batch_sched(cjobs, ctuned, stream), args.steps, 2)
     compressed = {"value": round(world * B * args.steps / (t_c / 1e3), 2), "unit": UNIT,
                   "key_bytes": ckeys[0].nbytes, "full_key_bytes": keys[0].nbytes,
-                  "schedule": list(ctuned.as_tuple())}
+                  "schedule": list(ctuned.as_tuple() + ctuned.impl())}
     del cjobs, ckeys
 
     # ---- the paper's parameter sets (Table III): 4 ciphertexts a step, own keys
@@ -485,9 +490,13 @@ def main():
             "table3_sets": table3,
             "hoisted_rotations": hoisted,
             "compressed_keys": compressed,
-            "schedule": {"tuned": list(tuned.as_tuple()), "fields": "dataflow, oc_variant, chunk, order",
+            "schedule": {"tuned": list(tuned.as_tuple() + tuned.impl()),
+                         "fields": "dataflow, oc_variant, chunk, order, ntt, bconv",
                          "source": "fixed by --schedule" if args.schedule else "ks_autotune",
-                         "candidates_ms": [round(x, 3) for x in tune_ms]},
+                         "candidates_ms": [round(x, 3) for x in tune_ms],
+                         "impl_ms": dict(zip(["two-pass NTT, tensor-core BConv", "cluster NTT, tensor-core BConv",
+                                              "two-pass NTT, CUDA-core BConv", "cluster NTT, CUDA-core BConv"],
+                                             [round(x, 3) for x in impl_ms]))},
             "hbm_roofline": {"achieved": round(hbm_achieved, 1), "peak": hbm_gbs, "unit": "GB/s",
                              "frac": round(hbm_achieved / hbm_gbs, 4), "basis": f"{peak_src} copy bandwidth",
                              "algorithmic_bytes_per_ks": ALG_BYTES_PER_KS},

@@ -102,9 +102,14 @@ int ks_params_info(const ks_params *params, uint64_t *h_q, uint64_t *h_p,
  *     and joined back to the caller's stream (the memory-bound combine
  *     kernels of one part then overlap the integer-bound passes of another);
  *     1 keeps every launch on the caller's stream.
+ *   KS_OPT_NTT_CLUSTER (default 0): run each NTT (forward and inverse) as
+ *     one launch in which a thread-block cluster transforms a limb, its
+ *     column and row passes exchanging the limb through distributed shared
+ *     memory, instead of two launches through device memory.  Ring degrees
+ *     without a cluster form (2^13, 2^17) keep the two launches.
  * Returns KS_EINVAL for an unknown option or value.  Not thread-safe with
  * concurrent calls on the same params object. */
-enum { KS_OPT_BCONV_TENSOR = 1, KS_OPT_BATCH_LANES = 2 };
+enum { KS_OPT_BCONV_TENSOR = 1, KS_OPT_BATCH_LANES = 2, KS_OPT_NTT_CLUSTER = 3 };
 int ks_params_set_option(ks_params *params, int option, int value);
 
 /* Device-side status of the library on the params object's GPU: bit 0 is set
@@ -253,10 +258,19 @@ typedef struct {
     int32_t dataflow;    /* KS_MP, KS_DC or KS_OC                                  */
     int32_t oc_variant;  /* KS_OC: 0 = fused row kernels (row pass, key product,
                             ModDown step in one kernel per row block), 1 = split
-                            (plain row pass, then a streaming combine kernel)     */
+                            (plain row pass, then a streaming combine kernel),
+                            2 = whole basis (one base conversion and one NTT
+                            launch over every raised limb, then the combines)  */
     int32_t chunk;       /* KS_OC: jobs per batched launch group, 1..64           */
     int32_t order;       /* 0 = jobs in the given order, 1 = grouped by level
                             (descending), 2 = grouped by key                     */
+    int32_t ntt;         /* NTT form: 0 = two launches (column pass, row pass),
+                            1 = one cluster launch per NTT (KS_OPT_NTT_CLUSTER),
+                            2 = the same with CTAs twice as wide; -1 = the
+                            parameter set's option                               */
+    int32_t bconv;       /* base conversion engine: 0 = CUDA cores, 1 = tensor
+                            cores where supported; -1 = the parameter set's
+                            option (KS_OPT_BCONV_TENSOR)                         */
 } ks_schedule;
 
 /* Batched key switch with an explicit schedule (see ks_schedule). */
@@ -272,20 +286,31 @@ int ks_set_default_schedule(ks_params *params, const ks_schedule *schedule);
  * Autotuning (schedule search by measurement) and its cache.
  * ------------------------------------------------------------------- */
 
-/* The candidate schedules the autotuner measures, in a fixed order (the
- * same order the learned cost model predicts).  *n_out = count; up to max
- * are written. */
+/* The structural candidate schedules the autotuner measures first, in a
+ * fixed order (the order the learned cost model predicts): dataflow, OC
+ * variant, launch group and job order, each with ntt = bconv = -1 (the
+ * parameter set's options).  *n_out = count; up to max are written. */
 int ks_tune_candidates(const ks_params *params, uint32_t max, ks_schedule *out, uint32_t *n_out);
 
-/* Time every candidate on this batch (each: one untimed run, then the best
- * of `reps` timed runs with CUDA events on `stream`; the jobs' outputs are
- * overwritten -- every schedule writes the same values).  ms_out[i] gets
- * candidate i's time in ms (max entries).  The fastest schedule is written
- * to *best and stored in the params' tuning cache under this batch's
- * signature (job count rounded up to a power of two, mean level rounded
- * to a multiple of 4), where KS_AUTO finds it.  Synchronises `stream`. */
+/* Autotune a batch in two stages (each timing: one untimed run, then the
+ * best of `reps` timed runs with CUDA events on `stream`; the jobs' outputs
+ * are overwritten -- every schedule writes the same values):
+ *   1. every structural candidate (ks_tune_candidates); ms_out[i] gets
+ *      candidate i's time in ms (max entries);
+ *   2. the fastest structure under each implementation pair (ntt, bconv) in
+ *      {(0,1), (1,1), (0,0), (1,0)} (ks_autotune_impl).
+ * The fastest schedule, with explicit ntt and bconv, is written to *best and
+ * stored in the params' tuning cache under this batch's signature (job count
+ * rounded up to a power of two, mean level rounded to a multiple of 4),
+ * where KS_AUTO finds it.  Synchronises `stream`. */
 int ks_autotune(ks_params *params, uint32_t n, const ks_job *h_jobs, uint32_t reps, ks_stream_t stream,
                 uint32_t max, float *ms_out, ks_schedule *best);
+
+/* Stage 2 alone: time `base` under the four implementation pairs above
+ * (ms_out[4] in that order, may be NULL) and write the fastest to *best.
+ * Does not touch the tuning cache.  Synchronises `stream`. */
+int ks_autotune_impl(ks_params *params, uint32_t n, const ks_job *h_jobs, uint32_t reps, ks_stream_t stream,
+                     const ks_schedule *base, float *ms_out, ks_schedule *best);
 
 /* Tuning cache: store / look up the schedule of a signature (n jobs, mean
  * level); lookup returns KS_OK and fills *out, or KS_EINVAL if absent. */

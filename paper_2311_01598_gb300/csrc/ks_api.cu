@@ -185,9 +185,9 @@ static int active_digits(const ks_params *P, int nact) { return (nact + P->alpha
 static const ulonglong2 *pre_level(const ks_params *P, int nact) { return P->d_up_pre_lvl + (size_t)(nact - 1) * P->nq; }
 
 // ------------------------------------------------------------------ ModDown
-static int run_moddown(const ks_params *P, Workspace *w, int nact, int npoly, u64 *out0, u64 *out1, cudaStream_t st)
+static int run_moddown(const ks_params *P, const Tables &T, Workspace *w, int nact, int npoly, u64 *out0, u64 *out1,
+                       cudaStream_t st)
 {
-    const Tables &T = P->tables;
     const size_t N = P->N;
     const int nt = nact + P->kp;
     int rc;
@@ -210,10 +210,9 @@ static int run_moddown(const ks_params *P, Workspace *w, int nact, int npoly, u6
 
 // ------------------------------------------------------------------ MP
 // Max-Parallel: each stage over all towers, intermediates in device memory.
-static int run_mp(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, Workspace *w,
-                  cudaStream_t st)
+static int run_mp(const ks_params *P, const Tables &T, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1,
+                  Workspace *w, cudaStream_t st)
 {
-    const Tables &T = P->tables;
     const size_t N = P->N;
     const int nt = nact + P->kp;
     const int nd = active_digits(P, nact);
@@ -231,7 +230,7 @@ static int run_mp(const ks_params *P, const ks_key *K, int nact, const u64 *d, u
     if ((rc = launch_ntt_fwd(T, one_map(mD, nd * nt), false, st)) != KS_OK) return rc;
     // P4 + P5: key product summed over digits.
     if ((rc = launch_apply_key(T, nact, 0, nd, d, w->D, (size_t)nt * N, key_view(K), w->cp, false, st)) != KS_OK) return rc;
-    return run_moddown(P, w, nact, 2, out0, out1, st);
+    return run_moddown(P, T, w, nact, 2, out0, out1, st);
 }
 
 // ------------------------------------------------------------------ hoisted rotations
@@ -308,10 +307,9 @@ static int run_hoisted(ks_params *P, uint32_t R, const ks_key *const *keys, cons
 // ------------------------------------------------------------------ DC
 // Digit-Centric: ModUp P1..P5 for one digit at a time, partial sums of c'
 // accumulated in device memory, then ModDown.
-static int run_dc(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, Workspace *w,
-                  cudaStream_t st)
+static int run_dc(const ks_params *P, const Tables &T, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1,
+                  Workspace *w, cudaStream_t st)
 {
-    const Tables &T = P->tables;
     const int nt = nact + P->kp;
     const int nd = active_digits(P, nact);
     int rc;
@@ -328,7 +326,7 @@ static int run_dc(const ks_params *P, const ks_key *K, int nact, const u64 *d, u
         if ((rc = launch_ntt_fwd(T, one_map(mD, nt), false, st)) != KS_OK) return rc;
         if ((rc = launch_apply_key(T, nact, j, j + 1, d, w->D, 0, key_view(K), w->cp, j > 0, st)) != KS_OK) return rc;
     }
-    return run_moddown(P, w, nact, 2, out0, out1, st);
+    return run_moddown(P, T, w, nact, 2, out0, out1, st);
 }
 
 // ------------------------------------------------------------------ OC
@@ -350,11 +348,11 @@ static OcJob oc_job(const ks_params *P, const ks_key *K, int nact, const u64 *d,
     return J;
 }
 
-static int run_oc(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, Workspace *w,
-                  cudaStream_t st)
+static int run_oc(const ks_params *P, const Tables &T, int oc_variant, const ks_key *K, int nact, const u64 *d, u64 *out0,
+                  u64 *out1, Workspace *w, cudaStream_t st)
 {
     OcJob J = oc_job(P, K, nact, d, out0, out1, w->oc);
-    return launch_oc(P->tables, 1, &J, P->sched.oc_variant, st);
+    return launch_oc(T, 1, &J, oc_variant, st);
 }
 
 static int check_params(const ks_params *P)
@@ -659,8 +657,24 @@ static int keygen_impl(const ks_params *P, const int8_t *h_s, const int64_t *h_s
     return KS_OK;
 }
 
-static int switch_one(ks_params *P, const ks_key *K, uint32_t nact, const uint64_t *d, uint64_t *o0, uint64_t *o1,
-                      ks_dataflow df, cudaStream_t st)
+// Tables of one call: the parameter set's tables with the schedule's
+// implementation choices applied (-1 keeps the parameter set's option).
+static Tables call_tables(const ks_params *P, const ks_schedule &sc)
+{
+    Tables T = P->tables;
+    if (sc.bconv == 0) {
+        T.up_tc = nullptr;
+        T.dn_tc = nullptr;
+    } else if (sc.bconv == 1) {
+        T.up_tc = P->d_up_tc;  // null where the parameter set has no tensor-core form
+        T.dn_tc = P->d_dn_tc;
+    }
+    if (sc.ntt >= 0) T.ntt_cluster = sc.ntt;
+    return T;
+}
+
+static int switch_one(ks_params *P, const Tables &T, int oc_variant, const ks_key *K, uint32_t nact, const uint64_t *d,
+                      uint64_t *o0, uint64_t *o1, ks_dataflow df, cudaStream_t st)
 {
     Workspace *w = nullptr;
     const ks_dataflow eff = df == KS_AUTO ? (ks_dataflow)P->sched.dataflow : df;
@@ -668,10 +682,10 @@ static int switch_one(ks_params *P, const ks_key *K, uint32_t nact, const uint64
     if (rc) return rc;
     if (df == KS_AUTO) df = (ks_dataflow)P->sched.dataflow;
     switch (df) {
-    case KS_MP: return run_mp(P, K, (int)nact, d, o0, o1, w, st);
-    case KS_DC: return run_dc(P, K, (int)nact, d, o0, o1, w, st);
+    case KS_MP: return run_mp(P, T, K, (int)nact, d, o0, o1, w, st);
+    case KS_DC: return run_dc(P, T, K, (int)nact, d, o0, o1, w, st);
     case KS_OC:
-    case KS_AUTO: return run_oc(P, K, (int)nact, d, o0, o1, w, st);
+    case KS_AUTO: return run_oc(P, T, oc_variant, K, (int)nact, d, o0, o1, w, st);
     }
     return fail(KS_EINVAL, "unknown dataflow");
 }
@@ -699,8 +713,8 @@ int ks_switch(const ks_params *P, const ks_key *K, uint32_t level_towers, const 
     if ((rc = check_job(P, K, level_towers, d_in, d_out0, d_out1)) != KS_OK) return rc;
     if ((int)dataflow < 0 || (int)dataflow > 3) return fail(KS_EINVAL, "unknown dataflow");
     if ((rc = set_device(P)) != KS_OK) return rc;
-    return switch_one(const_cast<ks_params *>(P), K, level_towers, d_in, d_out0, d_out1, dataflow,
-                      (cudaStream_t)stream);
+    return switch_one(const_cast<ks_params *>(P), call_tables(P, P->sched), P->sched.oc_variant, K, level_towers, d_in,
+                      d_out0, d_out1, dataflow, (cudaStream_t)stream);
 }
 
 int ks_params_set_option(ks_params *P, int option, int value)
@@ -712,6 +726,11 @@ int ks_params_set_option(ks_params *P, int option, int value)
         P->bconv_tensor = value;
         P->tables.up_tc = value ? P->d_up_tc : nullptr;
         P->tables.dn_tc = value ? P->d_dn_tc : nullptr;
+        return KS_OK;
+    }
+    if (option == KS_OPT_NTT_CLUSTER && value >= 0 && value <= 2) {
+        P->ntt_cluster = value;
+        P->tables.ntt_cluster = value;
         return KS_OK;
     }
     if (option == KS_OPT_BATCH_LANES && value >= 1 && value <= 4) {
@@ -763,10 +782,13 @@ int check_schedule(const ks_schedule *sc)
     if (sc->oc_variant < 0 || sc->oc_variant > 2) return fail(KS_EINVAL, "schedule oc_variant must be 0, 1 or 2");
     if (sc->chunk < 1 || sc->chunk > kMaxBatch) return fail(KS_EINVAL, "schedule chunk must be in 1..64");
     if (sc->order < 0 || sc->order > 2) return fail(KS_EINVAL, "schedule order must be 0, 1 or 2");
+    if (sc->ntt < -1 || sc->ntt > 2) return fail(KS_EINVAL, "schedule ntt must be -1, 0, 1 or 2");
+    if (sc->bconv < -1 || sc->bconv > 1) return fail(KS_EINVAL, "schedule bconv must be -1, 0 or 1");
     return KS_OK;
 }
 
-static int run_oc_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st);
+static int run_oc_batch(ks_params *P, const Tables &T, uint32_t n, const ks_job *jobs, const ks_schedule &sc,
+                        cudaStream_t st);
 constexpr uint32_t kLaneJobs = 4;  // fewest jobs worth a lane of their own
 
 static int lane_streams(ks_params *P)
@@ -797,10 +819,12 @@ int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &s
                          [&](uint32_t a, uint32_t b) { return jobs[a].level_towers > jobs[b].level_towers; });
     else if (sc.order == 2)
         std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) { return jobs[a].key < jobs[b].key; });
+    const Tables T = call_tables(P, sc);
     if (sc.dataflow == KS_MP || sc.dataflow == KS_DC) {
         for (uint32_t i : idx) {
             const ks_job &j = jobs[i];
-            rc = switch_one(P, j.key, j.level_towers, j.d_in, j.d_out0, j.d_out1, (ks_dataflow)sc.dataflow, st);
+            rc = switch_one(P, T, sc.oc_variant, j.key, j.level_towers, j.d_in, j.d_out0, j.d_out1,
+                            (ks_dataflow)sc.dataflow, st);
             if (rc) return rc;
         }
         return KS_OK;
@@ -823,7 +847,7 @@ int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &s
         for (int l = 0; l < lanes; ++l) {
             const uint32_t cnt = n / lanes + ((uint32_t)l < n % lanes ? 1 : 0);
             if ((rc = cuda_check(cudaStreamWaitEvent(P->lane_st[l], P->lane_ev[4], 0), "lane fork")) != KS_OK) return rc;
-            if ((rc = run_oc_batch(P, cnt, sorted.data() + at, one, P->lane_st[l])) != KS_OK) return rc;
+            if ((rc = run_oc_batch(P, T, cnt, sorted.data() + at, one, P->lane_st[l])) != KS_OK) return rc;
             if ((rc = cuda_check(cudaEventRecord(P->lane_ev[l], P->lane_st[l]), "lane join")) != KS_OK) return rc;
             if ((rc = cuda_check(cudaStreamWaitEvent(st, P->lane_ev[l], 0), "lane join")) != KS_OK) return rc;
             at += cnt;
@@ -832,11 +856,12 @@ int run_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &s
     }
     std::vector<ks_job> sorted(n);
     for (uint32_t i = 0; i < n; ++i) sorted[i] = jobs[idx[i]];
-    return run_oc_batch(P, n, sorted.data(), sc, st);
+    return run_oc_batch(P, T, n, sorted.data(), sc, st);
 }
 
 // Output-Centric batch in the given order on one stream.
-static int run_oc_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, cudaStream_t st)
+static int run_oc_batch(ks_params *P, const Tables &T, uint32_t n, const ks_job *jobs, const ks_schedule &sc,
+                        cudaStream_t st)
 {
     int rc;
     Workspace *w = nullptr;
@@ -867,7 +892,7 @@ static int run_oc_batch(ks_params *P, uint32_t n, const ks_job *jobs, const ks_s
     }
     for (uint32_t i0 = 0; i0 < n; i0 += (uint32_t)sc.chunk) {
         const int m = (int)std::min<uint32_t>((uint32_t)sc.chunk, n - i0);
-        if ((rc = launch_oc(P->tables, m, oj.data() + i0, sc.oc_variant, st)) != KS_OK) return rc;
+        if ((rc = launch_oc(T, m, oj.data() + i0, sc.oc_variant, st)) != KS_OK) return rc;
     }
     return KS_OK;
 }
@@ -1136,7 +1161,7 @@ int ks_moddown(const ks_params *P, uint32_t level_towers, const uint64_t *d_cp, 
     // fold the ModDown factors in (the key normally carries them)
     LimbMap ms{d_cp, w->cp, nullptr, nt, 0, 0, 0, nact, -1};
     if ((rc = launch_scale(P->tables, one_map(ms, nt), P->d_plain_sc, st)) != KS_OK) return rc;
-    return run_moddown(P, w, nact, 1, d_out, d_out, st);
+    return run_moddown(P, P->tables, w, nact, 1, d_out, d_out, st);
 }
 
 }  // extern "C"

@@ -75,6 +75,7 @@ struct Tables {
     const uint4 *up_tc;
     const int *up_tc_lvl;
     const uint4 *dn_tc;
+    int ntt_cluster;  // host side: NTTs as one cluster launch where supported
     int logN;
     int nq, kp, alpha, ndig;
 };
@@ -106,6 +107,7 @@ struct ks_params {
     uint4 *d_up_tc = nullptr, *d_dn_tc = nullptr;  // tensor-core BConv slabs
     int *d_up_tc_lvl = nullptr;
     int bconv_tensor = 1;                // use the tensor-core BConv where supported
+    int ntt_cluster = 0;                 // NTTs as one cluster launch where supported
     int batch_lanes = 2;                 // internal streams a large Output-Centric batch is split over
     cudaStream_t lane_st[4] = {};        // created on first use
     cudaEvent_t lane_ev[5] = {};
@@ -118,7 +120,7 @@ struct ks_params {
     std::mutex mu;
     std::map<void *, ks::Workspace *> ws;
     // default schedule (KS_OC / KS_AUTO without a tuned entry)
-    ks_schedule sched{KS_OC, 1, 64, 0};
+    ks_schedule sched{KS_OC, 1, 64, 0, -1, -1};
     // tuning cache: (job-count bucket, mean-level bucket) -> schedule
     std::map<std::pair<uint32_t, uint32_t>, ks_schedule> tune;
     // double-buffered device staging of ks_switch_batch_host

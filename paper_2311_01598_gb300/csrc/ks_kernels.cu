@@ -280,6 +280,10 @@ int launch_inv_col(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaS
 int launch_ntt_fwd(const Tables &T, const LimbMaps &m, bool canonical, cudaStream_t st)
 {
     if (m.n == 0 || m.pre[m.n] == 0) return KS_OK;
+    if (T.ntt_cluster) {
+        const int rc = launch_ntt_fwd_cluster(T, m, canonical, st);
+        if (rc != KS_EUNSUPPORTED) return rc;
+    }
     KS_DISPATCH_LOGN(T.logN, fwd_col_S, T, m, st);
     LimbMaps m2 = m;
     for (int j = 0; j < m2.n; ++j) m2.m[j].src = m2.m[j].dst;
@@ -290,6 +294,10 @@ int launch_ntt_fwd(const Tables &T, const LimbMaps &m, bool canonical, cudaStrea
 int launch_ntt_inv(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaStream_t st)
 {
     if (m.n == 0 || m.pre[m.n] == 0) return KS_OK;
+    if (T.ntt_cluster) {
+        const int rc = launch_ntt_inv_cluster(T, m, any_scale(m) ? 1 : scale_by_ninv ? 2 : 0, st);
+        if (rc != KS_EUNSUPPORTED) return rc;
+    }
     KS_DISPATCH_LOGN(T.logN, inv_row_S, T, m, st);
     LimbMaps m2 = m;
     for (int j = 0; j < m2.n; ++j) m2.m[j].src = m2.m[j].dst;

@@ -67,6 +67,14 @@ int launch_ntt_fwd(const Tables &T, const LimbMaps &m, bool canonical, cudaStrea
 // place); the column pass multiplies by the per-entry scale when the job's
 // map has one, or by N^-1 when scale_by_ninv; output canonical.  Input below 2q.
 int launch_ntt_inv(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaStream_t st);
+// One-launch forms over thread-block clusters (ks_ntt_cluster.cu): the same
+// contracts and bit-identical outputs; sc of the inverse: 0 none, 1 the
+// job's per-entry scale, 2 N^-1.  They return KS_EUNSUPPORTED, launching
+// nothing, when the ring degree's shape or the device has no cluster form;
+// launch_ntt_fwd/inv use them when T.ntt_cluster is set and fall back.
+bool ntt_cluster_shape(int logN);
+int launch_ntt_fwd_cluster(const Tables &T, const LimbMaps &m, bool canonical, cudaStream_t st);
+int launch_ntt_inv_cluster(const Tables &T, const LimbMaps &m, int sc, cudaStream_t st);
 // Single passes.
 int launch_fwd_col(const Tables &T, const LimbMaps &m, cudaStream_t st);
 int launch_inv_col(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaStream_t st);

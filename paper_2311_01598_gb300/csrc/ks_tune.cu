@@ -2,6 +2,7 @@
 // schedules of a batch with CUDA events, a per-parameter-set cache of the
 // winners (used by KS_AUTO), its text persistence, and synthetic keys for
 // tuning runs.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -15,18 +16,63 @@
 namespace ks {
 
 // Candidate order is part of the interface: the learned cost model predicts
-// one time per candidate in this order.
+// one time per structural candidate in this order.
 static std::vector<ks_schedule> candidates()
 {
     std::vector<ks_schedule> c;
-    c.push_back({KS_MP, 0, 1, 0});
-    c.push_back({KS_DC, 0, 1, 0});
-    c.push_back({KS_OC, 0, 64, 0});
-    for (int ch : {1, 8, 64}) c.push_back({KS_OC, 1, ch, 0});
-    for (int ch : {1, 8, 16, 64}) c.push_back({KS_OC, 2, ch, 0});
-    c.push_back({KS_OC, 1, 64, 1});
-    c.push_back({KS_OC, 2, 64, 1});
+    c.push_back({KS_MP, 0, 1, 0, -1, -1});
+    c.push_back({KS_DC, 0, 1, 0, -1, -1});
+    c.push_back({KS_OC, 0, 64, 0, -1, -1});
+    for (int ch : {1, 8, 64}) c.push_back({KS_OC, 1, ch, 0, -1, -1});
+    for (int ch : {1, 8, 16, 64}) c.push_back({KS_OC, 2, ch, 0, -1, -1});
+    c.push_back({KS_OC, 1, 64, 1, -1, -1});
+    c.push_back({KS_OC, 2, 64, 1, -1, -1});
     return c;
+}
+
+// Implementation pairs (ntt, bconv) of the second stage, in ms_out order.
+static const int kImpl[4][2] = {{0, 1}, {1, 1}, {0, 0}, {1, 0}};
+
+// Best of reps timed runs of one schedule (after one untimed run).
+static int time_schedule(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, uint32_t reps,
+                         cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float *ms)
+{
+    int rc = run_batch(P, n, jobs, sc, st);  // untimed: scratch allocation, caches
+    float m = 1e30f;
+    for (uint32_t r = 0; r < reps && rc == KS_OK; ++r) {
+        cudaEventRecord(e0, st);
+        rc = run_batch(P, n, jobs, sc, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(KS_ECUDA, "ks_autotune: device error while timing");
+        }
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        m = std::min(m, t);
+    }
+    *ms = m;
+    return rc;
+}
+
+static int tune_impl(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps, cudaStream_t st, cudaEvent_t e0,
+                     cudaEvent_t e1, const ks_schedule &base, float *ms_out, ks_schedule *best)
+{
+    float best_ms = 1e30f;
+    for (int i = 0; i < 4; ++i) {
+        ks_schedule sc = base;
+        sc.ntt = kImpl[i][0];
+        sc.bconv = kImpl[i][1];
+        float m = 0.f;
+        const int rc = time_schedule(P, n, jobs, sc, reps, st, e0, e1, &m);
+        if (rc != KS_OK) return rc;
+        if (ms_out) ms_out[i] = m;
+        if (m < best_ms) {
+            best_ms = m;
+            *best = sc;
+        }
+    }
+    return KS_OK;
 }
 
 std::pair<uint32_t, uint32_t> tune_signature(uint32_t n, uint32_t mean_level)
@@ -72,46 +118,49 @@ int ks_tune_candidates(const ks_params *P, uint32_t max, ks_schedule *out, uint3
     return KS_OK;
 }
 
+static int tune_events(ks_params *P, cudaEvent_t *e0, cudaEvent_t *e1)
+{
+    if (cudaSetDevice(P->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "cudaSetDevice failed");
+    }
+    if (cudaEventCreate(e0) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "ks_autotune: event creation failed");
+    }
+    if (cudaEventCreate(e1) != cudaSuccess) {
+        cudaGetLastError();
+        cudaEventDestroy(*e0);
+        return fail(KS_ECUDA, "ks_autotune: event creation failed");
+    }
+    return KS_OK;
+}
+
 int ks_autotune(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps, ks_stream_t stream, uint32_t max,
                 float *ms_out, ks_schedule *best)
 {
     int rc = check_batch(P, n, jobs);
     if (rc) return rc;
     if (n == 0 || reps < 1 || !best) return fail(KS_EINVAL, "ks_autotune: need n >= 1, reps >= 1 and best");
-    if (cudaSetDevice(P->device) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(KS_ECUDA, "cudaSetDevice failed");
-    }
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(KS_ECUDA, "ks_autotune: event creation failed");
-    }
+    if ((rc = tune_events(P, &e0, &e1)) != KS_OK) return rc;
+    // stage 1: structure
     std::vector<ks_schedule> c = candidates();
     float best_ms = 1e30f;
+    ks_schedule base = c[0];
     for (size_t i = 0; i < c.size() && rc == KS_OK; ++i) {
-        rc = run_batch(P, n, jobs, c[i], st);  // untimed: scratch allocation, caches
-        float m = 1e30f;
-        for (uint32_t r = 0; r < reps && rc == KS_OK; ++r) {
-            cudaEventRecord(e0, st);
-            rc = run_batch(P, n, jobs, c[i], st);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess) {
-                cudaGetLastError();
-                rc = fail(KS_ECUDA, "ks_autotune: device error while timing");
-                break;
-            }
-            float t = 0.f;
-            cudaEventElapsedTime(&t, e0, e1);
-            m = std::min(m, t);
-        }
+        float m = 0.f;
+        rc = time_schedule(P, n, jobs, c[i], reps, st, e0, e1, &m);
+        if (rc != KS_OK) break;
         if (i < max && ms_out) ms_out[i] = m;
         if (m < best_ms) {
             best_ms = m;
-            *best = c[i];
+            base = c[i];
         }
     }
+    // stage 2: implementation of the fastest structure
+    if (rc == KS_OK) rc = tune_impl(P, n, jobs, reps, st, e0, e1, base, nullptr, best);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != KS_OK) return rc;
@@ -119,6 +168,21 @@ int ks_autotune(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps, ks_
     for (uint32_t i = 0; i < n; ++i) lv += jobs[i].level_towers;
     P->tune[tune_signature(n, (uint32_t)(lv / n))] = *best;
     return KS_OK;
+}
+
+int ks_autotune_impl(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps, ks_stream_t stream,
+                     const ks_schedule *base, float *ms_out, ks_schedule *best)
+{
+    int rc = check_batch(P, n, jobs);
+    if (rc) return rc;
+    if ((rc = check_schedule(base)) != KS_OK) return rc;
+    if (n == 0 || reps < 1 || !best) return fail(KS_EINVAL, "ks_autotune_impl: need n >= 1, reps >= 1 and best");
+    cudaEvent_t e0, e1;
+    if ((rc = tune_events(P, &e0, &e1)) != KS_OK) return rc;
+    rc = tune_impl(P, n, jobs, reps, (cudaStream_t)stream, e0, e1, *base, ms_out, best);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
 }
 
 int ks_tune_cache_put(ks_params *P, uint32_t n_jobs, uint32_t mean_level, const ks_schedule *s)
@@ -144,12 +208,12 @@ int ks_tune_cache_save(const ks_params *P, const char *path)
     if (!P || !path) return fail(KS_EINVAL, "NULL argument");
     std::ofstream f(path);
     if (!f) return fail(KS_EINVAL, std::string("cannot write ") + path);
-    f << "# ks tuning cache v1\n";
+    f << "# ks tuning cache v2 (sched=dataflow,oc_variant,chunk,order,ntt,bconv)\n";
     const std::string tag = params_tag(P), dev = device_name(P->device);
     for (const auto &kv : P->tune)
         f << dev << " " << tag << " n=" << kv.first.first << " level=" << kv.first.second
           << " sched=" << kv.second.dataflow << "," << kv.second.oc_variant << "," << kv.second.chunk << ","
-          << kv.second.order << "\n";
+          << kv.second.order << "," << kv.second.ntt << "," << kv.second.bconv << "\n";
     return f.good() ? KS_OK : fail(KS_EINVAL, std::string("write failed: ") + path);
 }
 
@@ -163,10 +227,13 @@ int ks_tune_cache_load(ks_params *P, const char *path)
     while (std::getline(f, line)) {
         if (line.empty() || line[0] == '#' || line.compare(0, prefix.size(), prefix) != 0) continue;
         unsigned n = 0, lvl = 0;
-        int d = 0, v = 0, ch = 0, o = 0;
-        if (std::sscanf(line.c_str() + prefix.size(), "n=%u level=%u sched=%d,%d,%d,%d", &n, &lvl, &d, &v, &ch, &o) != 6)
-            continue;
-        ks_schedule s{d, v, ch, o};
+        int d = 0, v = 0, ch = 0, o = 0, nt = -1, bc = -1;
+        // v1 lines hold the four structural fields; the implementation fields
+        // then take the parameter set's options (-1)
+        const int got = std::sscanf(line.c_str() + prefix.size(), "n=%u level=%u sched=%d,%d,%d,%d,%d,%d", &n, &lvl,
+                                    &d, &v, &ch, &o, &nt, &bc);
+        if (got != 6 && got != 8) continue;
+        ks_schedule s{d, v, ch, o, nt, bc};
         if (check_schedule(&s) != KS_OK) continue;
         P->tune[{n, lvl}] = s;
     }

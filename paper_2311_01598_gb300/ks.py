@@ -30,16 +30,27 @@ class KSError(RuntimeError):
 
 
 class Schedule(ctypes.Structure):
-    """ks_schedule: dataflow (MP/DC/OC), oc_variant (0 fused, 1 split),
-    chunk (jobs per batched launch group), order (0 given, 1 by level, 2 by key)."""
+    """ks_schedule: dataflow (MP/DC/OC), oc_variant (0 fused, 1 split, 2
+    whole basis), chunk (jobs per batched launch group), order (0 given,
+    1 by level, 2 by key), ntt (0 two launches, 1/2 cluster launch, -1 the
+    parameter set's option) and bconv (0 CUDA cores, 1 tensor cores, -1 the
+    option)."""
     _fields_ = [("dataflow", ctypes.c_int32), ("oc_variant", ctypes.c_int32), ("chunk", ctypes.c_int32),
-                ("order", ctypes.c_int32)]
+                ("order", ctypes.c_int32), ("ntt", ctypes.c_int32), ("bconv", ctypes.c_int32)]
+
+    def __init__(self, dataflow=0, oc_variant=0, chunk=1, order=0, ntt=-1, bconv=-1):
+        super().__init__(dataflow, oc_variant, chunk, order, ntt, bconv)
 
     def as_tuple(self):
+        """The structural fields (what the cost model ranks)."""
         return (self.dataflow, self.oc_variant, self.chunk, self.order)
 
+    def impl(self):
+        return (self.ntt, self.bconv)
+
     def __repr__(self):
-        return f"Schedule(dataflow={self.dataflow}, oc_variant={self.oc_variant}, chunk={self.chunk}, order={self.order})"
+        return (f"Schedule(dataflow={self.dataflow}, oc_variant={self.oc_variant}, chunk={self.chunk}, "
+                f"order={self.order}, ntt={self.ntt}, bconv={self.bconv})")
 
 
 class ServerConfig(ctypes.Structure):
@@ -109,6 +120,8 @@ def lib():
         L.ks_tune_candidates.argtypes = [vp, u32, ctypes.POINTER(Schedule), ctypes.POINTER(u32)]
         L.ks_autotune.argtypes = [vp, u32, ctypes.POINTER(Job), u32, vp, u32, ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(Schedule)]
+        L.ks_autotune_impl.argtypes = [vp, u32, ctypes.POINTER(Job), u32, vp, ctypes.POINTER(Schedule),
+                                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(Schedule)]
         L.ks_tune_cache_put.argtypes = [vp, u32, u32, ctypes.POINTER(Schedule)]
         L.ks_tune_cache_get.argtypes = [vp, u32, u32, ctypes.POINTER(Schedule)]
         L.ks_tune_cache_save.argtypes = [vp, ctypes.c_char_p]
@@ -124,7 +137,7 @@ def lib():
         L.ks_mlp_forward.argtypes = [vp, u32, vp, vp, vp]
         L.ks_mlp_gradients.argtypes = [vp, u32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
         L.ks_mlp_train_step.argtypes = [vp, u32, vp, vp, vp, ctypes.c_float, ctypes.POINTER(ctypes.c_float), vp]
-        for name in ("ks_tune_candidates", "ks_autotune", "ks_tune_cache_put", "ks_tune_cache_get",
+        for name in ("ks_tune_candidates", "ks_autotune", "ks_autotune_impl", "ks_tune_cache_put", "ks_tune_cache_get",
                      "ks_tune_cache_save", "ks_tune_cache_load", "ks_key_synthetic", "ks_mlp_create",
                      "ks_mlp_get_params", "ks_mlp_set_params", "ks_mlp_forward", "ks_mlp_gradients",
                      "ks_mlp_train_step"):
@@ -298,6 +311,11 @@ class Params:
         """KS_OPT_BATCH_LANES: library streams a large Output-Centric batch is split over."""
         check(lib().ks_params_set_option(self.handle, 2, int(lanes)))
 
+    def set_ntt_cluster(self, on: bool) -> None:
+        """KS_OPT_NTT_CLUSTER: each NTT as one thread-block-cluster launch
+        (distributed shared memory between its passes) where supported."""
+        check(lib().ks_params_set_option(self.handle, 3, int(on)))
+
     def device_status(self, clear: bool = True) -> int:
         """ks_device_status: bit 0 = a tensor-core kernel's bounded MMA wait gave up."""
         f = ctypes.c_uint32()
@@ -367,6 +385,16 @@ class Params:
         ms = (ctypes.c_float * nc)()
         best = Schedule()
         check(lib().ks_autotune(self.handle, n, arr, reps, _stream_handle(stream), nc, ms, ctypes.byref(best)))
+        return best, [float(x) for x in ms]
+
+    def autotune_impl(self, jobs, base: "Schedule", reps: int = 3, stream=None):
+        """Time `base` under the implementation pairs (ntt, bconv) = (0,1),
+        (1,1), (0,0), (1,0); returns (best, [ms])."""
+        arr, n = self._jobs(jobs)
+        ms = (ctypes.c_float * 4)()
+        best = Schedule()
+        check(lib().ks_autotune_impl(self.handle, n, arr, reps, _stream_handle(stream), ctypes.byref(base), ms,
+                                     ctypes.byref(best)))
         return best, [float(x) for x in ms]
 
     def tune_cache_put(self, n_jobs: int, mean_level: int, schedule: "Schedule") -> None:

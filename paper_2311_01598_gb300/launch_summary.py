@@ -33,8 +33,8 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 TRAFFIC_PATH = os.path.join(HERE, "data", "ncu_traffic_gb300.json")
 # the device-code files whose change invalidates recorded per-kernel DRAM traffic
-KERNEL_SOURCES = ("csrc/ks_kernels.cu", "csrc/ks_oc.cu", "csrc/ks_bconv_tc.cu", "csrc/ks_device.cuh",
-                  "csrc/ks_ntt_core.cuh", "csrc/ks_launch.h")
+KERNEL_SOURCES = ("csrc/ks_kernels.cu", "csrc/ks_oc.cu", "csrc/ks_bconv_tc.cu", "csrc/ks_ntt_cluster.cu",
+                  "csrc/ks_device.cuh", "csrc/ks_ntt_core.cuh", "csrc/ks_launch.h")
 
 
 def kernel_sources_sha() -> str:
@@ -102,7 +102,7 @@ LIB_NAMES = {"k_fwd_row": "ntt_fwd_row", "k_fwd_col": "ntt_fwd_col", "k_inv_row"
              "k_inv_col": "ntt_inv_col", "k_bconv_up": "bconv_up", "k_bconv_down": "bconv_down",
              "k_bconv_tc<0>": "bconv_up", "k_bconv_tc<1>": "bconv_down",
              "k_oc_comb_qw": "oc_comb_q", "k_oc_comb_pw": "oc_comb_p", "k_oc_comb_q": "oc_comb_q",
-             "k_oc_comb_p": "oc_comb_p"}
+             "k_oc_comb_p": "oc_comb_p", "k_fwd_cl": "ntt_fwd_cl", "k_inv_cl": "ntt_inv_cl"}
 
 
 def lib_name(kernel_name):

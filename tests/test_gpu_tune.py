@@ -77,10 +77,13 @@ def test_autotune_caches_fastest_and_auto_uses_it():
         want.append(C.keyswitch(5, d, evk))
         jobs.append((key, 5, ks.to_device(d), ks.empty((5, C.N)), ks.empty((5, C.N))))
     cands = P.tune_candidates()
+    assert all(c.impl() == (-1, -1) for c in cands)
     best, ms = P.autotune(jobs, reps=2)
+    # stage 1 picks the structure, stage 2 an explicit implementation pair
     assert len(ms) == len(cands) and best.as_tuple() == cands[int(np.argmin(ms))].as_tuple()
+    assert best.impl() in ((0, 1), (1, 1), (0, 0), (1, 0))
     cached = P.tune_cache_get(6, 5)
-    assert cached is not None and cached.as_tuple() == best.as_tuple()
+    assert cached is not None and cached.as_tuple() == best.as_tuple() and cached.impl() == best.impl()
     for (_, _, _, o0, o1) in jobs:   # clear, then run KS_AUTO (the cached schedule)
         o0.zero_()
         o1.zero_()
@@ -92,7 +95,44 @@ def test_autotune_caches_fastest_and_auto_uses_it():
         P.tune_cache_save(path)
         P2 = ks.Params(12, 5, 2, 2)
         P2.tune_cache_load(path)
-        assert P2.tune_cache_get(6, 5).as_tuple() == best.as_tuple()
+        got = P2.tune_cache_get(6, 5)
+        assert got.as_tuple() == best.as_tuple() and got.impl() == best.impl()
+        # a line of the four-field format loads with the options' implementation
+        with open(path) as f:
+            line = [l for l in f if "sched=" in l and not l.startswith("#")][0]
+        with open(path, "w") as f:
+            f.write(line.split("sched=")[0] + "sched=2,1,8,0\n")
+        P3 = ks.Params(12, 5, 2, 2)
+        P3.tune_cache_load(path)
+        got = P3.tune_cache_get(6, 5)
+        assert got.as_tuple() == (2, 1, 8, 0) and got.impl() == (-1, -1)
+
+
+def test_autotune_impl_times_four_implementations():
+    """Stage 2 alone: the four (ntt, bconv) pairs of a structure are timed,
+    the fastest is returned, and every pair gives the oracle's outputs."""
+    need_gpu()
+    ks = built_lib()
+    P, C = pair(12, 5, 2, 2)
+    s = inputs.ternary_secret(C.N, 14)
+    evk = C.keygen(s, inputs.galois_secret(s, 3), seed=14)
+    key = P.upload_key(evk)
+    jobs, want = [], []
+    for i in range(4):
+        d = inputs.uniform_towers(C.q, C.N, seed=240 + i)
+        want.append(C.keyswitch(5, d, evk))
+        jobs.append((key, 5, ks.to_device(d), ks.empty((5, C.N)), ks.empty((5, C.N))))
+    base = ks.Schedule(2, 2, 64, 0)
+    best, ms = P.autotune_impl(jobs, base, reps=2)
+    pairs = [(0, 1), (1, 1), (0, 0), (1, 0)]
+    assert len(ms) == 4 and best.impl() == pairs[int(np.argmin(ms))] and best.as_tuple() == base.as_tuple()
+    for pr in pairs:
+        for (_, _, _, o0, o1) in jobs:
+            o0.zero_()
+            o1.zero_()
+        P.switch_batch_sched(jobs, ks.Schedule(2, 2, 64, 0, *pr))
+        for (_, _, _, o0, o1), (w0, w1) in zip(jobs, want):
+            assert np.array_equal(ks.to_host(o0), w0) and np.array_equal(ks.to_host(o1), w1), pr
 
 
 def test_cost_model_regret_on_gb300_dataset():
