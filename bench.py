@@ -77,7 +77,7 @@ def algorithmic_work(nact=NQ):
 def class_work(nact=NQ):
     """Algorithmic work per key switch of each kernel class of the
     Output-Centric schedule (split variant): (kind, units, bytes).  kind
-    "bfly": units are NTT butterflies; "mac": base-conversion
+    "bfly"/"ibfly": units are forward/inverse NTT butterflies; "mac": base-conversion
     multiply-accumulates; "hbm": a streaming kernel judged on bytes.  Bytes
     count each limb the kernel must read or write once (1 limb = 8N bytes)."""
     alpha = (NQ + DNUM - 1) // DNUM
@@ -90,11 +90,11 @@ def class_work(nact=NQ):
     inv_limbs = nact + 2 * K                      # prep + ModDown P1
     fwd_limbs = nd * K + q_modup + 2 * nact       # P section + Q section (ModUp, ModDown)
     return {
-        "ntt_inv_row": ("bfly", inv_limbs * half * LB, 2 * inv_limbs * LIMB),
-        "ntt_inv_col": ("bfly", inv_limbs * half * LA, 2 * inv_limbs * LIMB),
+        "ntt_inv_row": ("ibfly", inv_limbs * half * LB, 2 * inv_limbs * LIMB),
+        "ntt_inv_col": ("ibfly", inv_limbs * half * LA, 2 * inv_limbs * LIMB),
         "ntt_fwd_col": ("bfly", fwd_limbs * half * LA, 2 * fwd_limbs * LIMB),
         "ntt_fwd_row": ("bfly", fwd_limbs * half * LB, 2 * fwd_limbs * LIMB),
-        "ntt_inv_cl": ("bfly", inv_limbs * half * LOGN, 2 * inv_limbs * LIMB),
+        "ntt_inv_cl": ("ibfly", inv_limbs * half * LOGN, 2 * inv_limbs * LIMB),
         "ntt_fwd_cl": ("bfly", fwd_limbs * half * LOGN, 2 * fwd_limbs * LIMB),
         "bconv_up": ("mac", sum(a * (K + nact - a) for a in al) * N, (2 * nact + nd * K + q_modup) * LIMB),
         "bconv_down": ("mac", 2 * K * nact * N, (2 * K + 2 * nact) * LIMB),
@@ -435,6 +435,7 @@ def main():
     hbm_achieved = value / world * ALG_BYTES_PER_KS / 1e9
 
     bfly_peak, mac_peak = ks.probe_alu()
+    ibfly_peak = ks.probe_inv_bfly()
     work = class_work()
     from paper_2311_01598_gb300 import launch_summary
     traffic_rec = launch_summary.recorded_traffic()  # ncu DRAM bytes per key switch, current sources only
@@ -458,12 +459,13 @@ def main():
             out.update({"bound": "hbm", "unit": "GB/s", "achieved": round(gbs, 1), "peak": hbm_gbs,
                         "frac": round(gbs / hbm_gbs, 4), "peak_basis": f"{peak_src} copy bandwidth"})
         else:
-            peak = bfly_peak if kind == "bfly" else mac_peak
+            peak = {"bfly": bfly_peak, "ibfly": ibfly_peak}.get(kind, mac_peak)
             rate = units / secs_per_ks
-            out.update({"bound": "alu", "unit": "G" + ("butterfly" if kind == "bfly" else "mac") + "/s",
+            out.update({"bound": "alu", "unit": "G" + ("mac" if kind == "mac" else "butterfly") + "/s",
                         "achieved": round(rate / 1e9, 2), "peak": round(peak / 1e9, 2), "frac": round(rate / peak, 4),
                         "algorithmic_units_per_launch": int(units * B * args.steps / cnt),
-                        "peak_basis": "ks_probe_alu: register-only loop of the same device code on all 152 SMs",
+                        "peak_basis": ("ks_probe_inv_bfly" if kind == "ibfly" else "ks_probe_alu")
+                        + ": register-only loop of the same device code on all 152 SMs",
                         "hbm_frac_of_kernel": round(gbs / hbm_gbs, 4)})
         return out
 
@@ -504,7 +506,8 @@ def main():
             "kernels": {k: {"launches": c, "ms": round(t, 3), "frac": per_kernel[k].get("frac"),
                             "bound": per_kernel[k].get("bound")}
                         for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])},
-            "alu_probe": {"butterflies_per_s": bfly_peak, "bconv_macs_per_s": mac_peak,
+            "alu_probe": {"butterflies_per_s": bfly_peak, "inverse_butterflies_per_s": ibfly_peak,
+                          "bconv_macs_per_s": mac_peak,
                           "int_pipes_lanes_per_clk_sm": ks.probe_int_pipes()},
             "work_per_ks": algorithmic_work(),
             "cpu_baseline": cpu,

@@ -439,6 +439,10 @@ int ks_server_run_trace(ks_server *server, uint32_t n, const ks_request *reqs, c
  * accumulates per second.  iters: loop trips per thread (e.g. 4096). */
 int ks_probe_alu(int iters, double *bfly_per_s, double *mac_per_s);
 
+/* The same ceiling for the inverse (Harvey) NTT butterfly, inverse
+ * butterflies per second (the ceiling of the inverse NTT passes). */
+int ks_probe_inv_bfly(int iters, double *inv_bfly_per_s);
+
 /* Issue rates of single integer instructions on this GPU, in lanes per SM
  * per clock (all SMs, 8 independent chains per thread, the device's clock
  * attribute): out[0] mad.lo.u32, [1] mad.wide.u32 (64-bit accumulate),

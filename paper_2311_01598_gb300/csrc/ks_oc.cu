@@ -284,6 +284,22 @@ __device__ __forceinline__ void key_macv(const KeyView &K, int j, int t, size_t 
     }
 }
 
+// the key words of V coefficients (regenerated a half for a compressed key)
+template <bool CK, int V>
+__device__ __forceinline__ void key_words(const KeyView &K, int j, int t, size_t n, int nfull, int logN, u64 q,
+                                          u64 (&kb)[V], u64 (&ka)[V])
+{
+    const size_t N = (size_t)1 << logN;
+    if (CK && K.comp) {
+        ldv<V>(K.evk + ((size_t)j * nfull + t) * N + n, kb);
+#pragma unroll
+        for (int c = 0; c < V; ++c) ka[c] = key_a_word(K.a_seed, j, t, n + c, logN, nfull, q);
+    } else {
+        ldv<V>(K.evk + ((size_t)(2 * j) * nfull + t) * N + n, kb);
+        ldv<V>(K.evk + ((size_t)(2 * j + 1) * nfull + t) * N + n, ka);
+    }
+}
+
 static bool any_compressed(const OcJobs &oj)
 {
     for (int i = 0; i < oj.n; ++i)
@@ -362,13 +378,234 @@ __global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
     stv<V>(J.out1 + (size_t)t * N + n, o1);
 }
 
+// ------------------------------------------------------------------ shared keys
+// Combine kernels for jobs that share a key: one block reads each key word
+// once and applies it to every job of its group (up to kGroupJobs), so a
+// key's limbs cross HBM once per group instead of once per job.  Same
+// arithmetic, per job, as the per-job kernels above.  Pairs with two
+// coefficients a thread measured fastest on the 64-job mixed-level batch
+// (Q combine 0.99 ms against 1.08 ms per job); groups of four were slower
+// than the per-job kernels (1.34 ms with one coefficient a thread, 1.59 ms
+// with two).
+constexpr int kGroupJobs = 2;  // jobs a block serves
+constexpr int kGroupV = 2;     // coefficients a thread
+struct KeyGroups {
+    int n;                     // groups
+    int pre[kMaxBatch + 1];    // Q-combine row blocks of group g: [pre[g], pre[g+1]) (largest nact)
+    int first[kMaxBatch + 1];  // members of group g: mem[first[g] .. first[g+1])
+    int mem[kMaxBatch];        // job indices into the launch's OcJobs
+};
+
+// Row n of the section's limbs: WHOLE = the whole-basis layout (D
+// [nd][nact+K], then v [2][nact]); otherwise the split layout (P section D
+// [nd][K]; Q section D [nd][nact], then v [2][nact]).
+template <bool WHOLE>
+__device__ __forceinline__ const u64 *p_limb(const OcJob &J, int j, int k, int K, size_t N)
+{
+    return WHOLE ? J.tmp + ((size_t)j * (J.nact + K) + J.nact + k) * N : J.tmp + ((size_t)j * K + k) * N;
+}
+template <bool WHOLE>
+__device__ __forceinline__ const u64 *q_limb(const OcJob &J, int j, int t, int j0, int K, size_t N)
+{
+    if (j == j0) return J.d + (size_t)t * N;
+    return J.tmp + ((size_t)j * (WHOLE ? J.nact + K : J.nact) + t) * N;
+}
+template <bool WHOLE>
+__device__ __forceinline__ const u64 *v_limb(const OcJob &J, int x, int t, int K, size_t N)
+{
+    const size_t base = WHOLE ? (size_t)J.nd * (J.nact + K) : (size_t)J.nd * J.nact;
+    return J.tmp + (base + (size_t)x * J.nact + t) * N;
+}
+
+// P towers.  grid (N/(256V), groups*K).
+template <bool CK, bool WHOLE, int V>
+__global__ void __launch_bounds__(256) k_oc_comb_pg(Tables T, OcJobs oj, KeyGroups kg)
+{
+    const int K = T.kp;
+    const int g = blockIdx.y / K, k = blockIdx.y % K;
+    const int m0 = kg.first[g], cnt = kg.first[g + 1] - m0;
+    const KeyView key = oj.job[kg.mem[m0]].key;
+    const int tf = T.nq + k;
+    const int nfull = T.nq + K;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const ModC &mc = T.modc[tf];
+    int ndm = 0;
+    for (int i = 0; i < cnt; ++i) ndm = max(ndm, oj.job[kg.mem[m0 + i]].nd);
+    U128 sb[kGroupJobs][V], sa[kGroupJobs][V];
+#pragma unroll
+    for (int i = 0; i < kGroupJobs; ++i)
+#pragma unroll
+        for (int c = 0; c < V; ++c) sb[i][c] = sa[i][c] = U128{0, 0};
+    for (int j = 0; j < ndm; ++j) {
+        u64 kb[V], ka[V];
+        key_words<CK, V>(key, j, tf, n, nfull, T.logN, mc.q, kb, ka);
+#pragma unroll
+        for (int i = 0; i < kGroupJobs; ++i)
+            if (i < cnt) {
+                const OcJob &J = oj.job[kg.mem[m0 + i]];
+                if (j < J.nd) {
+                    u64 x[V];
+                    ldv<V>(p_limb<WHOLE>(J, j, k, K, N) + n, x);
+#pragma unroll
+                    for (int c = 0; c < V; ++c) {
+                        mac128(sb[i][c], x[c], kb[c]);
+                        mac128(sa[i][c], x[c], ka[c]);
+                    }
+                }
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < kGroupJobs; ++i)
+        if (i < cnt) {
+            const OcJob &J = oj.job[kg.mem[m0 + i]];
+            const int t = J.nact + k, nt = J.nact + K;
+            u64 ob[V], oa[V];
+#pragma unroll
+            for (int c = 0; c < V; ++c) {
+                ob[c] = reduce_any(redc(sb[i][c], mc.q, mc.mont), mc.q, mc.one_sh);
+                oa[c] = key_a_finish<CK>(key, sa[i][c], mc, T.key_sc, tf);
+            }
+            stv<V>(J.cp + (size_t)t * N + n, ob);
+            stv<V>(J.cp + (size_t)(nt + t) * N + n, oa);
+        }
+}
+
+// Q towers and the ModDown subtraction.  grid (N/(256V), kg.pre[kg.n]).
+template <bool CK, bool WHOLE, int V>
+__global__ void __launch_bounds__(256) k_oc_comb_qg(Tables T, OcJobs oj, KeyGroups kg)
+{
+    const int K = T.kp;
+    const int g = find_slot(kg.pre, kg.n, blockIdx.y);
+    const int t = blockIdx.y - kg.pre[g];
+    const int m0 = kg.first[g], cnt = kg.first[g + 1] - m0;
+    const KeyView key = oj.job[kg.mem[m0]].key;
+    const int j0 = t / T.alpha;
+    const int nfull = T.nq + K;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const ModC &mc = T.modc[t];
+    int ndm = 0;
+    for (int i = 0; i < cnt; ++i) {
+        const OcJob &J = oj.job[kg.mem[m0 + i]];
+        if (J.nact > t) ndm = max(ndm, J.nd);
+    }
+    U128 sb[kGroupJobs][V], sa[kGroupJobs][V];
+#pragma unroll
+    for (int i = 0; i < kGroupJobs; ++i)
+#pragma unroll
+        for (int c = 0; c < V; ++c) sb[i][c] = sa[i][c] = U128{0, 0};
+    for (int j = 0; j < ndm; ++j) {
+        u64 kb[V], ka[V];
+        key_words<CK, V>(key, j, t, n, nfull, T.logN, mc.q, kb, ka);
+#pragma unroll
+        for (int i = 0; i < kGroupJobs; ++i)
+            if (i < cnt) {
+                const OcJob &J = oj.job[kg.mem[m0 + i]];
+                if (J.nact > t && j < J.nd) {
+                    u64 x[V];
+                    ldv<V>(q_limb<WHOLE>(J, j, t, j0, K, N) + n, x);
+#pragma unroll
+                    for (int c = 0; c < V; ++c) {
+                        mac128(sb[i][c], x[c], kb[c]);
+                        mac128(sa[i][c], x[c], ka[c]);
+                    }
+                }
+            }
+    }
+    const u64 q40 = 40 * mc.q;
+#pragma unroll
+    for (int i = 0; i < kGroupJobs; ++i)
+        if (i < cnt) {
+            const OcJob &J = oj.job[kg.mem[m0 + i]];
+            if (J.nact > t) {
+                u64 vb[V], va[V], o0[V], o1[V];
+                ldv<V>(v_limb<WHOLE>(J, 0, t, K, N) + n, vb);
+                ldv<V>(v_limb<WHOLE>(J, 1, t, K, N) + n, va);
+#pragma unroll
+                for (int c = 0; c < V; ++c) {
+                    const u64 cb = reduce_any(redc(sb[i][c], mc.q, mc.mont), mc.q, mc.one_sh);
+                    const u64 ca = key_a_finish<CK>(key, sa[i][c], mc, T.key_sc, t);
+                    o0[c] = reduce_any(cb + q40 - vb[c], mc.q, mc.one_sh);
+                    o1[c] = reduce_any(ca + q40 - va[c], mc.q, mc.one_sh);
+                }
+                stv<V>(J.out0 + (size_t)t * N + n, o0);
+                stv<V>(J.out1 + (size_t)t * N + n, o1);
+            }
+        }
+}
+
+// Groups of jobs sharing a key (by stored key address), members in
+// descending level, at most kGroupJobs each.  Returns false when no two jobs
+// share a key (the per-job kernels are used then).
+static bool key_groups(const OcJobs &oj, KeyGroups &kg)
+{
+    std::vector<std::vector<int>> by_key;
+    std::vector<const u64 *> keys;
+    for (int i = 0; i < oj.n; ++i) {
+        const u64 *k = oj.job[i].key.evk;
+        size_t at = 0;
+        while (at < keys.size() && keys[at] != k) ++at;
+        if (at == keys.size()) {
+            keys.push_back(k);
+            by_key.emplace_back();
+        }
+        by_key[at].push_back(i);
+    }
+    if ((int)keys.size() == oj.n) return false;
+    kg.n = 0;
+    kg.pre[0] = 0;
+    kg.first[0] = 0;
+    int m = 0;
+    for (auto &members : by_key) {
+        std::stable_sort(members.begin(), members.end(),
+                         [&](int a, int b) { return oj.job[a].nact > oj.job[b].nact; });
+        for (size_t s = 0; s < members.size(); s += kGroupJobs) {
+            const size_t e = std::min(members.size(), s + kGroupJobs);
+            int top = 0;
+            for (size_t i = s; i < e; ++i) {
+                kg.mem[m++] = members[i];
+                top = std::max(top, oj.job[members[i]].nact);
+            }
+            kg.first[kg.n + 1] = m;
+            kg.pre[kg.n + 1] = kg.pre[kg.n] + top;
+            ++kg.n;
+        }
+    }
+    return true;
+}
+
+template <bool WHOLE>
+static void comb_grouped(const Tables &T, const OcJobs &oj, const KeyGroups &kg, bool p_section, cudaStream_t st)
+{
+    const size_t N = (size_t)1 << T.logN;
+    const bool ck = any_compressed(oj);
+    constexpr int V = kGroupV;
+    if (p_section) {
+        const dim3 g((unsigned)(N / (256 * V)), kg.n * T.kp);
+        if (ck)
+            KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_pg<true, WHOLE, V><<<g, 256, 0, st>>>(T, oj, kg)));
+        else
+            KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_pg<false, WHOLE, V><<<g, 256, 0, st>>>(T, oj, kg)));
+    } else {
+        const dim3 g((unsigned)(N / (256 * V)), kg.pre[kg.n]);
+        if (ck)
+            KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qg<true, WHOLE, V><<<g, 256, 0, st>>>(T, oj, kg)));
+        else
+            KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qg<false, WHOLE, V><<<g, 256, 0, st>>>(T, oj, kg)));
+    }
+}
+
 static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
     // Q towers: two coefficients a thread (16-byte accesses); the P-tower
     // combine has few rows and keeps one (measured faster)
     const dim3 gp((unsigned)(N / 256), oj.n * T.kp), gq((unsigned)(N / 512), oj.pre[oj.n]);
-    if (p_section) {
+    KeyGroups kg;
+    if (key_groups(oj, kg)) {
+        comb_grouped<false>(T, oj, kg, p_section, st);
+    } else if (p_section) {
         if (any_compressed(oj))
             KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_p<true, 1><<<gp, 256, 0, st>>>(T, oj)));
         else
@@ -495,16 +732,22 @@ static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream
     if ((rc = launch_bconv_up(T, bu, st)) != KS_OK) return rc;          // P2, every tower
     if ((rc = launch_ntt_fwd(T, mD, false, st)) != KS_OK) return rc;    // P3
     const bool ck = any_compressed(oj);
+    KeyGroups kg;
+    const bool grouped = key_groups(oj, kg);
     // Q towers two coefficients a thread, P towers one (as in oc_combine)
     const dim3 gp((unsigned)(N / 256), n * K), gq((unsigned)(N / 512), oj.pre[n]);
-    if (ck)  // P4+P5, P towers
+    if (grouped)  // P4+P5, P towers
+        comb_grouped<true>(T, oj, kg, true, st);
+    else if (ck)
         KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_pw<true, 1><<<gp, 256, 0, st>>>(T, oj)));
     else
         KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_pw<false, 1><<<gp, 256, 0, st>>>(T, oj)));
     if ((rc = launch_ntt_inv(T, mw, false, st)) != KS_OK) return rc;    // ModDown P1
     if ((rc = launch_bconv_down(T, bd, st)) != KS_OK) return rc;        // ModDown P2
     if ((rc = launch_ntt_fwd(T, mv, false, st)) != KS_OK) return rc;    // ModDown P3
-    if (ck)  // P4+P5 Q, ModDown P4
+    if (grouped)  // P4+P5 Q, ModDown P4
+        comb_grouped<true>(T, oj, kg, false, st);
+    else if (ck)
         KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qw<true, 2><<<gq, 256, 0, st>>>(T, oj)));
     else
         KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qw<false, 2><<<gq, 256, 0, st>>>(T, oj)));

@@ -35,6 +35,28 @@ __global__ void __launch_bounds__(kProbeThreads) k_probe_bfly(u64 *out, u64 q, u
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the loop alive
 }
 
+// The inverse (Harvey) butterfly in the same pattern.
+__global__ void __launch_bounds__(kProbeThreads) k_probe_ibfly(u64 *out, u64 q, u64 w, u64 wp, int iters)
+{
+    u64 x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = (threadIdx.x * 16 + i + blockIdx.x) % q;
+    const u64 q2 = 2 * q;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) inv_bfly(x[i], x[i + 8], w + i, wp + i, q, q2);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            inv_bfly(x[i], x[i + 4], w, wp, q, q2);
+            inv_bfly(x[i + 8], x[i + 12], w + 1, wp + 1, q, q2);
+        }
+    }
+    u64 s = 0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += x[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 __global__ void __launch_bounds__(kProbeThreads) k_probe_bmac(u64 *out, u64 c, int iters)
 {
     BAcc acc[8];
@@ -168,6 +190,36 @@ extern "C" int ks_probe_alu(int iters, double *bfly_per_s, double *mac_per_s)
         *mac_per_s = (double)kProbeBlocks * kProbeThreads * iters * 8 / (ms * 1e-3);
     }
     if (rc == KS_OK && cudaGetLastError() != cudaSuccess) rc = fail(KS_ECUDA, "ks_probe_alu: kernel failed");
+    if (out) cudaFree(out);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return rc;
+}
+
+extern "C" int ks_probe_inv_bfly(int iters, double *inv_bfly_per_s)
+{
+    if (iters < 1 || !inv_bfly_per_s) return fail(KS_EINVAL, "ks_probe_inv_bfly: bad argument");
+    u64 *out = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = KS_OK;
+    if (cudaMalloc((void **)&out, sizeof(u64) * kProbeBlocks * kProbeThreads) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        rc = fail(KS_ECUDA, "ks_probe_inv_bfly: setup failed");
+    }
+    const u64 q = 18014398509309953ull;
+    const u64 w = 1234567890123ull;
+    const u64 wp = (u64)(((unsigned __int128)w << 64) / q);
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && rc == KS_OK; ++rep) {  // first repetition warms up
+        cudaEventRecord(e0);
+        k_probe_ibfly<<<kProbeBlocks, kProbeThreads>>>(out, q, w, wp, iters);
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        *inv_bfly_per_s = (double)kProbeBlocks * kProbeThreads * iters * 16 / (ms * 1e-3);
+    }
+    if (rc == KS_OK && cudaGetLastError() != cudaSuccess) rc = fail(KS_ECUDA, "ks_probe_inv_bfly: kernel failed");
     if (out) cudaFree(out);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

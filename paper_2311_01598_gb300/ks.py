@@ -166,6 +166,8 @@ def lib():
         L.ks_probe_int_pipes.restype = ci
         L.ks_probe_alu.argtypes = [ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
         L.ks_probe_alu.restype = ci
+        L.ks_probe_inv_bfly.argtypes = [ci, ctypes.POINTER(ctypes.c_double)]
+        L.ks_probe_inv_bfly.restype = ci
         L.ks_kernel_launches.argtypes = []
         L.ks_kernel_launches.restype = ctypes.c_uint64
         L.ks_profile_enable.argtypes = [ci]
@@ -567,6 +569,13 @@ def probe_alu(iters: int = 4096) -> tuple[float, float]:
     b, m = ctypes.c_double(), ctypes.c_double()
     check(lib().ks_probe_alu(iters, ctypes.byref(b), ctypes.byref(m)))
     return b.value, m.value
+
+
+def probe_inv_bfly(iters: int = 4096) -> float:
+    """Inverse butterflies/s ceiling of this GPU."""
+    b = ctypes.c_double()
+    check(lib().ks_probe_inv_bfly(iters, ctypes.byref(b)))
+    return b.value
 
 
 def profile_enable(on: bool = True) -> None:
