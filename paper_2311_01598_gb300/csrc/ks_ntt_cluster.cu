@@ -18,7 +18,6 @@
 #include "ks_ntt_core.cuh"
 
 namespace ks {
-namespace {
 
 // Cluster geometry of a two-pass shape, its CTAs widened MUL times (each
 // CTA covers MUL column groups and MUL row groups of the two-pass kernels in
@@ -26,7 +25,7 @@ namespace {
 // split a limb over the same number of CTAs with the same block size, and C
 // is at most 16 (the non-portable cluster limit).
 template <class S, int MUL>
-struct Cl {
+struct NttClusterShape {
     static constexpr int COLS = S::COLS * MUL, ROWS = S::ROWS * MUL;
     static constexpr int C = (1 << S::LB) / COLS;
     static constexpr bool OK = C >= 1 && C * COLS == (1 << S::LB) && C == (1 << S::LA) / ROWS &&
@@ -37,6 +36,11 @@ struct Cl {
     static constexpr int SMEM = BUFW * 8 + (1 << S::LA) * 16 + ROWS * S::REGB * 16;
     static constexpr int MINB = S::LA <= 8 ? (4 / MUL > 0 ? 4 / MUL : 1) : 1;
 };
+
+template <class S, int MUL>
+using Cl = NttClusterShape<S, MUL>;
+
+namespace {
 
 __device__ __forceinline__ int cluster_rank()
 {
