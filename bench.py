@@ -70,7 +70,9 @@ def algorithmic_work(nact=NQ):
     bconv_up = sum(min(alpha, nact - j * alpha) * (nt - min(alpha, nact - j * alpha)) for j in range(nd)) * N
     bconv_down = 2 * KP * nact * N
     key_mac = 2 * nd * nt * N
-    return {"ntt": n_ntt, "butterflies": n_ntt * bfly, "bconv_macs": bconv_up + bconv_down, "key_macs": key_mac,
+    n_inv = ntt["modup_intt"] + ntt["moddown_intt"]
+    return {"ntt": n_ntt, "butterflies": n_ntt * bfly, "forward_butterflies": (n_ntt - n_inv) * bfly,
+            "inverse_butterflies": n_inv * bfly, "bconv_macs": bconv_up + bconv_down, "key_macs": key_mac,
             "modmul": n_ntt * bfly + bconv_up + bconv_down + key_mac + nact * N, "a_last": a_last}
 
 
@@ -474,9 +476,26 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as orc
         rate, reps, el, cores = oracle_rate()
         cpu = {"value": round(rate, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{reps} whole key switches at N=2^16 L+1=24 K=8 dnum=3 ({el:.1f} s)"}
+        orc.set_threads(1)  # the same oracle on one core (one whole key switch)
+        rate1, reps1, el1, _ = oracle_rate(seconds=1.0, min_reps=1)
+        orc.set_threads(cores)
+        cpu["single_core"] = {"value": round(rate1, 4), "unit": UNIT,
+                              "sample": f"{reps1} whole key switch(es), one thread ({el1:.1f} s)"}
+
+    # step-level integer ceiling: the step's butterflies and base-conversion
+    # multiply-accumulates at the probes' rates (the key products are
+    # streaming work, judged by the HBM fraction)
+    wk = algorithmic_work()
+    alu_s_per_ks = (wk["forward_butterflies"] / bfly_peak + wk["inverse_butterflies"] / ibfly_peak
+                    + wk["bconv_macs"] / mac_peak)
+    alu_roofline = {"achieved": round(value / world, 2), "ceiling": round(1.0 / alu_s_per_ks, 1), "unit": UNIT,
+                    "frac": round(value / world * alu_s_per_ks, 4),
+                    "basis": "forward/inverse butterflies and CUDA-core-equivalent base-conversion MACs per key "
+                             "switch at the ks_probe_alu / ks_probe_inv_bfly rates"}
 
     if rank == 0:
         line = {
@@ -503,6 +522,7 @@ def main():
                              "frac": round(hbm_achieved / hbm_gbs, 4), "basis": f"{peak_src} copy bandwidth",
                              "algorithmic_bytes_per_ks": ALG_BYTES_PER_KS},
             "roofline": roofline,
+            "alu_roofline": alu_roofline,
             "kernels": {k: {"launches": c, "ms": round(t, 3), "frac": per_kernel[k].get("frac"),
                             "bound": per_kernel[k].get("bound")}
                         for k, (c, t) in sorted(prof.items(), key=lambda kv: -kv[1][1])},
