@@ -189,6 +189,19 @@ int ks_switch_hoisted(const ks_params *params, uint32_t n_rot, const ks_key *con
                       uint32_t level_towers, const uint64_t *d_in, uint64_t *const *d_out0, uint64_t *const *d_out1,
                       ks_stream_t stream);
 
+/* The automorphism X -> X^g of a polynomial in evaluation form (Sec. II:
+ * the slot permutation of a rotation): slot k of the output takes slot k' of
+ * the input with 2brv(k')+1 = (2brv(k)+1) g mod 2N, tower by tower.  With
+ * accumulate = 1 the result is added to d_out mod q (so a rotation by g is
+ * (phi_g(c0) + out0, out1) with out0, out1 from ks_switch_hoisted of c1).
+ *   first_tower, n_towers : towers of the full basis (Q towers 0..n_q-1, then
+ *                           the K special towers) held by d_in and d_out;
+ *   galois                : odd, below 2N;
+ *   d_in, d_out           : device [n_towers][N], canonical; must not overlap.
+ * n_towers = 0 is a no-op. */
+int ks_automorph(const ks_params *params, uint32_t first_tower, uint32_t n_towers, uint64_t galois,
+                 const uint64_t *d_in, uint64_t *d_out, int accumulate, ks_stream_t stream);
+
 /* One job of a batched key switch. */
 typedef struct {
     const ks_key *key;

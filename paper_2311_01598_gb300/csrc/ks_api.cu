@@ -771,6 +771,24 @@ int ks_switch_hoisted(const ks_params *P, uint32_t n_rot, const ks_key *const *k
                        (cudaStream_t)stream);
 }
 
+int ks_automorph(const ks_params *P, uint32_t first_tower, uint32_t n_towers, uint64_t galois, const uint64_t *d_in,
+                 uint64_t *d_out, int accumulate, ks_stream_t stream)
+{
+    int rc = check_params(P);
+    if (rc) return rc;
+    if (n_towers == 0) return KS_OK;
+    if (!d_in || !d_out) return fail(KS_EINVAL, "ks_automorph: NULL data pointer");
+    if ((uint64_t)first_tower + n_towers > (uint64_t)(P->nq + P->kp))
+        return fail(KS_EINVAL, "ks_automorph: towers beyond the basis");
+    if (galois % 2 == 0 || galois >= 2ull * P->N) return fail(KS_EINVAL, "galois element must be odd and below 2N");
+    const size_t bytes = (size_t)n_towers * P->N * sizeof(u64);
+    const char *a = (const char *)d_in, *b = (const char *)d_out;
+    if (a < b + bytes && b < a + bytes) return fail(KS_EINVAL, "ks_automorph: d_in and d_out overlap");
+    if ((rc = set_device(P)) != KS_OK) return rc;
+    return launch_automorph(P->tables, (int)first_tower, (int)n_towers, d_in, d_out, galois, accumulate != 0,
+                            (cudaStream_t)stream);
+}
+
 }  // extern "C"
 
 namespace ks {

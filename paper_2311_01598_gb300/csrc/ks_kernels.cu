@@ -478,6 +478,21 @@ __device__ __forceinline__ size_t galois_slot(size_t n, u64 g, int logN)
     return (size_t)(__brev((unsigned)((e - 1) >> 1)) >> (32 - logN));
 }
 
+// Evaluation-domain automorphism X -> X^g of n towers starting at full
+// tower t0: out[t][n] = in[t][galois_slot(n)] (+ out[t][n] mod q_t with
+// accumulate).  Inputs canonical; grid (N/256, towers).
+__global__ void __launch_bounds__(256) k_automorph(Tables T, int t0, const u64 *in, u64 *out, u64 galois,
+                                                   int accumulate)
+{
+    const int t = blockIdx.y;
+    const size_t N = (size_t)1 << T.logN;
+    const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const u64 q = T.modc[t0 + t].q;
+    const u64 v = in[(size_t)t * N + galois_slot(n, galois, T.logN)];
+    u64 *o = out + (size_t)t * N + n;
+    *o = accumulate ? reduce2(*o + v, q) : v;
+}
+
 template <bool CK>
 __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, int j1, const u64 *d, const u64 *D,
                                                    size_t dstride, KeyView key, u64 *cp, int accumulate, u64 galois)
@@ -508,6 +523,17 @@ __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, i
     }
     *cb = rb;
     *ca = ra;
+}
+
+int launch_automorph(const Tables &T, int t0, int ntowers, const u64 *in, u64 *out, uint64_t galois, bool accumulate,
+                     cudaStream_t st)
+{
+    if (ntowers == 0) return KS_OK;
+    const size_t N = (size_t)1 << T.logN;
+    KS_LAUNCH(st, "automorph",
+              k_automorph<<<dim3((unsigned)(N / 256), (unsigned)ntowers), 256, 0, st>>>(T, t0, in, out, galois,
+                                                                                       accumulate ? 1 : 0));
+    return launch_status("automorphism launch");
 }
 
 int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u64 *d, const u64 *D,

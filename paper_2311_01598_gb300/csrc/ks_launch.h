@@ -132,6 +132,11 @@ int tc_error_flag(bool clear);
 int launch_apply_key(const Tables &T, int nact, int j_begin, int j_end, const u64 *d, const u64 *D,
                      size_t D_digit_stride, const KeyView &key, u64 *cp, bool accumulate, cudaStream_t st,
                      uint64_t galois = 1);
+// Automorphism X -> X^g of the evaluation slots of ntowers limbs (full
+// towers t0..t0+ntowers-1): out = phi_g(in), or out + phi_g(in) mod q with
+// accumulate.  in and out must not overlap.
+int launch_automorph(const Tables &T, int t0, int ntowers, const u64 *in, u64 *out, uint64_t galois, bool accumulate,
+                     cudaStream_t st);
 // ModDown P4 (single job; P^-1 folded): out_x[i] = cp[x][i] - v[x][i] mod q_i,
 // v lazy NTT output.
 int launch_down_final(const Tables &T, int nact, int npoly, const u64 *cp, size_t cp_stride, const u64 *v,

@@ -162,6 +162,8 @@ def lib():
         L.ks_switch_hoisted.argtypes = [vp, ctypes.c_uint32, ctypes.POINTER(vp), ctypes.POINTER(ctypes.c_uint64),
                                         ctypes.c_uint32, vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         L.ks_switch_hoisted.restype = ci
+        L.ks_automorph.argtypes = [vp, u32, u32, u64, vp, vp, ci, vp]
+        L.ks_automorph.restype = ci
         L.ks_probe_int_pipes.argtypes = [ctypes.POINTER(ctypes.c_double), ci]
         L.ks_probe_int_pipes.restype = ci
         L.ks_probe_alu.argtypes = [ci, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
@@ -336,6 +338,12 @@ class Params:
         o0 = (ctypes.c_void_p * max(1, R))(*[_ptr(o).value for o in outs0])
         o1 = (ctypes.c_void_p * max(1, R))(*[_ptr(o).value for o in outs1])
         check(lib().ks_switch_hoisted(self.handle, R, ka, ga, nact, _ptr(d), o0, o1, _stream_handle(stream)))
+
+    def automorph(self, first_tower: int, galois: int, d_in, d_out, accumulate: bool = False, stream=None) -> None:
+        """ks_automorph: d_out = phi_g(d_in) (or d_out + phi_g(d_in) with
+        accumulate), X -> X^g on the evaluation slots of every tower."""
+        check(lib().ks_automorph(self.handle, first_tower, d_in.shape[0], int(galois), _ptr(d_in), _ptr(d_out),
+                                 1 if accumulate else 0, _stream_handle(stream)))
 
     def switch_noalloc(self, key: Key, nact: int, d, out0, out1, stream=None) -> None:
         """ks_switch_noalloc: Output-Centric key switch using the library's
