@@ -459,14 +459,11 @@ bool bconv_tc_supported(const Tables &T, int nsrc)
 
 static int sm_count()
 {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
-            cudaGetLastError();
-            n = 1;
-        }
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+        cudaGetLastError();
+        n = 1;
     }
     return n;
 }
@@ -478,11 +475,9 @@ static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int 
     // target blocks of equal size (at most 16): 24 targets run as 12 + 12
     const int TBN = (span + TC_TB - 1) / TC_TB;
     const int TB = (span + TBN - 1) / TBN;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_bconv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PIPE_SMEM);
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    once_per_device(attr,
+                    [] { cudaFuncSetAttribute(k_bconv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PIPE_SMEM); });
     const int XT = (int)(((size_t)1 << T.logN) / TC_M);
     const long long items = (long long)XT * TBN * Z;
     if (items <= 0) return KS_OK;

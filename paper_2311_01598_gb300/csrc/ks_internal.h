@@ -16,6 +16,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstdint>
 #include <map>
@@ -163,6 +164,30 @@ class LaunchScope {
         ::ks::LaunchScope ks_scope_(st, name); \
         __VA_ARGS__;                          \
     } while (0)
+
+// Per-device one-time setup (kernel attributes are per device context):
+// runs setup() once for the current device; callers on other threads wait
+// for it to finish.  done is the caller's static bit set of devices.
+inline std::mutex &setup_mutex()
+{
+    static std::mutex m;
+    return m;
+}
+template <class F>
+inline void once_per_device(std::atomic<uint64_t> &done, F &&setup)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    std::lock_guard<std::mutex> g(setup_mutex());
+    if (done.load(std::memory_order_relaxed) & bit) return;
+    setup();
+    done.fetch_or(bit, std::memory_order_release);
+}
 
 // Thread-local error message (ks_last_error).
 void set_error(const std::string &msg);

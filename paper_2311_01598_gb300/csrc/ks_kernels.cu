@@ -159,16 +159,16 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_inv_col(Tables T, L
 template <class S>
 static void set_smem_attrs()
 {
-    static bool done = false;  // per instantiation
-    if (done) return;
-    cudaFuncSetAttribute(k_fwd_col<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-    cudaFuncSetAttribute(k_inv_col<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-    cudaFuncSetAttribute(k_inv_col<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-    cudaFuncSetAttribute(k_inv_col<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-    cudaFuncSetAttribute(k_fwd_row<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
-    cudaFuncSetAttribute(k_fwd_row<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
-    cudaFuncSetAttribute(k_inv_row<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
-    done = true;
+    static std::atomic<uint64_t> done{0};  // per instantiation, per device
+    once_per_device(done, [] {
+        cudaFuncSetAttribute(k_fwd_col<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+        cudaFuncSetAttribute(k_inv_col<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+        cudaFuncSetAttribute(k_inv_col<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+        cudaFuncSetAttribute(k_inv_col<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+        cudaFuncSetAttribute(k_fwd_row<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
+        cudaFuncSetAttribute(k_fwd_row<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
+        cudaFuncSetAttribute(k_inv_row<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+    });
 }
 
 static int launch_status(const char *what)

@@ -244,18 +244,24 @@ static bool prepare(KERN kern, int C, int threads, int smem)
 template <class S, int MUL>
 struct ClKernels {
     typedef Cl<S, MUL> G;
+    // per device: attributes set and the cluster shape accepted
     static bool ready()
     {
-        static const bool ok = [] {
+        static std::atomic<uint64_t> done{0}, ok{0};
+        once_per_device(done, [] {
             bool r = true;
             r = r && prepare(k_fwd_cl<S, MUL, false>, G::C, G::THREADS, G::SMEM);
             r = r && prepare(k_fwd_cl<S, MUL, true>, G::C, G::THREADS, G::SMEM);
             r = r && prepare(k_inv_cl<S, MUL, 0>, G::C, G::THREADS, G::SMEM);
             r = r && prepare(k_inv_cl<S, MUL, 1>, G::C, G::THREADS, G::SMEM);
             r = r && prepare(k_inv_cl<S, MUL, 2>, G::C, G::THREADS, G::SMEM);
-            return r;
-        }();
-        return ok;
+            int dev = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+            if (r) ok.fetch_or(1ull << (dev & 63));
+        });
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) cudaGetLastError();
+        return (ok.load() >> (dev & 63)) & 1;
     }
 };
 

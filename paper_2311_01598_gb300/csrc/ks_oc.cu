@@ -201,12 +201,11 @@ __global__ void __launch_bounds__(S::THREADS_B) k_oc_rowQ(Tables T, OcJobs oj)
 template <class S>
 static void oc_rows_S(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
 {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<uint64_t> attr{0};
+    once_per_device(attr, [] {
         cudaFuncSetAttribute(k_oc_rowP<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowSmem<S>::BYTES);
         cudaFuncSetAttribute(k_oc_rowQ<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowSmem<S>::BYTES);
-        attr = true;
-    }
+    });
     if (p_section)
         KS_LAUNCH(st, "oc_row_p",
                   k_oc_rowP<S><<<dim3((1 << S::LA) / S::ROWS, oj.n * T.kp), S::THREADS_B, RowSmem<S>::BYTES, st>>>(
