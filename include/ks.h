@@ -162,8 +162,11 @@ size_t ks_key_bytes(const ks_key *key);
  *   d_out0/out1  : device [l+1][N]; receive (out0, out1) with
  *                  out0 + out1*s = d*s' + small noise (mod Q_l), canonical.
  *                  Must not overlap d_in or each other.
- * Device scratch is owned by the params object, one set per stream; calls
- * on different streams may overlap. */
+ * d_in, d_out0 and d_out1 must be 16-byte aligned (every cudaMalloc and
+ * torch allocation is; an offset view may not be): KS_EINVAL otherwise.
+ * The same holds for the jobs of every batched, hoisted and host-staged
+ * call.  Device scratch is owned by the params object, one set per stream;
+ * calls on different streams may overlap. */
 int ks_switch(const ks_params *params, const ks_key *key, uint32_t level_towers,
               const uint64_t *d_in, uint64_t *d_out0, uint64_t *d_out1, ks_dataflow dataflow,
               ks_stream_t stream);

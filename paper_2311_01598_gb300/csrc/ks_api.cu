@@ -696,6 +696,9 @@ static int check_job(const ks_params *P, const ks_key *K, uint32_t nact, const u
     if (!K || K->params != P) return fail(KS_EINVAL, "key is NULL or belongs to another params object");
     if (nact < 1 || nact > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
     if (!d || !o0 || !o1) return fail(KS_EINVAL, "NULL data pointer");
+    // the combine kernels move two words at a time
+    if (((uintptr_t)d | (uintptr_t)o0 | (uintptr_t)o1) & 15)
+        return fail(KS_EINVAL, "d_in, d_out0 and d_out1 must be 16-byte aligned");
     const size_t bytes = (size_t)nact * P->N * sizeof(u64);
     auto overlap = [bytes](const void *a, const void *b) {
         const char *x = (const char *)a, *y = (const char *)b;

@@ -245,21 +245,28 @@ static int oc_rows(const Tables &T, const OcJobs &oj, bool p_section, cudaStream
 template <int V>
 __device__ __forceinline__ void ldv(const u64 *p, u64 (&o)[V])
 {
-    if constexpr (V == 2) {
-        const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p);
-        o[0] = t.x;
-        o[1] = t.y;
-    } else {
+    static_assert(V == 1 || V % 2 == 0, "one word or pairs");
+    if constexpr (V == 1) {
         o[0] = *p;
+    } else {
+#pragma unroll
+        for (int c = 0; c < V; c += 2) {
+            const ulonglong2 t = *reinterpret_cast<const ulonglong2 *>(p + c);
+            o[c] = t.x;
+            o[c + 1] = t.y;
+        }
     }
 }
 template <int V>
 __device__ __forceinline__ void stv(u64 *p, const u64 (&v)[V])
 {
-    if constexpr (V == 2)
-        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(v[0], v[1]);
-    else
+    static_assert(V == 1 || V % 2 == 0, "one word or pairs");
+    if constexpr (V == 1) {
         *p = v[0];
+    } else {
+#pragma unroll
+        for (int c = 0; c < V; c += 2) *reinterpret_cast<ulonglong2 *>(p + c) = make_ulonglong2(v[c], v[c + 1]);
+    }
 }
 // key product of V coefficients: x * b_j and x * a_j added into sb, sa
 template <bool CK, int V>
@@ -598,9 +605,10 @@ static void comb_grouped(const Tables &T, const OcJobs &oj, const KeyGroups &kg,
 static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
-    // Q towers: two coefficients a thread (16-byte accesses); the P-tower
-    // combine has few rows and keeps one (measured faster)
-    const dim3 gp((unsigned)(N / 256), oj.n * T.kp), gq((unsigned)(N / 512), oj.pre[oj.n]);
+    // Q towers: four coefficients a thread (two 16-byte accesses per
+    // stream: 0.42 ms against 0.47 ms with two at the benchmark step); the
+    // P-tower combine has few rows and keeps one (two measured slower)
+    const dim3 gp((unsigned)(N / 256), oj.n * T.kp), gq((unsigned)(N / 1024), oj.pre[oj.n]);
     KeyGroups kg;
     if (key_groups(oj, kg)) {
         comb_grouped<false>(T, oj, kg, p_section, st);
@@ -611,9 +619,9 @@ static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, cudaStr
             KS_LAUNCH(st, "oc_comb_p", (k_oc_comb_p<false, 1><<<gp, 256, 0, st>>>(T, oj)));
     } else {
         if (any_compressed(oj))
-            KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_q<true, 2><<<gq, 256, 0, st>>>(T, oj)));
+            KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_q<true, 4><<<gq, 256, 0, st>>>(T, oj)));
         else
-            KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_q<false, 2><<<gq, 256, 0, st>>>(T, oj)));
+            KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_q<false, 4><<<gq, 256, 0, st>>>(T, oj)));
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(KS_ECUDA, std::string("OC combine launch: ") + cudaGetErrorString(e));
@@ -733,8 +741,8 @@ static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream
     const bool ck = any_compressed(oj);
     KeyGroups kg;
     const bool grouped = key_groups(oj, kg);
-    // Q towers two coefficients a thread, P towers one (as in oc_combine)
-    const dim3 gp((unsigned)(N / 256), n * K), gq((unsigned)(N / 512), oj.pre[n]);
+    // Q towers four coefficients a thread, P towers one (as in oc_combine)
+    const dim3 gp((unsigned)(N / 256), n * K), gq((unsigned)(N / 1024), oj.pre[n]);
     if (grouped)  // P4+P5, P towers
         comb_grouped<true>(T, oj, kg, true, st);
     else if (ck)
@@ -747,9 +755,9 @@ static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream
     if (grouped)  // P4+P5 Q, ModDown P4
         comb_grouped<true>(T, oj, kg, false, st);
     else if (ck)
-        KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qw<true, 2><<<gq, 256, 0, st>>>(T, oj)));
+        KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qw<true, 4><<<gq, 256, 0, st>>>(T, oj)));
     else
-        KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qw<false, 2><<<gq, 256, 0, st>>>(T, oj)));
+        KS_LAUNCH(st, "oc_comb_q", (k_oc_comb_qw<false, 4><<<gq, 256, 0, st>>>(T, oj)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(KS_ECUDA, std::string("OC whole-basis launch: ") + cudaGetErrorString(e));
     return KS_OK;
