@@ -279,7 +279,9 @@ typedef struct {
                             launch over every raised limb, then the combines)  */
     int32_t chunk;       /* KS_OC: jobs per batched launch group, 1..64           */
     int32_t order;       /* 0 = jobs in the given order, 1 = grouped by level
-                            (descending), 2 = grouped by key                     */
+                            (descending), 2 = grouped by key (KS_OC: jobs of a
+                            launch sharing a key also share each read of its
+                            limbs in the combine kernels)                        */
     int32_t ntt;         /* NTT form: 0 = two launches (column pass, row pass),
                             1 = one cluster launch per NTT (KS_OPT_NTT_CLUSTER),
                             2 = the same with CTAs twice as wide; -1 = the
@@ -312,7 +314,8 @@ int ks_tune_candidates(const ks_params *params, uint32_t max, ks_schedule *out, 
  * best of `reps` timed runs with CUDA events on `stream`; the jobs' outputs
  * are overwritten -- every schedule writes the same values):
  *   1. every structural candidate (ks_tune_candidates); ms_out[i] gets
- *      candidate i's time in ms (max entries);
+ *      candidate i's time in ms (max entries); of the candidates within
+ *      0.3% of the fastest, the one with the largest launch group wins;
  *   2. the fastest structure under each implementation pair (ntt, bconv) in
  *      {(0,1), (1,1), (0,0), (1,0)} (ks_autotune_impl).
  * The fastest schedule, with explicit ntt and bconv, is written to *best and

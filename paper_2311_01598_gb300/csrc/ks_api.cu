@@ -913,7 +913,7 @@ static int run_oc_batch(ks_params *P, const Tables &T, uint32_t n, const ks_job 
     }
     for (uint32_t i0 = 0; i0 < n; i0 += (uint32_t)sc.chunk) {
         const int m = (int)std::min<uint32_t>((uint32_t)sc.chunk, n - i0);
-        if ((rc = launch_oc(T, m, oj.data() + i0, sc.oc_variant, st)) != KS_OK) return rc;
+        if ((rc = launch_oc(T, m, oj.data() + i0, sc.oc_variant, st, sc.order == 2)) != KS_OK) return rc;
     }
     return KS_OK;
 }

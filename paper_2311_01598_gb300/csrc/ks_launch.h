@@ -175,6 +175,9 @@ size_t oc_scratch_words(const Tables &T, int nact);
 // base-conversion launch and one NTT launch, then runs the same per-tower
 // combine kernels (special towers, ModDown, Q towers).
 enum { KS_OC_FUSED = 0, KS_OC_SPLIT = 1, KS_OC_WHOLE = 2 };
-int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st);
+// share_keys: jobs of a launch that share a key run through the key-grouped
+// combine kernels (each key word read once per group of jobs); otherwise
+// every job streams its own key limbs.
+int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st, bool share_keys = false);
 
 }  // namespace ks

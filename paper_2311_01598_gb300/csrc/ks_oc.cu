@@ -388,11 +388,12 @@ __global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
 // Combine kernels for jobs that share a key: one block reads each key word
 // once and applies it to every job of its group (up to kGroupJobs), so a
 // key's limbs cross HBM once per group instead of once per job.  Same
-// arithmetic, per job, as the per-job kernels above.  Pairs with two
-// coefficients a thread measured fastest on the 64-job mixed-level batch
-// (Q combine 0.99 ms against 1.08 ms per job); groups of four were slower
-// than the per-job kernels (1.34 ms with one coefficient a thread, 1.59 ms
-// with two).
+// arithmetic, per job, as the per-job kernels above.  Used when the
+// schedule orders jobs by key.  On the 64-job mixed-level batch (16 keys),
+// pairs at two coefficients a thread beat the per-job kernels at two (Q
+// combine 0.99 against 1.08 ms) but not at four (8293 against 8329
+// key-switches/s for the batch); groups of four were slower still, and
+// pairs at four coefficients need 128 registers a thread.
 constexpr int kGroupJobs = 2;  // jobs a block serves
 constexpr int kGroupV = 2;     // coefficients a thread
 struct KeyGroups {
@@ -602,7 +603,7 @@ static void comb_grouped(const Tables &T, const OcJobs &oj, const KeyGroups &kg,
     }
 }
 
-static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, cudaStream_t st)
+static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, bool share_keys, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
     // Q towers: four coefficients a thread (two 16-byte accesses per
@@ -610,7 +611,7 @@ static int oc_combine(const Tables &T, const OcJobs &oj, bool p_section, cudaStr
     // P-tower combine has few rows and keeps one (two measured slower)
     const dim3 gp((unsigned)(N / 256), oj.n * T.kp), gq((unsigned)(N / 1024), oj.pre[oj.n]);
     KeyGroups kg;
-    if (key_groups(oj, kg)) {
+    if (share_keys && key_groups(oj, kg)) {
         comb_grouped<false>(T, oj, kg, p_section, st);
     } else if (p_section) {
         if (any_compressed(oj))
@@ -708,7 +709,7 @@ __global__ void __launch_bounds__(256) k_oc_comb_qw(Tables T, OcJobs oj)
     stv<V>(J.out1 + (size_t)t * N + n, o1);
 }
 
-static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream_t st)
+static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, bool share_keys, cudaStream_t st)
 {
     const size_t N = (size_t)1 << T.logN;
     const int K = T.kp;
@@ -740,7 +741,7 @@ static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream
     if ((rc = launch_ntt_fwd(T, mD, false, st)) != KS_OK) return rc;    // P3
     const bool ck = any_compressed(oj);
     KeyGroups kg;
-    const bool grouped = key_groups(oj, kg);
+    const bool grouped = share_keys && key_groups(oj, kg);
     // Q towers four coefficients a thread, P towers one (as in oc_combine)
     const dim3 gp((unsigned)(N / 256), n * K), gq((unsigned)(N / 1024), oj.pre[n]);
     if (grouped)  // P4+P5, P towers
@@ -763,9 +764,9 @@ static int launch_oc_whole(const Tables &T, int n, const OcJob *jobs, cudaStream
     return KS_OK;
 }
 
-static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int variant, cudaStream_t st)
+static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int variant, bool share_keys, cudaStream_t st)
 {
-    if (variant == KS_OC_WHOLE) return launch_oc_whole(T, n, jobs, st);
+    if (variant == KS_OC_WHOLE) return launch_oc_whole(T, n, jobs, share_keys, st);
     const size_t N = (size_t)1 << T.logN;
     const int K = T.kp;
     int rc;
@@ -802,7 +803,7 @@ static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int varian
         if ((rc = launch_inv_col(T, mw, false, st)) != KS_OK) return rc;
     } else {
         if ((rc = launch_ntt_fwd(T, mp, false, st)) != KS_OK) return rc;
-        if ((rc = oc_combine(T, oj, true, st)) != KS_OK) return rc;
+        if ((rc = oc_combine(T, oj, true, share_keys, st)) != KS_OK) return rc;
         if ((rc = launch_ntt_inv(T, mw, false, st)) != KS_OK) return rc;
     }
     // 3. Q section
@@ -826,10 +827,10 @@ static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int varian
         return oc_rows(T, oj, false, st);
     }
     if ((rc = launch_ntt_fwd(T, mq, false, st)) != KS_OK) return rc;
-    return oc_combine(T, oj, false, st);
+    return oc_combine(T, oj, false, share_keys, st);
 }
 
-int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st)
+int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st, bool share_keys)
 {
     // The fused row kernels read the key's a half from memory: batches with
     // a compressed key run the split variant instead.
@@ -840,7 +841,7 @@ int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaSt
                 break;
             }
     for (int i0 = 0; i0 < njobs; i0 += kMaxBatch) {
-        int rc = launch_oc_chunk(T, std::min(kMaxBatch, njobs - i0), jobs + i0, variant, st);
+        int rc = launch_oc_chunk(T, std::min(kMaxBatch, njobs - i0), jobs + i0, variant, share_keys, st);
         if (rc != KS_OK) return rc;
     }
     return KS_OK;

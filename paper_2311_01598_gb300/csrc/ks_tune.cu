@@ -30,6 +30,9 @@ static std::vector<ks_schedule> candidates()
     return c;
 }
 
+// Relative timing difference below which stage 1 treats schedules as tied.
+constexpr float kTieFrac = 0.003f;
+
 // Implementation pairs (ntt, bconv) of the second stage, in ms_out order.
 static const int kImpl[4][2] = {{0, 1}, {1, 1}, {0, 0}, {1, 0}};
 
@@ -147,18 +150,23 @@ int ks_autotune(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps, ks_
     if ((rc = tune_events(P, &e0, &e1)) != KS_OK) return rc;
     // stage 1: structure
     std::vector<ks_schedule> c = candidates();
+    std::vector<float> ms(c.size(), 1e30f);
     float best_ms = 1e30f;
-    ks_schedule base = c[0];
     for (size_t i = 0; i < c.size() && rc == KS_OK; ++i) {
-        float m = 0.f;
-        rc = time_schedule(P, n, jobs, c[i], reps, st, e0, e1, &m);
+        rc = time_schedule(P, n, jobs, c[i], reps, st, e0, e1, &ms[i]);
         if (rc != KS_OK) break;
-        if (i < max && ms_out) ms_out[i] = m;
-        if (m < best_ms) {
-            best_ms = m;
-            base = c[i];
-        }
+        if (i < max && ms_out) ms_out[i] = ms[i];
+        best_ms = std::min(best_ms, ms[i]);
     }
+    // Among the schedules within kTieFrac of the fastest (timing noise),
+    // the one with the largest launch groups: the same time in fewer launches.
+    ks_schedule base = c[0];
+    int base_chunk = -1;
+    for (size_t i = 0; i < c.size(); ++i)
+        if (ms[i] <= best_ms * (1.0f + kTieFrac) && c[i].chunk > base_chunk) {
+            base = c[i];
+            base_chunk = c[i].chunk;
+        }
     // stage 2: implementation of the fastest structure
     if (rc == KS_OK) rc = tune_impl(P, n, jobs, reps, st, e0, e1, base, nullptr, best);
     cudaEventDestroy(e0);

@@ -79,8 +79,13 @@ def test_autotune_caches_fastest_and_auto_uses_it():
     cands = P.tune_candidates()
     assert all(c.impl() == (-1, -1) for c in cands)
     best, ms = P.autotune(jobs, reps=2)
-    # stage 1 picks the structure, stage 2 an explicit implementation pair
-    assert len(ms) == len(cands) and best.as_tuple() == cands[int(np.argmin(ms))].as_tuple()
+    # stage 1 picks the structure (the largest launch group among those
+    # within 0.3% of the fastest), stage 2 an explicit implementation pair
+    # (bounds a hair apart: the library compares in float)
+    assert len(ms) == len(cands)
+    loose = [c.as_tuple() for c, m in zip(cands, ms) if m <= min(ms) * 1.0031]
+    tight = [c.chunk for c, m in zip(cands, ms) if m <= min(ms) * 1.0029]
+    assert best.as_tuple() in loose and best.chunk >= max(tight)
     assert best.impl() in ((0, 1), (1, 1), (0, 0), (1, 0))
     cached = P.tune_cache_get(6, 5)
     assert cached is not None and cached.as_tuple() == best.as_tuple() and cached.impl() == best.impl()
