@@ -3,7 +3,6 @@ from __future__ import annotations
 
 import functools
 
-import numpy as np
 import pytest
 
 from oracle import oracle as orc

@@ -2,8 +2,6 @@
 include/ks.h declares (no GPU needed: nothing here launches device work)."""
 import ctypes
 
-import pytest
-
 
 def test_library_exports_header_symbols():
     from paper_2311_01598_gb300 import build, ks

@@ -10,7 +10,7 @@ import pytest
 
 from oracle import oracle as orc
 from paper_2311_01598_gb300 import inputs
-from tests._bigint import centre, crt, mulmod_arr, negacyclic_schoolbook, prod
+from tests._bigint import centre, crt, negacyclic_schoolbook, prod
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
