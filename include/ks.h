@@ -432,7 +432,9 @@ int ks_server_create(const ks_server_config *cfg, ks_server **out);
 /* Finish every queued and running request, then stop and free. */
 void ks_server_destroy(ks_server *server);
 /* Queue a request (thread-safe, non-blocking); *ticket identifies it.
- * Requests whose scratch exceeds the whole budget fail with KS_EINVAL. */
+ * Buffers as for ks_switch (16-byte aligned, not overlapping); requests
+ * that break this, or whose scratch exceeds the whole budget, fail with
+ * KS_EINVAL. */
 int ks_server_submit(ks_server *server, const ks_request *req, uint64_t *ticket);
 /* Wait for a request: its status, or KS_ETIMEOUT if still unfinished after
  * timeout_ms (the request keeps running). */

@@ -285,6 +285,18 @@ int ks_server_submit(ks_server *S, const ks_request *req, uint64_t *ticket)
     if (!P || !req->key || req->key->params != P) return fail(KS_EINVAL, "request key/params mismatch");
     if (req->level_towers < 1 || req->level_towers > (uint32_t)P->nq) return fail(KS_EINVAL, "bad level");
     if (!req->d_in || !req->d_out0 || !req->d_out1) return fail(KS_EINVAL, "NULL data pointer");
+    // the combine kernels move two words at a time
+    if (((uintptr_t)req->d_in | (uintptr_t)req->d_out0 | (uintptr_t)req->d_out1) & 15)
+        return fail(KS_EINVAL, "d_in, d_out0 and d_out1 must be 16-byte aligned");
+    {
+        const size_t len = (size_t)req->level_towers * P->N * sizeof(u64);
+        auto overlap = [len](const void *a, const void *b) {
+            const char *x = (const char *)a, *y = (const char *)b;
+            return x < y + len && y < x + len;
+        };
+        if (overlap(req->d_in, req->d_out0) || overlap(req->d_in, req->d_out1) || overlap(req->d_out0, req->d_out1))
+            return fail(KS_EINVAL, "d_in, d_out0, d_out1 overlap");
+    }
     if (P->device != S->device) return fail(KS_EINVAL, "params on another device");
     Req r;
     r.P = P;

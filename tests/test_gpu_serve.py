@@ -74,3 +74,27 @@ def test_submit_wait_and_admission_limits():
         w0, w1 = ks.empty((12, C.N)), ks.empty((12, C.N))
         P.switch(keys[0], 12, d, w0, w1, "OC")
         assert torch.equal(w0, o0) and torch.equal(w1, o1)
+
+
+def test_submit_rejects_misaligned_and_overlapping_buffers():
+    """Requests with buffers the kernels cannot take (not 16-byte aligned,
+    or outputs overlapping the input) are refused at submission; the server
+    keeps serving valid requests."""
+    torch = need_gpu()
+    ks = built_lib()
+    P, C, evks, keys = _setup(ks, 12, 4, 2, 2, 1, 4)
+    srv = ks.Server(max_inflight_jobs=4, max_batch=4, n_streams=1, hbm_budget_bytes=64 << 20)
+    d = ks.to_device(inputs.uniform_towers(C.q, C.N, seed=720))
+    o0, o1 = ks.empty((4, C.N)), ks.empty((4, C.N))
+    flat = torch.zeros(4 * C.N + 1, dtype=torch.int64, device="cuda")
+    shifted = flat[1:].view(4, C.N)
+    with pytest.raises(RuntimeError, match="16-byte aligned"):
+        srv.submit(P, keys[0], 4, shifted, o0, o1)
+    with pytest.raises(RuntimeError, match="overlap"):
+        srv.submit(P, keys[0], 4, d, d, o1)
+    t = srv.submit(P, keys[0], 4, d, o0, o1)
+    assert srv.wait(t, 60000) == ks.KS_OK
+    srv.close()
+    w0, w1 = ks.empty((4, C.N)), ks.empty((4, C.N))
+    P.switch(keys[0], 4, d, w0, w1, "OC")
+    assert torch.equal(w0, o0) and torch.equal(w1, o1)
