@@ -213,7 +213,7 @@ struct Shape {
     static constexpr int TA = 1 << (LA - RA), TB = 1 << (LB - RB);  // threads per sub-transform
     static constexpr int COLS_W = (256 / TA) < 16 ? 16 : (256 / TA);
     static constexpr int COLS = COLS_W > (1 << LB) ? (1 << LB) : COLS_W;  // columns per column-pass CTA
-    static constexpr int ROWS_W = 256 / TB;
+    static constexpr int ROWS_W = 64 / TB < 1 ? 1 : 64 / TB;
     static constexpr int ROWS = ROWS_W > (1 << LA) ? (1 << LA) : ROWS_W;  // rows per row-pass CTA
     static constexpr int THREADS_A = COLS * TA;
     static constexpr int THREADS_B = ROWS * TB;
@@ -221,12 +221,15 @@ struct Shape {
     static constexpr int ROWPAD = (1 << LB) + (1 << LB) / MB;  // padded row in shared memory
     static constexpr int SMEM_A = (1 << LA) * COLS * 8 + (1 << LA) * 16;
     static constexpr int SMEM_B = ROWS * ROWPAD * 8;
-    // CTAs per SM requested from the register allocator: four (64 registers
-    // a thread) hides the global-load latency of the passes better than the
-    // compiler's default of three; the 32-value column pass of 2^17 stays at
-    // the default (it would spill).
+    // CTAs per SM requested from the register allocator: 64 registers a
+    // thread (four 256-thread column-pass CTAs; sixteen row-pass CTAs of 64
+    // threads, 4 rows at 2^16: each block barrier holds only two warps, and
+    // the forward row pass ran 6% faster with 8-row and 2% faster again with
+    // 4-row blocks than with 16-row ones; 8-column column-pass blocks were
+    // slower); the 32-value column pass of 2^17 stays at the compiler's
+    // default (it would spill).
     static constexpr int MINB_A = LA <= 8 ? 4 : 1;
-    static constexpr int MINB_B = 4;
+    static constexpr int MINB_B = 16;
     // The forward row kernel stages its rows' first-round twiddles (REGB
     // entries a row, REGB-1 used) in shared memory after the row buffers.
     static constexpr int SMEM_BT = SMEM_B + ROWS * REGB * 16;

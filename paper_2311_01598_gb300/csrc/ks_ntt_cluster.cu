@@ -19,18 +19,18 @@
 
 namespace ks {
 
-// Cluster geometry of a two-pass shape, its CTAs widened MUL times (each
-// CTA covers MUL column groups and MUL row groups of the two-pass kernels in
-// parallel): C CTAs per limb.  Supported when the column and row passes
-// split a limb over the same number of CTAs with the same block size, and C
-// is at most 16 (the non-portable cluster limit).
+// Cluster geometry of a two-pass shape: CTAs of MUL column groups of the
+// column pass (COLS columns), C CTAs per limb, each then running the row
+// pass on ROWS = 2^LA / C rows.  Supported when both passes fit the same
+// block size and C is at most 16 (the non-portable cluster limit).
 template <class S, int MUL>
 struct NttClusterShape {
-    static constexpr int COLS = S::COLS * MUL, ROWS = S::ROWS * MUL;
+    static constexpr int COLS = S::COLS * MUL;
     static constexpr int C = (1 << S::LB) / COLS;
-    static constexpr bool OK = C >= 1 && C * COLS == (1 << S::LB) && C == (1 << S::LA) / ROWS &&
-                               S::THREADS_A == S::THREADS_B && C <= 16;
-    static constexpr int THREADS = S::THREADS_A * MUL;
+    static constexpr int ROWS = C > 0 ? (1 << S::LA) / C : 1;
+    static constexpr int THREADS = COLS * S::TA;
+    static constexpr bool OK = C >= 1 && C * COLS == (1 << S::LB) && C * ROWS == (1 << S::LA) &&
+                               ROWS * S::TB == THREADS && C <= 16;
     static constexpr int BLOCKW = S::N / (C > 0 ? C : 1);  // words of a CTA's block of the limb
     static constexpr int BUFW = BLOCKW > ROWS * S::ROWPAD ? BLOCKW : ROWS * S::ROWPAD;
     static constexpr int SMEM = BUFW * 8 + (1 << S::LA) * 16 + ROWS * S::REGB * 16;
