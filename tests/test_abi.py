@@ -1,6 +1,13 @@
 """The C-ABI library builds for sm_103a, loads, and exports every symbol that
 include/ks.h declares (no GPU needed: nothing here launches device work)."""
 import ctypes
+import os
+import re
+import shutil
+import subprocess
+import tempfile
+
+import pytest
 
 
 def test_library_exports_header_symbols():
@@ -46,3 +53,24 @@ def test_product_path_does_not_import_oracle():
                 with open(os.path.join(root, f)) as fh:
                     text = fh.read()
                 assert not re.search(r"\boracle\b.*import|import\s+oracle|from\s+oracle|ks_oracle", text), f
+
+
+def test_header_is_plain_c():
+    """include/ks.h compiles as strict C99 (a C caller needs no C++ and no
+    torch types), every entry point referenced once."""
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    inc = os.path.join(root, "include")
+    text = open(os.path.join(inc, "ks.h")).read()
+    names = sorted(set(re.findall(r"^\w[\w\s\*]*?\b(ks_\w+)\s*\(", text, re.M)))
+    assert "ks_switch" in names and "ks_switch_batch" in names
+    body = "\n".join(f"    (void)&{n};" for n in names)
+    src = f'#include "ks.h"\nint main(void)\n{{\n{body}\n    return 0;\n}}\n'
+    with tempfile.TemporaryDirectory() as tmp:
+        c = os.path.join(tmp, "t.c")
+        open(c, "w").write(src)
+        r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I" + inc, "-fsyntax-only", c],
+                           capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
