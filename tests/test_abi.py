@@ -44,8 +44,6 @@ def test_header_declares_the_boundary():
 
 def test_product_path_does_not_import_oracle():
     """The product package never references the oracle."""
-    import os
-    import re
     pkg = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2311_01598_gb300")
     for root, _, files in os.walk(pkg):
         for f in files:
