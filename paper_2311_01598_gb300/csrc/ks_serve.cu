@@ -45,7 +45,14 @@ struct Req {
 struct Batch {
     std::vector<uint64_t> tickets;
     cudaEvent_t ev = nullptr;
+    size_t lane = 0;
 };
+
+// Batches queued on one lane at most: a further batch would only wait behind
+// them, so requests stay in the server's queue and join a larger batch once
+// a lane frees up (at low load every lane is idle and requests launch at
+// once).
+constexpr int kLaneDepth = 2;
 
 // First-fit allocator over [0, size) with coalescing free list.
 class Pool {
@@ -93,7 +100,7 @@ struct ks_server {
     unsigned char *pool_mem = nullptr;
     ks::Pool pool;
     std::vector<cudaStream_t> lanes;
-    size_t next_lane = 0;
+    std::vector<int> lane_batches;  // batches in flight per lane
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<uint64_t> queue;
@@ -140,12 +147,18 @@ static void scheduler(ks_server *S)
             }
             if (q != cudaSuccess) cudaGetLastError();
             cudaEventDestroy(S->inflight[b].ev);
+            S->lane_batches[S->inflight[b].lane] -= 1;
             S->inflight.erase(S->inflight.begin() + (long)b);
             progress = true;
         }
         if (progress) S->cv_done.notify_all();
         // 2. admit and launch batches, oldest request first
         while (!S->queue.empty() && S->inflight_jobs < S->cfg.max_inflight_jobs) {
+            // the least loaded lane, if any lane has room for another batch
+            size_t li = 0;
+            for (size_t l = 1; l < S->lanes.size(); ++l)
+                if (S->lane_batches[l] < S->lane_batches[li]) li = l;
+            if (S->lane_batches[li] >= kLaneDepth) break;
             const ks_params *P0 = S->reqs[S->queue.front()].P;
             std::vector<uint64_t> take;
             for (auto it = S->queue.begin(); it != S->queue.end();) {
@@ -183,11 +196,12 @@ static void scheduler(ks_server *S)
                 J.nd = nd;
             }
             S->inflight_jobs += (uint32_t)take.size();
-            cudaStream_t lane = S->lanes[S->next_lane++ % S->lanes.size()];
+            cudaStream_t lane = S->lanes[li];
             lk.unlock();
             int rc = launch_oc(P0->tables, (int)jobs.size(), jobs.data(), P0->sched.oc_variant, lane);
             Batch bt;
             bt.tickets = take;
+            bt.lane = li;
             if (cudaEventCreateWithFlags(&bt.ev, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventRecord(bt.ev, lane) != cudaSuccess) {
                 cudaGetLastError();
@@ -211,6 +225,7 @@ static void scheduler(ks_server *S)
             }
             S->n_batches += 1;
             S->max_batch_seen = std::max<uint64_t>(S->max_batch_seen, take.size());
+            S->lane_batches[li] += 1;
             S->inflight.push_back(bt);
             progress = true;
         }
@@ -257,6 +272,7 @@ int ks_server_create(const ks_server_config *cfg, ks_server **out)
         }
         S->lanes.push_back(st);
     }
+    S->lane_batches.assign(S->lanes.size(), 0);
     S->t0 = Clock::now();
     S->worker = std::thread(scheduler, S);
     *out = S;
