@@ -46,6 +46,7 @@ class Schedule(ctypes.Structure):
         return (self.dataflow, self.oc_variant, self.chunk, self.order)
 
     def impl(self):
+        """The implementation fields (ntt, bconv)."""
         return (self.ntt, self.bconv)
 
     def __repr__(self):
@@ -74,6 +75,7 @@ class Job(ctypes.Structure):
 
 
 def lib_path() -> str:
+    """Path of the in-tree CUDA library."""
     return _build.LIB
 
 
@@ -195,6 +197,7 @@ def exported_symbols() -> list[str]:
 
 
 def check(rc: int) -> None:
+    """Raise KSError with ks_last_error() unless rc is KS_OK."""
     if rc != KS_OK:
         raise KSError(rc, lib().ks_last_error().decode())
 
@@ -225,9 +228,11 @@ class Key:
 
     @property
     def nbytes(self) -> int:
+        """ks_key_bytes: device memory the key occupies."""
         return int(lib().ks_key_bytes(self.handle))
 
     def close(self) -> None:
+        """ks_key_destroy (idempotent)."""
         if self.handle:
             lib().ks_key_destroy(self.handle)
             self.handle = None
@@ -261,6 +266,7 @@ class Params:
         self.alpha, self.ndig = alpha.value, ndig.value
 
     def close(self) -> None:
+        """ks_params_destroy (idempotent)."""
         if self.handle:
             lib().ks_params_destroy(self.handle)
             self.handle = None
@@ -272,10 +278,13 @@ class Params:
             pass
 
     def active_digits(self, nact: int) -> int:
+        """Digits holding towers at level nact: ceil(nact / alpha)."""
         return (nact + self.alpha - 1) // self.alpha
 
     # -- keys ---------------------------------------------------------------
     def keygen(self, s, s_prime, seed: int, stream=None) -> Key:
+        """ks_keygen_upload: a key switching s_prime to s (s ternary int8[N],
+        s_prime int64[N] in coefficient form), sampled from seed."""
         s = np.ascontiguousarray(s, dtype=np.int8)
         sp = np.ascontiguousarray(s_prime, dtype=np.int64)
         h = ctypes.c_void_p()
@@ -294,6 +303,8 @@ class Params:
         return Key(self, h.value)
 
     def upload_key(self, evk: np.ndarray, stream=None) -> Key:
+        """ks_key_upload_raw: an evaluation key given in full,
+        [ndig][2][nq+kp][N] canonical words in evaluation form."""
         evk = np.ascontiguousarray(evk, dtype=np.uint64)
         assert evk.shape == (self.ndig, 2, self.nq + self.kp, self.N)
         h = ctypes.c_void_p()
@@ -302,6 +313,8 @@ class Params:
 
     # -- key switching --------------------------------------------------------
     def switch(self, key: Key, nact: int, d, out0, out1, dataflow=OC, stream=None) -> None:
+        """ks_switch: key switch of d ([nact][N], evaluation form) into
+        out0, out1 under dataflow "MP", "DC", "OC" or "AUTO"."""
         df = DATAFLOWS[dataflow] if isinstance(dataflow, str) else dataflow
         check(lib().ks_switch(self.handle, key.handle, nact, _ptr(d), _ptr(out0), _ptr(out1), df,
                               _stream_handle(stream)))
@@ -352,7 +365,8 @@ class Params:
                                       _stream_handle(stream)))
 
     def switch_batch(self, jobs, dataflow=OC, stream=None) -> None:
-        """jobs: iterable of (key, nact, d, out0, out1)."""
+        """ks_switch_batch: jobs is an iterable of (key, nact, d, out0, out1);
+        "AUTO" uses the tuned schedule of the batch's signature."""
         df = DATAFLOWS[dataflow] if isinstance(dataflow, str) else dataflow
         jobs = list(jobs)
         arr = (Job * max(1, len(jobs)))()
@@ -369,19 +383,23 @@ class Params:
         return arr, len(jobs)
 
     def switch_batch_sched(self, jobs, schedule: "Schedule", stream=None) -> None:
+        """ks_switch_batch_sched: the batch run under an explicit schedule."""
         arr, n = self._jobs(jobs)
         check(lib().ks_switch_batch_sched(self.handle, n, arr, ctypes.byref(schedule), _stream_handle(stream)))
 
     def default_schedule(self) -> "Schedule":
+        """ks_get_default_schedule: the schedule of single calls and non-AUTO batches."""
         sc = Schedule()
         check(lib().ks_get_default_schedule(self.handle, ctypes.byref(sc)))
         return sc
 
     def set_default_schedule(self, schedule: "Schedule") -> None:
+        """ks_set_default_schedule."""
         check(lib().ks_set_default_schedule(self.handle, ctypes.byref(schedule)))
 
     # -- autotuning -----------------------------------------------------------
     def tune_candidates(self) -> list:
+        """ks_tune_candidates: the structural schedules, in the cost model's order."""
         n = ctypes.c_uint32()
         check(lib().ks_tune_candidates(self.handle, 0, None, ctypes.byref(n)))
         arr = (Schedule * n.value)()
@@ -389,7 +407,9 @@ class Params:
         return [arr[i] for i in range(n.value)]
 
     def autotune(self, jobs, reps: int = 3, stream=None):
-        """Time every candidate schedule on the batch; returns (best, [ms])."""
+        """ks_autotune: times the structural candidates (returned ms, in
+        candidate order), then the fastest one under each implementation
+        pair; returns (best, [ms]) and caches best for KS_AUTO."""
         arr, n = self._jobs(jobs)
         nc = len(self.tune_candidates())
         ms = (ctypes.c_float * nc)()
@@ -408,20 +428,25 @@ class Params:
         return best, [float(x) for x in ms]
 
     def tune_cache_put(self, n_jobs: int, mean_level: int, schedule: "Schedule") -> None:
+        """ks_tune_cache_put: the schedule KS_AUTO uses for this batch signature."""
         check(lib().ks_tune_cache_put(self.handle, n_jobs, mean_level, ctypes.byref(schedule)))
 
     def tune_cache_get(self, n_jobs: int, mean_level: int):
+        """ks_tune_cache_get: the cached schedule of a signature, or None."""
         sc = Schedule()
         rc = lib().ks_tune_cache_get(self.handle, n_jobs, mean_level, ctypes.byref(sc))
         return sc if rc == KS_OK else None
 
     def tune_cache_save(self, path: str) -> None:
+        """ks_tune_cache_save: the cache as text keyed by device and parameter set."""
         check(lib().ks_tune_cache_save(self.handle, path.encode()))
 
     def tune_cache_load(self, path: str) -> None:
+        """ks_tune_cache_load: lines for this device and parameter set are merged in."""
         check(lib().ks_tune_cache_load(self.handle, path.encode()))
 
     def key_synthetic(self, seed: int, stream=None) -> Key:
+        """ks_key_synthetic: a key of pseudo-random residues (timing and tuning only)."""
         h = ctypes.c_void_p()
         check(lib().ks_key_synthetic(self.handle, seed & (2**64 - 1), _stream_handle(stream), ctypes.byref(h)))
         return Key(self, h.value)
@@ -438,13 +463,17 @@ class Params:
 
     # -- stages ----------------------------------------------------------------
     def ntt(self, first_tower: int, data, inverse: bool = False, stream=None) -> None:
+        """ks_ntt: in-place forward (canonical output) or inverse negacyclic NTT
+        of data[i] in the tower first_tower + i."""
         n = data.shape[0]
         check(lib().ks_ntt(self.handle, first_tower, n, _ptr(data), 1 if inverse else 0, _stream_handle(stream)))
 
     def modup(self, nact: int, d, ext, stream=None) -> None:
+        """ks_modup: ModUp P1-P3 of d into the raised digits ext."""
         check(lib().ks_modup(self.handle, nact, _ptr(d), _ptr(ext), _stream_handle(stream)))
 
     def moddown(self, nact: int, cp, out, stream=None) -> None:
+        """ks_moddown: ModDown P1-P4 of cp (over D_l) into out."""
         check(lib().ks_moddown(self.handle, nact, _ptr(cp), _ptr(out), _stream_handle(stream)))
 
 
@@ -460,6 +489,7 @@ class Server:
         self._keep = []
 
     def close(self):
+        """ks_server_destroy: finish every request, then stop (idempotent)."""
         if self.handle:
             lib().ks_server_destroy(self.handle)
             self.handle = None
@@ -472,23 +502,28 @@ class Server:
 
     @staticmethod
     def request(params, key, nact, d, out0, out1) -> Request:
+        """A ks_request for submit or run_trace."""
         return Request(params.handle, key.handle, nact, _ptr(d).value, _ptr(out0).value, _ptr(out1).value)
 
     def submit(self, params, key, nact, d, out0, out1) -> int:
+        """ks_server_submit: queue a key switch; returns its ticket."""
         t = ctypes.c_uint64()
         r = self.request(params, key, nact, d, out0, out1)
         check(lib().ks_server_submit(self.handle, ctypes.byref(r), ctypes.byref(t)))
         return t.value
 
     def wait(self, ticket: int, timeout_ms: int = 60000) -> int:
+        """ks_server_wait: KS_OK once the request is done, KS_ETIMEOUT if not yet."""
         return int(lib().ks_server_wait(self.handle, ticket, timeout_ms))
 
     def times(self, ticket: int):
+        """ks_server_times: (arrival, admission, completion) in seconds of the server's clock."""
         a, m, d = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
         check(lib().ks_server_times(self.handle, ticket, ctypes.byref(a), ctypes.byref(m), ctypes.byref(d)))
         return a.value, m.value, d.value
 
     def stats(self):
+        """ks_server_stats: requests done, batches launched, largest batch."""
         a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
         check(lib().ks_server_stats(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"done": a.value, "batches": b.value, "max_batch": c.value}
@@ -516,6 +551,7 @@ class Mlp:
         self.dims = list(dims)
 
     def close(self):
+        """ks_mlp_destroy (idempotent)."""
         if self.handle:
             lib().ks_mlp_destroy(self.handle)
             self.handle = None
@@ -528,25 +564,30 @@ class Mlp:
 
     @property
     def nparams(self) -> int:
+        """ks_mlp_num_params: weights and biases of every layer."""
         return int(lib().ks_mlp_num_params(self.handle))
 
     def get_params(self) -> np.ndarray:
+        """ks_mlp_get_params: the flat parameter vector (host copy)."""
         out = np.zeros(self.nparams, dtype=np.float32)
         check(lib().ks_mlp_get_params(self.handle, _ptr(out)))
         return out
 
     def set_params(self, p) -> None:
+        """ks_mlp_set_params: replace the flat parameter vector."""
         p = np.ascontiguousarray(p, dtype=np.float32)
         assert p.size == self.nparams
         check(lib().ks_mlp_set_params(self.handle, _ptr(p)))
 
     def forward(self, x, stream=None):
+        """ks_mlp_forward: y = MLP(x) for x [batch][dims[0]] on the GPU."""
         import torch
         y = torch.empty((x.shape[0], self.dims[-1]), dtype=torch.float32, device=x.device)
         check(lib().ks_mlp_forward(self.handle, x.shape[0], _ptr(x), _ptr(y), _stream_handle(stream)))
         return y
 
     def gradients(self, x, t, mask=None, stream=None):
+        """ks_mlp_gradients: (masked mean-square loss, flat gradient)."""
         g = np.zeros(self.nparams, dtype=np.float32)
         loss = ctypes.c_float()
         check(lib().ks_mlp_gradients(self.handle, x.shape[0], _ptr(x), _ptr(t), _ptr(mask), _ptr(g),
@@ -554,6 +595,7 @@ class Mlp:
         return float(loss.value), g
 
     def train_step(self, x, t, lr: float, mask=None, stream=None) -> float:
+        """ks_mlp_train_step: one full-batch Adam step; returns the loss before it."""
         loss = ctypes.c_float()
         check(lib().ks_mlp_train_step(self.handle, x.shape[0], _ptr(x), _ptr(t), _ptr(mask), lr,
                                       ctypes.byref(loss), _stream_handle(stream)))
@@ -562,6 +604,7 @@ class Mlp:
 
 # -- measurement hooks ---------------------------------------------------------------
 def kernel_launches() -> int:
+    """ks_kernel_launches: library kernel launches so far in this process."""
     return int(lib().ks_kernel_launches())
 
 
@@ -587,6 +630,7 @@ def probe_inv_bfly(iters: int = 4096) -> float:
 
 
 def profile_enable(on: bool = True) -> None:
+    """ks_profile_enable: bracket every library launch with CUDA events."""
     lib().ks_profile_enable(1 if on else 0)
 
 
@@ -606,14 +650,17 @@ def profile_collect(max_names: int = 64) -> dict:
 
 # -- torch helpers (device memory only) ------------------------------------------
 def to_device(a: np.ndarray, device="cuda"):
+    """uint64 numpy array -> int64 torch tensor on the GPU (same bits)."""
     import torch
     return torch.from_numpy(np.ascontiguousarray(a, dtype=np.uint64).view(np.int64)).to(device)
 
 
 def to_host(t) -> np.ndarray:
+    """int64 torch tensor -> uint64 numpy array (same bits)."""
     return t.cpu().numpy().view(np.uint64)
 
 
 def empty(shape, device="cuda"):
+    """Uninitialised int64 device tensor for library outputs."""
     import torch
     return torch.empty(shape, dtype=torch.int64, device=device)
