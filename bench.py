@@ -42,6 +42,7 @@ ALG_BYTES_PER_KS = NQ * LIMB + DNUM * 2 * (NQ + KP) * LIMB + 2 * NQ * LIMB
 
 
 def peaks():
+    """(HBM copy GB/s, maximum SM MHz, source): the measured peaks file, else the fallback figures."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
@@ -106,6 +107,7 @@ def class_work(nact=NQ):
 
 
 def workload_config(B, dataflow, world):
+    """The `config` object of the JSON line."""
     return {"workload": f"hybrid key switch N=2^16 L+1=24 K=8 dnum=3 alpha=8 54-bit primes, {B} "
                         f"ciphertexts/step each with its own Galois key, {dataflow} batched",
             "batch_per_gpu": B, "dataflow": dataflow, "parallelism": f"replicas x{world}",
@@ -196,6 +198,7 @@ class ClockSampler:
         self.thread = None
 
     def start(self):
+        """Start sampling nvidia-smi in the background."""
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
@@ -211,6 +214,7 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def stop(self):
+        """Stop sampling; returns the clock summary."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         time.sleep(0.2)
@@ -264,6 +268,7 @@ def oracle_rate(seconds: float = 10.0, min_reps: int = 2):
 
 # ------------------------------------------------------------------ main
 def main():
+    """Parse the arguments and print one JSON line (our arm or the reference arm)."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)

@@ -24,6 +24,7 @@ SOURCES = ["ks_kernels.cu", "ks_oc.cu", "ks_api.cu", "ks_host.cpp", "ks_noalloc.
 
 
 def nvcc() -> str:
+    """Path of nvcc (PATH or /usr/local/cuda)."""
     for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
             return cand
@@ -51,6 +52,7 @@ def _compile(src: str) -> str:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile changed sources in parallel and link the library; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
     if force:

@@ -37,6 +37,7 @@ def max_over_ranks(x: float, device=None) -> float:
 
 
 def sum_over_ranks(x: float, device=None) -> float:
+    """Sum of a value over all ranks (the value itself without a process group)."""
     import torch
     import torch.distributed as dist
     if not (dist.is_available() and dist.is_initialized()):

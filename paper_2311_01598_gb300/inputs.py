@@ -21,6 +21,7 @@ SEED_BASE = 0xC1F10
 
 
 def rng(seed: int) -> np.random.Generator:
+    """The seeded generator every input comes from (numpy PCG64)."""
     return np.random.Generator(np.random.PCG64(seed))
 
 
@@ -34,6 +35,7 @@ def uniform_towers(primes, N: int, seed: int) -> np.ndarray:
 
 
 def ternary_secret(N: int, seed: int) -> np.ndarray:
+    """A uniform ternary secret in coefficient form (int8[N])."""
     return rng(seed).integers(-1, 2, size=N, dtype=np.int64).astype(np.int8)
 
 

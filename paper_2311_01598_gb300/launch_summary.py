@@ -38,6 +38,7 @@ KERNEL_SOURCES = ("csrc/ks_kernels.cu", "csrc/ks_oc.cu", "csrc/ks_bconv_tc.cu", 
 
 
 def kernel_sources_sha() -> str:
+    """SHA-256 over the device-code files whose change invalidates the recorded traffic."""
     h = hashlib.sha256()
     for rel in KERNEL_SOURCES:
         with open(os.path.join(HERE, rel), "rb") as f:
@@ -79,6 +80,7 @@ def read_launches(path):
 
 
 def summarise(rows, first, count):
+    """Per-kernel (name, launches, total ns, share) over the window [first, first+count)."""
     win = rows[first:first + count] if count else rows[first:]
     per = {}
     for name, _, ns in win:
@@ -90,6 +92,7 @@ def summarise(rows, first, count):
 
 
 def to_markdown(table, total, n):
+    """The summary as a markdown table."""
     out = [f"{n} launches, {total / 1e3:.1f} us total (ncu: cold cache, serialised)", "",
            "| kernel | launches | total us | share |", "|---|---|---|---|"]
     for name, c, t, sh in table:
@@ -141,6 +144,7 @@ def traffic_from_report(rep, key_switches):
 
 
 def main_traffic(argv):
+    """`traffic` subcommand: record DRAM bytes per key switch from an ncu report."""
     ap = argparse.ArgumentParser()
     ap.add_argument("report")
     ap.add_argument("--key-switches", type=int, required=True)
@@ -155,6 +159,7 @@ def main_traffic(argv):
 
 
 def main():
+    """Command line: summarise a launch list, or `traffic`."""
     import sys
     if len(sys.argv) > 1 and sys.argv[1] == "traffic":
         return main_traffic(sys.argv[2:])

@@ -17,6 +17,7 @@ from . import inputs, ks
 
 
 def main():
+    """Run the key switches to be profiled (see the module docstring)."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--dataflow", default="OC")
     ap.add_argument("--logN", type=int, default=16)

@@ -18,6 +18,7 @@ import numpy as np
 
 
 def build_mix(seed=0, n_bufsets=96):
+    """Parameter sets, device-resident keys and reusable buffers of the serving mix."""
     import torch
 
     from . import inputs, ks
@@ -34,6 +35,7 @@ def build_mix(seed=0, n_bufsets=96):
 
 
 def make_trace(mix, n, rate, seed):
+    """n requests of the mix with Poisson arrival times at the given rate."""
     from . import inputs, ks
     p16, p17, keys16, keys17, bufs16, bufs17 = mix
     rng = np.random.default_rng(seed)
@@ -54,6 +56,7 @@ def make_trace(mix, n, rate, seed):
 
 
 def run(rates, n, seed=0, slots=48, batch=16, lanes=3, budget_gib=24):
+    """Replay one trace per offered rate through a fresh server; one result dict per rate."""
     from . import ks
     mix = build_mix(seed)
     out = []
@@ -78,6 +81,7 @@ def run(rates, n, seed=0, slots=48, batch=16, lanes=3, budget_gib=24):
 
 
 def main():
+    """Command line: one JSON line per offered rate."""
     ap = argparse.ArgumentParser()
     ap.add_argument("--rates", default="500,1000,2000,3000,4000")
     ap.add_argument("--n", type=int, default=1500)

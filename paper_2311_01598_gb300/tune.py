@@ -42,6 +42,7 @@ def features(logN, nq, dnum, kp, batch):
 
 
 def sample_workload(rng):
+    """One workload (logN, nq, dnum, kp, batch) of the cost-model domain."""
     logN = int(rng.integers(13, 18))
     nq = int(rng.integers(2, 49))
     dnum = int(rng.integers(1, nq + 1))
@@ -82,11 +83,13 @@ def collect(n_workloads, seed, out_path, reps=2, log=print):
 
 
 def load(path):
+    """Rows of a timing dataset (JSON lines)."""
     with open(path) as f:
         return [json.loads(l) for l in f if l.strip()]
 
 
 def arrays(rows):
+    """Features X and targets T (log time per key switch, one per candidate)."""
     X = np.stack([features(r["logN"], r["nq"], r["dnum"], r["kp"], r["batch"]) for r in rows])
     # target: log of time per key switch (ms), one per candidate
     T = np.array([[math.log(m / r["batch"]) for m in r["ms"]] for r in rows], dtype=np.float32)
@@ -100,17 +103,20 @@ class CostModel:
         self.mlp, self.t_mean, self.t_scale = mlp, float(t_mean), float(t_scale)
 
     def predict(self, X):
+        """Predicted log time per key switch of every candidate for each row of X."""
         import torch
         x = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
         y = self.mlp.forward(x).cpu().numpy()
         return y * self.t_scale + self.t_mean
 
     def save(self, path):
+        """Parameters and target normalisation as .npz."""
         np.savez(path, params=self.mlp.get_params(), dims=np.array(self.mlp.dims), t_mean=self.t_mean,
                  t_scale=self.t_scale)
 
     @staticmethod
     def load(path):
+        """A model saved by save()."""
         from . import ks
         z = np.load(path)
         m = ks.Mlp([int(v) for v in z["dims"]])
@@ -160,12 +166,14 @@ def evaluate(model, rows, default_index):
 
 
 def split(rows, frac=0.8, seed=0):
+    """Seeded train/test split of the rows."""
     idx = np.random.default_rng(seed).permutation(len(rows))
     k = int(len(rows) * frac)
     return [rows[i] for i in idx[:k]], [rows[i] for i in idx[k:]]
 
 
 def default_candidate_index(candidates, default):
+    """Index of the default schedule among the candidates."""
     return [c.as_tuple() for c in candidates].index(default.as_tuple())
 
 
@@ -176,6 +184,7 @@ def choose(model, params, batch, candidates):
 
 
 def main():
+    """Command line: `collect` timings on the GPU or `train` the cost model."""
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
     c = sub.add_parser("collect")
