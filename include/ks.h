@@ -228,15 +228,26 @@ int ks_switch_batch(const ks_params *params, uint32_t n, const ks_job *h_jobs,
  * KS_OC, but the scratch is one static device array of
  * ks_switch_noalloc_max_words() words (32 MiB), reserved on every GPU that
  * loads the library until the process exits.
- *   - Requests needing more scratch (n_words grows with N, the level and K)
- *     fail with KS_EINVAL and a message giving both sizes; nothing runs.
+ *   - Argument errors are refused as ks_switch refuses them (KS_EINVAL
+ *     before any launch): level outside 1..n_q, NULL, overlapping, or not
+ *     16-byte aligned d_in/d_out0/d_out1.
+ *   - The scratch needed is (nact + nd*(nact+K) + 2*nact + 2*(nact+K)) * N
+ *     words at level nact (nd = active digits); e.g. N=2^16, 24+8 primes,
+ *     dnum 3 at the top level needs 232 limbs, 15.2 million words.
+ *     Requests needing more than the array holds fail with KS_EINVAL and a
+ *     message giving both sizes; nothing runs.
+ *   - Runs with the parameter set's current schedule and engines (as
+ *     ks_switch with KS_OC does, including after ks_set_default_schedule).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress, with that device current); make that first call
  *     before any stream capture.
  *   - No cudaMalloc, cudaFree or allocating library routine is called.
  *   - All calls share the one array: calls that may overlap on the GPU (on
  *     different streams without ordering between them) race and must not be
- *     issued.  Nothing in the array needs to start at zero. */
+ *     issued.  Nothing in the array needs to start at zero.
+ *   - The array's address is kept for the life of the process:
+ *     cudaDeviceReset while the library is in use is not supported (it also
+ *     frees every params object's and key's device memory). */
 int ks_switch_noalloc(const ks_params *params, const ks_key *key, uint32_t level_towers,
                       const uint64_t *d_in, uint64_t *d_out0, uint64_t *d_out1, ks_stream_t stream);
 /* Words of the static scratch array of ks_switch_noalloc. */

@@ -330,7 +330,7 @@ static int run_dc(const ks_params *P, const Tables &T, const ks_key *K, int nact
 }
 
 // ------------------------------------------------------------------ OC
-static OcJob oc_job(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, u64 *scratch)
+OcJob oc_job(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, u64 *scratch)
 {
     const size_t N = P->N;
     const int nd = active_digits(P, nact);
@@ -353,6 +353,40 @@ static int run_oc(const ks_params *P, const Tables &T, int oc_variant, const ks_
 {
     OcJob J = oc_job(P, K, nact, d, out0, out1, w->oc);
     return launch_oc(T, 1, &J, oc_variant, st);
+}
+
+// Tables of one call: the parameter set's tables with the schedule's
+// implementation choices applied (-1 keeps the parameter set's option).
+Tables call_tables(const ks_params *P, const ks_schedule &sc)
+{
+    Tables T = P->tables;
+    if (sc.bconv == 0) {
+        T.up_tc = nullptr;
+        T.dn_tc = nullptr;
+    } else if (sc.bconv == 1) {
+        T.up_tc = P->d_up_tc;  // null where the parameter set has no tensor-core form
+        T.dn_tc = P->d_dn_tc;
+    }
+    if (sc.ntt >= 0) T.ntt_cluster = sc.ntt;
+    return T;
+}
+
+int check_job(const ks_params *P, const ks_key *K, uint32_t nact, const uint64_t *d, const uint64_t *o0,
+              const uint64_t *o1)
+{
+    if (!K || K->params != P) return fail(KS_EINVAL, "key is NULL or belongs to another params object");
+    if (nact < 1 || nact > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
+    if (!d || !o0 || !o1) return fail(KS_EINVAL, "NULL data pointer");
+    // the combine kernels move two words at a time
+    if (((uintptr_t)d | (uintptr_t)o0 | (uintptr_t)o1) & 15)
+        return fail(KS_EINVAL, "d_in, d_out0 and d_out1 must be 16-byte aligned");
+    const size_t bytes = (size_t)nact * P->N * sizeof(u64);
+    auto overlap = [bytes](const void *a, const void *b) {
+        const char *x = (const char *)a, *y = (const char *)b;
+        return x < y + bytes && y < x + bytes;
+    };
+    if (overlap(d, o0) || overlap(d, o1) || overlap(o0, o1)) return fail(KS_EINVAL, "d_in, d_out0, d_out1 overlap");
+    return KS_OK;
 }
 
 static int check_params(const ks_params *P)
@@ -657,22 +691,6 @@ static int keygen_impl(const ks_params *P, const int8_t *h_s, const int64_t *h_s
     return KS_OK;
 }
 
-// Tables of one call: the parameter set's tables with the schedule's
-// implementation choices applied (-1 keeps the parameter set's option).
-static Tables call_tables(const ks_params *P, const ks_schedule &sc)
-{
-    Tables T = P->tables;
-    if (sc.bconv == 0) {
-        T.up_tc = nullptr;
-        T.dn_tc = nullptr;
-    } else if (sc.bconv == 1) {
-        T.up_tc = P->d_up_tc;  // null where the parameter set has no tensor-core form
-        T.dn_tc = P->d_dn_tc;
-    }
-    if (sc.ntt >= 0) T.ntt_cluster = sc.ntt;
-    return T;
-}
-
 static int switch_one(ks_params *P, const Tables &T, int oc_variant, const ks_key *K, uint32_t nact, const uint64_t *d,
                       uint64_t *o0, uint64_t *o1, ks_dataflow df, cudaStream_t st)
 {
@@ -688,24 +706,6 @@ static int switch_one(ks_params *P, const Tables &T, int oc_variant, const ks_ke
     case KS_AUTO: return run_oc(P, T, oc_variant, K, (int)nact, d, o0, o1, w, st);
     }
     return fail(KS_EINVAL, "unknown dataflow");
-}
-
-static int check_job(const ks_params *P, const ks_key *K, uint32_t nact, const uint64_t *d, const uint64_t *o0,
-                     const uint64_t *o1)
-{
-    if (!K || K->params != P) return fail(KS_EINVAL, "key is NULL or belongs to another params object");
-    if (nact < 1 || nact > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
-    if (!d || !o0 || !o1) return fail(KS_EINVAL, "NULL data pointer");
-    // the combine kernels move two words at a time
-    if (((uintptr_t)d | (uintptr_t)o0 | (uintptr_t)o1) & 15)
-        return fail(KS_EINVAL, "d_in, d_out0 and d_out1 must be 16-byte aligned");
-    const size_t bytes = (size_t)nact * P->N * sizeof(u64);
-    auto overlap = [bytes](const void *a, const void *b) {
-        const char *x = (const char *)a, *y = (const char *)b;
-        return x < y + bytes && y < x + bytes;
-    };
-    if (overlap(d, o0) || overlap(d, o1) || overlap(o0, o1)) return fail(KS_EINVAL, "d_in, d_out0, d_out1 overlap");
-    return KS_OK;
 }
 
 int ks_switch(const ks_params *P, const ks_key *K, uint32_t level_towers, const uint64_t *d_in, uint64_t *d_out0,

@@ -168,6 +168,17 @@ struct OcJob {
 };
 // Scratch words one job needs at level nact.
 size_t oc_scratch_words(const Tables &T, int nact);
+// The job of one key switch with its scratch (oc_scratch_words words) at
+// `scratch`: y, then the section temporaries, then c' (ks_api.cu).
+OcJob oc_job(const ks_params *P, const ks_key *K, int nact, const u64 *d, u64 *out0, u64 *out1, u64 *scratch);
+// Host-side checks of one job's arguments (key of this parameter set, level
+// in 1..n_q, non-NULL, 16-byte aligned, non-overlapping buffers); KS_OK or
+// KS_EINVAL with the message set (ks_api.cu).
+int check_job(const ks_params *P, const ks_key *K, uint32_t nact, const uint64_t *d, const uint64_t *o0,
+              const uint64_t *o1);
+// The parameter set's tables with a schedule's implementation choices
+// (base-conversion engine, NTT form) applied (ks_api.cu).
+Tables call_tables(const ks_params *P, const ks_schedule &sc);
 // Output-Centric variants: FUSED runs each section's row pass, key product
 // and ModDown step in one kernel per row block; SPLIT runs the row passes
 // with the plain row-pass kernel and the key product / subtraction in a

@@ -49,8 +49,10 @@ static int noalloc_scratch(int device, u64 **out)
 }
 
 // Scratch words the Output-Centric schedule needs at level nact: y (nact
-// limbs), the section temporaries (max(nd*K, (nd+2)*nact) limbs) and c'
-// (2*(nact+K) limbs).
+// limbs), the section temporaries (nd*(nact+K) + 2*nact limbs, nd the active
+// digits) and c' (2*(nact+K) limbs), each limb N words.  The layout is the
+// one oc_job builds for ks_switch, so the check below and the kernels' writes
+// agree by construction.
 static size_t noalloc_words(const ks_params *P, int nact) { return oc_scratch_words(P->tables, nact); }
 
 }  // namespace ks
@@ -63,16 +65,11 @@ extern "C" int ks_switch_noalloc(const ks_params *P, const ks_key *K, uint32_t l
                                  uint64_t *d_out0, uint64_t *d_out1, ks_stream_t stream)
 {
     if (!P) return fail(KS_EINVAL, "params is NULL");
-    if (!K || K->params != P) return fail(KS_EINVAL, "key is NULL or belongs to another params object");
-    if (level_towers < 1 || level_towers > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
-    if (!d_in || !d_out0 || !d_out1) return fail(KS_EINVAL, "NULL data pointer");
-    const size_t bytes = (size_t)level_towers * P->N * sizeof(u64);
-    auto overlap = [bytes](const void *a, const void *b) {
-        const char *x = (const char *)a, *y = (const char *)b;
-        return x < y + bytes && y < x + bytes;
-    };
-    if (overlap(d_in, d_out0) || overlap(d_in, d_out1) || overlap(d_out0, d_out1))
-        return fail(KS_EINVAL, "d_in, d_out0, d_out1 overlap");
+    // the same argument checks as ks_switch: level range, NULL pointers,
+    // 16-byte alignment (the combine kernels move two words at a time) and
+    // overlapping buffers, all before anything is launched
+    int rc = check_job(P, K, level_towers, d_in, d_out0, d_out1);
+    if (rc != KS_OK) return rc;
     const int nact = (int)level_towers;
     const size_t need = noalloc_words(P, nact);
     if (need > kNoAllocScratchWords)
@@ -84,22 +81,11 @@ extern "C" int ks_switch_noalloc(const ks_params *P, const ks_key *K, uint32_t l
         return fail(KS_ECUDA, "cudaSetDevice failed");
     }
     u64 *base = nullptr;
-    int rc = noalloc_scratch(P->device, &base);
-    if (rc != KS_OK) return rc;
+    if ((rc = noalloc_scratch(P->device, &base)) != KS_OK) return rc;
     // Every scratch word the schedule reads is written earlier in the same
     // call, so nothing needs clearing between calls.
-    const size_t N = P->N;
-    const int nd = (nact + P->alpha - 1) / P->alpha;
-    OcJob J;
-    J.d = d_in;
-    J.out0 = d_out0;
-    J.out1 = d_out1;
-    J.key = key_view(K);
-    J.y = base;
-    J.tmp = J.y + (size_t)nact * N;
-    J.cp = J.tmp + ((size_t)nd * (nact + P->kp) + 2 * (size_t)nact) * N;
-    J.pre = P->d_up_pre_lvl + (size_t)(nact - 1) * P->nq;
-    J.nact = nact;
-    J.nd = nd;
-    return launch_oc(P->tables, 1, &J, P->sched.oc_variant, (cudaStream_t)stream);
+    const OcJob J = oc_job(P, K, nact, d_in, d_out0, d_out1, base);
+    // the default schedule's variant and engines, as ks_switch applies them
+    // with KS_OC (so both calls run the same kernels)
+    return launch_oc(call_tables(P, P->sched), 1, &J, P->sched.oc_variant, (cudaStream_t)stream);
 }
