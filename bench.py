@@ -379,9 +379,9 @@ def main():
     prof = ks.profile_collect()
     top = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
 
-    # ---- both Output-Centric variants on the same batch (schedule comparison)
+    # ---- every Output-Centric variant on the same batch (schedule comparison)
     variants = {}
-    for vname, v in (("fused", 0), ("split", 1), ("whole", 2)):
+    for vname, v in (("fused", 0), ("split", 1), ("whole", 2), ("tower", 3)):
         sc = ks.Schedule(2, v, 64, 0)
         f = lambda sc=sc: P.switch_batch_sched(jobs, sc, stream)  # noqa: E731
         t = timed(f, max(3, args.steps // 2), 2)

@@ -287,7 +287,12 @@ typedef struct {
                             ModDown step in one kernel per row block), 1 = split
                             (plain row pass, then a streaming combine kernel),
                             2 = whole basis (one base conversion and one NTT
-                            launch over every raised limb, then the combines)  */
+                            launch over every raised limb, then the combines),
+                            3 = one thread-block-cluster kernel per output
+                            tower (ModUp base conversion, NTTs, key product,
+                            ModDown, subtraction with the tower's limbs on
+                            chip; ring degrees with a cluster geometry and
+                            full keys, else run as 1)                          */
     int32_t chunk;       /* KS_OC: jobs per batched launch group, 1..64           */
     int32_t order;       /* 0 = jobs in the given order, 1 = grouped by level
                             (descending), 2 = grouped by key (KS_OC: jobs of a

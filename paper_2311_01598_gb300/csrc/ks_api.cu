@@ -800,7 +800,7 @@ int check_schedule(const ks_schedule *sc)
 {
     if (!sc) return fail(KS_EINVAL, "schedule is NULL");
     if (sc->dataflow < KS_MP || sc->dataflow > KS_OC) return fail(KS_EINVAL, "schedule dataflow must be MP, DC or OC");
-    if (sc->oc_variant < 0 || sc->oc_variant > 2) return fail(KS_EINVAL, "schedule oc_variant must be 0, 1 or 2");
+    if (sc->oc_variant < 0 || sc->oc_variant > 3) return fail(KS_EINVAL, "schedule oc_variant must be 0, 1, 2 or 3");
     if (sc->chunk < 1 || sc->chunk > kMaxBatch) return fail(KS_EINVAL, "schedule chunk must be in 1..64");
     if (sc->order < 0 || sc->order > 2) return fail(KS_EINVAL, "schedule order must be 0, 1 or 2");
     if (sc->ntt < -1 || sc->ntt > 2) return fail(KS_EINVAL, "schedule ntt must be -1, 0, 1 or 2");

@@ -166,6 +166,13 @@ struct OcJob {
     const ulonglong2 *pre;  // ModUp P1 factors of the level
     int nact, nd;
 };
+// The jobs of one Output-Centric launch group, with prefix counts of their Q
+// towers: job j owns Q-section items [pre[j], pre[j+1]).
+struct OcJobs {
+    int n;
+    int pre[kMaxBatch + 1];
+    OcJob job[kMaxBatch];
+};
 // Scratch words one job needs at level nact.
 size_t oc_scratch_words(const Tables &T, int nact);
 // The job of one key switch with its scratch (oc_scratch_words words) at
@@ -185,7 +192,15 @@ Tables call_tables(const ks_params *P, const ks_schedule &sc);
 // streaming combine kernel; WHOLE raises every digit to every tower in one
 // base-conversion launch and one NTT launch, then runs the same per-tower
 // combine kernels (special towers, ModDown, Q towers).
-enum { KS_OC_FUSED = 0, KS_OC_SPLIT = 1, KS_OC_WHOLE = 2 };
+enum { KS_OC_FUSED = 0, KS_OC_SPLIT = 1, KS_OC_WHOLE = 2, KS_OC_TOWER = 3 };
+// TOWER: the split variant's prep and special-tower section, then one
+// thread-block-cluster kernel per (job, Q output tower) that keeps the
+// tower's limbs on chip from ModUp base conversion to the ModDown
+// subtraction (ks_oc_tower.cu).  KS_EUNSUPPORTED (nothing launched) where
+// the ring degree has no cluster geometry, the device cannot run it, or a
+// job's key is compressed.
+bool oc_tower_supported(const Tables &T);
+int launch_oc_tower(const Tables &T, const OcJobs &oj, cudaStream_t st);
 // share_keys: jobs of a launch that share a key run through the key-grouped
 // combine kernels (each key word read once per group of jobs); otherwise
 // every job streams its own key limbs.

@@ -23,12 +23,6 @@
 
 namespace ks {
 
-struct OcJobs {
-    int n;
-    int pre[kMaxBatch + 1];  // Q-section row blocks of job j: [pre[j], pre[j+1]) (units of towers)
-    OcJob job[kMaxBatch];
-};
-
 // x * e with the stored key word e: REDC of the 128-bit product; x < 40q,
 // so the result is below q + 40q^2/2^64 < 2q before the correction.
 __device__ __forceinline__ u64 key_mul(u64 x, u64 e, u64 q, u64 mont)
@@ -806,7 +800,12 @@ static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int varian
         if ((rc = oc_combine(T, oj, true, share_keys, st)) != KS_OK) return rc;
         if ((rc = launch_ntt_inv(T, mw, false, st)) != KS_OK) return rc;
     }
-    // 3. Q section
+    // 3. Q section: one cluster kernel per output tower (TOWER), else the
+    // split or fused form below
+    if (variant == KS_OC_TOWER) {
+        rc = launch_oc_tower(T, oj, st);
+        if (rc != KS_EUNSUPPORTED) return rc;
+    }
     BUpJobs bq;
     bq.n = 0;
     BDnJobs bd;
@@ -832,6 +831,13 @@ static int launch_oc_chunk(const Tables &T, int n, const OcJob *jobs, int varian
 
 int launch_oc(const Tables &T, int njobs, const OcJob *jobs, int variant, cudaStream_t st, bool share_keys)
 {
+    // The tower kernel needs a ring degree with a cluster geometry and full
+    // keys; otherwise its launch group runs the split variant (same result).
+    if (variant == KS_OC_TOWER) {
+        bool ok = oc_tower_supported(T);
+        for (int i = 0; i < njobs && ok; ++i) ok = !jobs[i].key.comp;
+        if (!ok) variant = KS_OC_SPLIT;
+    }
     // The fused row kernels read the key's a half from memory: batches with
     // a compressed key run the split variant instead.
     if (variant == KS_OC_FUSED)

@@ -30,8 +30,8 @@ class KSError(RuntimeError):
 
 
 class Schedule(ctypes.Structure):
-    """ks_schedule: dataflow (MP/DC/OC), oc_variant (0 fused, 1 split, 2
-    whole basis), chunk (jobs per batched launch group), order (0 given,
+    """ks_schedule: dataflow (MP/DC/OC), oc_variant (0 fused rows, 1 split,
+    2 whole basis, 3 one cluster kernel per output tower), chunk (jobs per batched launch group), order (0 given,
     1 by level, 2 by key), ntt (0 two launches, 1/2 cluster launch, -1 the
     parameter set's option) and bconv (0 CUDA cores, 1 tensor cores, -1 the
     option)."""

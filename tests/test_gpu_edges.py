@@ -80,8 +80,10 @@ def max_w_cprime(C, nact):
 
 
 def check_all_paths(ks, P, C, key, nact, d, w0, w1, engines=(True,), what=""):
-    """MP, DC and OC single switches and the batched whole-basis and split
-    schedules, under each base-conversion engine, all equal to (w0, w1)."""
+    """MP, DC and OC single switches and the batched split, whole-basis and
+    per-tower cluster schedules, under each base-conversion engine (the
+    tower kernel's base conversions are always on the CUDA cores), all equal
+    to (w0, w1)."""
     dd = ks.to_device(d)
     for tensor in engines:
         P.set_bconv_tensor(tensor)
@@ -90,7 +92,7 @@ def check_all_paths(ks, P, C, key, nact, d, w0, w1, engines=(True,), what=""):
             P.switch(key, nact, dd, o0, o1, df)
             assert np.array_equal(ks.to_host(o0), w0), (what, nact, df, tensor, "out0")
             assert np.array_equal(ks.to_host(o1), w1), (what, nact, df, tensor, "out1")
-        for variant in (1, 2):
+        for variant in (1, 2, 3):
             jobs = [(key, nact, dd, ks.empty((nact, C.N)), ks.empty((nact, C.N))) for _ in range(2)]
             P.switch_batch_sched(jobs, ks.Schedule(2, variant, 64, 0))
             for (_, _, _, o0, o1) in jobs:
