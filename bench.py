@@ -114,7 +114,7 @@ def workload_config(B, dataflow, world):
             "l2": "inputs+keys per step exceed L2 (no flush)"}
 
 
-def mixed_batch(P, keys, stream, timed, world, steps, seed, n_jobs=64):
+def mixed_batch(P, keys, stream, timed, world, steps, seed, n_jobs=64, learned=None):
     """Key switches/s on a batch of n_jobs ciphertexts with levels uniform in
     4..24 (L+1 towers), each with one of the given keys: the schedule the
     autotuner picks, and the same schedule with jobs grouped by key."""
@@ -132,11 +132,28 @@ def mixed_batch(P, keys, stream, timed, world, steps, seed, n_jobs=64):
     t_auto = timed(lambda: P.switch_batch(jobs, "AUTO", stream), steps, 2)
     by_key = ks.Schedule(tuned.dataflow, tuned.oc_variant, tuned.chunk, 2, tuned.ntt, tuned.bconv)
     t_key = timed(lambda: P.switch_batch_sched(jobs, by_key, stream), steps, 2)
-    return {"value": round(world * n_jobs * steps / (t_auto / 1e3), 2), "unit": "key-switches/s",
-            "jobs": n_jobs, "levels": "uniform 4..24 of 24", "keys": len(keys),
-            "schedule": list(tuned.as_tuple() + tuned.impl()),
-            "grouped_by_key": round(world * n_jobs * steps / (t_key / 1e3), 2),
-            "mean_level": round(sum(levels) / n_jobs, 2)}
+    out = {"value": round(world * n_jobs * steps / (t_auto / 1e3), 2), "unit": "key-switches/s",
+           "jobs": n_jobs, "levels": "uniform 4..24 of 24", "keys": len(keys),
+           "schedule": list(tuned.as_tuple() + tuned.impl()),
+           "grouped_by_key": round(world * n_jobs * steps / (t_key / 1e3), 2),
+           "mean_level": round(sum(levels) / n_jobs, 2)}
+    if learned is not None:
+        out["learned_schedule"] = learned_regret(P, jobs, tuned, t_auto / steps, stream, timed, steps)
+    return out
+
+
+def learned_regret(P, jobs, tuned, ms_tuned, stream, timed, steps):
+    """The attached cost model's pick for a batch, timed beside the
+    exhaustive autotuner's pick (ms_tuned per call): regret in microseconds
+    per call and per key switch."""
+    pick, _ = P.predict_schedule(jobs, stream)
+    ms_pick = timed(lambda: P.switch_batch_sched(jobs, pick, stream), steps, 2) / steps
+    n = len(jobs)
+    return {"model_pick": list(pick.as_tuple() + pick.impl()), "autotuner_pick": list(tuned.as_tuple() + tuned.impl()),
+            "model_ms": round(ms_pick, 4), "autotuner_ms": round(ms_tuned, 4),
+            "regret_us_per_call": round((ms_pick - ms_tuned) * 1e3, 2),
+            "regret_us_per_ks": round((ms_pick - ms_tuned) * 1e3 / n, 3),
+            "regret_frac": round(ms_pick / ms_tuned - 1, 4)}
 
 
 def hoisted_rotations(P, keys, gals, d, stream, timed, world, steps):
@@ -389,7 +406,23 @@ def main():
 
     # ---- mixed batch: 64 ciphertexts with levels uniform in 4..24, each keyed
     # by one of the 16 Galois keys (jobs of one key and level share key limbs)
-    mixed = mixed_batch(P, keys, stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 7)
+    # ---- the learned cost model (committed, trained on GB300 autotuner
+    # timings by the library's kernels) attached to the parameter set: its
+    # pick for the headline batch and the mixed batch against the
+    # autotuner's, and its held-out regret on the committed dataset
+    from paper_2311_01598_gb300 import tune
+    cm = tune.CostModel.load(os.path.join(tune.DATA_DIR, "cost_model_gb300.npz"))
+    P.set_cost_model(cm.mlp, cm.t_mean, cm.t_scale)
+    learned = {"bench_batch": learned_regret(P, jobs, tuned, ms_per_step, stream, timed, max(3, args.steps // 2))}
+    mixed = mixed_batch(P, keys, stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 7,
+                        learned=cm)
+    learned["mixed_batch"] = mixed.pop("learned_schedule", None)
+    rows = tune.load(os.path.join(tune.DATA_DIR, "tune_gb300.jsonl"))
+    _, test_rows = tune.split(rows, 0.8, seed=0)
+    di = tune.default_candidate_index(P.tune_candidates(), P.default_schedule())
+    learned["held_out"] = {k: (round(v, 4) if isinstance(v, float) else v)
+                           for k, v in tune.evaluate(cm, test_rows, di).items()}
+    P.set_cost_model(None)
 
     # ---- 8 rotations of one ciphertext: hoisted (one ModUp) vs 8 separate switches
     hoisted = hoisted_rotations(P, keys[:8], gals[:8], d[0], stream, timed, world, steps=max(3, args.steps // 2))
@@ -513,6 +546,7 @@ def main():
             "oc_batched_over_mp_plain": round(value / singles["MP"], 3),
             "oc_variants": variants,
             "mixed_batch": mixed,
+            "learned_schedule": learned,
             "table3_sets": table3,
             "hoisted_rotations": hoisted,
             "compressed_keys": compressed,

@@ -333,7 +333,8 @@ int ks_tune_candidates(const ks_params *params, uint32_t max, ks_schedule *out, 
  *      candidate i's time in ms (max entries); of the candidates within
  *      0.3% of the fastest, the one with the largest launch group wins;
  *   2. the fastest structure under each implementation pair (ntt, bconv) in
- *      {(0,1), (1,1), (0,0), (1,0)} (ks_autotune_impl).
+ *      {(0,1), (1,1), (0,0), (1,0)} (ks_autotune_impl); when max leaves room
+ *      for them, ms_out[n_candidates + k] gets pair k's time.
  * The fastest schedule, with explicit ntt and bconv, is written to *best and
  * stored in the params' tuning cache under this batch's signature (job count
  * rounded up to a power of two, mean level rounded to a multiple of 4),
@@ -383,6 +384,34 @@ int ks_mlp_gradients(ks_mlp *mlp, uint32_t batch, const float *d_x, const float 
 int ks_mlp_train_step(ks_mlp *mlp, uint32_t batch, const float *d_x, const float *d_t, const float *d_mask,
                       float lr, float *h_loss, ks_stream_t stream);
 
+/* Learned schedule choice (the cost model in place of exhaustive search;
+ * the paper's dataflows are Sec. IV, the model is this library's).
+ * Attach a trained MLP to a parameter set: 7 inputs (ks_cost_features) and
+ * one output per structural candidate (ks_tune_candidates order) followed by
+ * one per implementation pair (ntt, bconv) in the order {(0,1), (1,1),
+ * (0,0), (1,0)}; outputs are normalised log ms per key switch, de-normalised
+ * as y * t_scale + t_mean.  The model is not owned and must outlive its use;
+ * NULL detaches.  Allocates the model's one-row buffers (so later
+ * predictions allocate nothing).  KS_EINVAL when the widths do not match.
+ * Once attached, ks_switch_batch with KS_AUTO on a batch whose signature is
+ * not in the tuning cache runs the model on `stream` (its forward kernel),
+ * reads the prediction back (this synchronises `stream`: make the first
+ * such call before any stream capture), stores the predicted schedule in
+ * the cache and runs it; ks_autotune remains the exhaustive search whose
+ * timings the model is trained on and judged against. */
+int ks_params_set_cost_model(ks_params *params, ks_mlp *model, float t_mean, float t_scale);
+/* The schedule the attached model predicts fastest for a batch (the fastest
+ * structural candidate with the fastest implementation pair).  h_pred
+ * (nullable) receives every de-normalised output (log ms per key switch).
+ * Synchronises `stream`.  KS_EINVAL when no model is attached. */
+int ks_predict_schedule(ks_params *params, uint32_t n, const ks_job *h_jobs, ks_stream_t stream,
+                        ks_schedule *out, float *h_pred);
+/* The model's 7 inputs for a batch (host): logN, L+1 (the batch's mean
+ * level, rounded), dnum (the parameter set's at the top level, else the
+ * active digits), K, log2 batch, alpha = ceil((L+1)/dnum), log2 input words,
+ * each scaled by fixed constants. */
+int ks_cost_features(const ks_params *params, uint32_t n, const ks_job *h_jobs, float *h_x);
+
 /* A key with pseudo-random residues generated on the device (for timing
  * and tuning; it switches to no particular secret). */
 int ks_key_synthetic(const ks_params *params, uint64_t seed, ks_stream_t stream, ks_key **out);
@@ -412,6 +441,47 @@ typedef struct {
  * reusing the host buffers. */
 int ks_switch_batch_host(const ks_params *params, uint32_t n, const ks_host_job *h_jobs,
                          ks_dataflow dataflow, ks_stream_t stream);
+
+/* ---------------------------------------------------------------------
+ * Tower-sharded key switching: one key switch split over G devices by tower
+ * (the output towers are independent, Sec. IV-C).  Rank g owns full Q towers
+ * [q_begin, q_end) and special towers [p_begin, p_end) (the ranks' ranges
+ * partition [0, n_q) and [0, k_p)), holds the input towers and the key limbs
+ * of those towers only, and produces its Q range of the outputs.  Per key
+ * switch at level l+1 (= level_towers), with the rank's active Q towers
+ * [min(q_begin, l+1), min(q_end, l+1)) = nq_own of them and np_own =
+ * p_end - p_begin special towers, nown = nq_own + np_own:
+ *   ks_shard_prep      d_own [nq_own][N] -> y_own [nq_own][N] (ModUp P1);
+ *   (caller)           all-gather y: y_all [l+1][N], towers in order;
+ *   ks_shard_keyprod   y_all, d_own -> cp_own [2][nown][N]: c' of the
+ *                      rank's towers (ModUp P2-P5); rows nq_own.. of each
+ *                      polynomial then hold w_own, the special towers after
+ *                      ModDown P1 (coefficient form);
+ *   (caller)           all-gather w: w_all [2][K][N], towers in order;
+ *   ks_shard_moddown   w_all, cp_own -> out0_own, out1_own [nq_own][N]
+ *                      (ModDown P2-P4).
+ * The gathered outputs equal ks_switch's bit for bit.  All data are device
+ * memory owned by the caller; scratch holds ks_shard_scratch_words() words
+ * (the same buffer for keyprod and moddown of one key switch).  Calls queue
+ * work on `stream` and return KS_EINVAL for bad ranges, levels or keys.  A
+ * rank with no active Q towers at a level skips prep and moddown. */
+typedef struct {
+    uint32_t q_begin, q_end; /* full Q towers of the rank */
+    uint32_t p_begin, p_end; /* special towers of the rank */
+} ks_shard;
+/* A key holding only the shard's towers ([ndig][2][own towers][N]), copied
+ * from a full key on `stream` (synchronised before returning).  Free it
+ * with ks_key_destroy; it serves the ks_shard_* calls only. */
+int ks_key_shard(const ks_key *full_key, const ks_shard *shard, ks_stream_t stream, ks_key **out);
+size_t ks_shard_scratch_words(const ks_params *params, const ks_shard *shard, uint32_t level_towers);
+int ks_shard_prep(const ks_params *params, const ks_shard *shard, uint32_t level_towers, const uint64_t *d_own,
+                  uint64_t *y_own, ks_stream_t stream);
+int ks_shard_keyprod(const ks_params *params, const ks_key *shard_key, uint32_t level_towers,
+                     const uint64_t *y_all, const uint64_t *d_own, uint64_t *cp_own, uint64_t *scratch,
+                     ks_stream_t stream);
+int ks_shard_moddown(const ks_params *params, const ks_key *shard_key, uint32_t level_towers,
+                     const uint64_t *w_all, const uint64_t *cp_own, uint64_t *out0_own, uint64_t *out1_own,
+                     uint64_t *scratch, ks_stream_t stream);
 
 /* ---------------------------------------------------------------------
  * Serving: continuous batching of key-switch requests.

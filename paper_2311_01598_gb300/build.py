@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off",
           "-I" + INCLUDE]
-SOURCES = ["ks_kernels.cu", "ks_oc.cu", "ks_api.cu", "ks_host.cpp", "ks_noalloc.cu", "ks_probe.cu", "ks_tune.cu", "ks_serve.cu", "ks_mlp.cu", "ks_bconv_tc.cu", "ks_ntt_cluster.cu", "ks_oc_tower.cu"]
+SOURCES = ["ks_kernels.cu", "ks_oc.cu", "ks_api.cu", "ks_host.cpp", "ks_noalloc.cu", "ks_probe.cu", "ks_tune.cu", "ks_serve.cu", "ks_mlp.cu", "ks_bconv_tc.cu", "ks_ntt_cluster.cu", "ks_oc_tower.cu", "ks_shard.cu"]
 
 
 def nvcc() -> str:

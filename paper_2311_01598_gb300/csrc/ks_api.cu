@@ -375,6 +375,7 @@ int check_job(const ks_params *P, const ks_key *K, uint32_t nact, const uint64_t
               const uint64_t *o1)
 {
     if (!K || K->params != P) return fail(KS_EINVAL, "key is NULL or belongs to another params object");
+    if (K->shard) return fail(KS_EINVAL, "key is a tower shard: it serves the ks_shard_* calls only");
     if (nact < 1 || nact > (uint32_t)P->nq) return fail(KS_EINVAL, "level_towers must be in 1..n_q");
     if (!d || !o0 || !o1) return fail(KS_EINVAL, "NULL data pointer");
     // the combine kernels move two words at a time
@@ -473,6 +474,8 @@ void ks_params_destroy(ks_params *P)
     cudaDeviceSynchronize();
     free_ws(P);
     free_tables(P);
+    if (P->d_cm_x) cudaFree(P->d_cm_x);
+    if (P->d_cm_y) cudaFree(P->d_cm_y);
     delete P;
 }
 
@@ -945,8 +948,19 @@ int ks_switch_batch(const ks_params *P, uint32_t n, const ks_job *jobs, ks_dataf
     if (dataflow == KS_AUTO && n > 0) {
         uint64_t lv = 0;
         for (uint32_t i = 0; i < n; ++i) lv += jobs[i].level_towers;
-        auto it = P->tune.find(tune_signature(n, (uint32_t)(lv / n)));
-        if (it != P->tune.end()) sc = it->second;
+        const auto sig = tune_signature(n, (uint32_t)(lv / n));
+        auto it = P->tune.find(sig);
+        if (it != P->tune.end()) {
+            sc = it->second;
+        } else if (P->cost_model) {
+            // learned schedule: the cost model's pick, cached for the signature
+            ks_schedule pick;
+            if ((rc = predict_schedule(const_cast<ks_params *>(P), n, jobs, (cudaStream_t)stream, &pick, nullptr)) !=
+                KS_OK)
+                return rc;
+            const_cast<ks_params *>(P)->tune[sig] = pick;
+            sc = pick;
+        }
     }
     return run_batch(const_cast<ks_params *>(P), n, jobs, sc, (cudaStream_t)stream);
 }

@@ -124,6 +124,11 @@ struct ks_params {
     ks_schedule sched{KS_OC, 1, 64, 0, -1, -1};
     // tuning cache: (job-count bucket, mean-level bucket) -> schedule
     std::map<std::pair<uint32_t, uint32_t>, ks_schedule> tune;
+    // learned cost model consulted by KS_AUTO on a tuning-cache miss (not
+    // owned), its target normalisation and its one-row input/output buffers
+    ks_mlp *cost_model = nullptr;
+    float cm_mean = 0.f, cm_scale = 1.f;
+    float *d_cm_x = nullptr, *d_cm_y = nullptr;
     // double-buffered device staging of ks_switch_batch_host
     std::mutex host_mu;
     ks::HostStage *stage = nullptr;
@@ -137,6 +142,11 @@ struct ks_key {
     size_t bytes = 0;
     int compressed = 0;
     uint64_t a_seed = 0;  // compressed: seed of the regenerated a half
+    // tower shard (ks_key_shard): the limbs of full Q towers [q0, q1) and
+    // special towers [p0, p1) only, [ndig][2][(q1-q0)+(p1-p0)][N]; used by
+    // the ks_shard_* calls only
+    int shard = 0;
+    uint32_t q0 = 0, q1 = 0, p0 = 0, p1 = 0;
 };
 
 namespace ks {
@@ -208,6 +218,14 @@ int check_batch(const ks_params *P, uint32_t n, const ks_job *jobs);
 int check_schedule(const ks_schedule *sc);
 // Tuning-cache signature of a batch.
 std::pair<uint32_t, uint32_t> tune_signature(uint32_t n, uint32_t mean_level);
+// The schedule the parameter set's cost model predicts fastest for a batch
+// (ks_tune.cu): runs the model's forward kernel on st and reads the
+// predictions back (synchronises st).  h_pred (nullable) receives the raw
+// outputs (predicted log ms per key switch).
+int predict_schedule(ks_params *P, uint32_t n, const ks_job *jobs, cudaStream_t st, ks_schedule *out, float *h_pred);
+// MLP internals used by the schedule predictor (ks_mlp.cu).
+int mlp_io_dims(const ks_mlp *M, int *in, int *out);
+int mlp_reserve(ks_mlp *M, int batch);
 // Fill a key buffer with pseudo-random canonical residues (ks_kernels.cu).
 int launch_key_random(const Tables &T, u64 *evk, uint64_t seed, cudaStream_t st);
 

@@ -414,17 +414,18 @@ __global__ void __launch_bounds__(BC_THREADS, 4) k_bconv_down(Tables T, BDnJobs 
     const BDnJob &J = bj.job[jb];
     const int x = blockIdx.z - bj.zpre[jb];
     const int nact = J.nact;
-    const int i0 = blockIdx.y * BC_TT;
-    if (i0 >= nact) return;
+    const int ib = J.i_begin, ie = J.i_end < 0 ? nact : J.i_end;
+    const int i0 = ib + blockIdx.y * BC_TT;  // first target tower of the block
+    if (i0 >= ie) return;
     const int K = T.kp;
     for (int idx = threadIdx.x; idx < K * BC_TT; idx += blockDim.x) {
         const int k = idx / BC_TT, g = idx % BC_TT;
-        cs[k][g] = (i0 + g < nact) ? T.dn_mat[(size_t)k * T.nq + i0 + g] : 0;
+        cs[k][g] = (i0 + g < ie) ? T.dn_mat[(size_t)k * T.nq + i0 + g] : 0;
     }
     __syncthreads();
     const size_t N = (size_t)1 << T.logN;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const u64 *w = J.cp + (size_t)x * J.cp_stride + (size_t)nact * N;
+    const u64 *w = J.w ? J.w + (size_t)x * J.w_stride : J.cp + (size_t)x * J.cp_stride + (size_t)nact * N;
     BAcc acc[BC_TT];
 #pragma unroll
     for (int g = 0; g < BC_TT; ++g) bacc_zero(acc[g]);
@@ -450,15 +451,21 @@ __global__ void __launch_bounds__(BC_THREADS, 4) k_bconv_down(Tables T, BDnJobs 
     u64 *vo = J.v + (size_t)x * J.v_stride;
 #pragma unroll
     for (int g = 0; g < BC_TT; ++g)
-        if (i0 + g < nact) vo[(size_t)(i0 + g) * N + n] = bacc_reduce(acc[g], T.modc[i0 + g]);
+        if (i0 + g < ie) vo[(size_t)(i0 + g - ib) * N + n] = bacc_reduce(acc[g], T.modc[i0 + g]);
 }
 
 int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st)
 {
     if (b.n == 0) return KS_OK;
-    if (T.dn_tc && bconv_tc_supported(T, T.kp)) return launch_bconv_down_tc(T, b, T.dn_tc, st);
+    bool ranged = false;
+    for (int i = 0; i < b.n; ++i)
+        ranged = ranged || b.job[i].i_begin != 0 || (b.job[i].i_end >= 0 && b.job[i].i_end != b.job[i].nact) ||
+                 b.job[i].w != nullptr;
+    if (!ranged && T.dn_tc && bconv_tc_supported(T, T.kp)) return launch_bconv_down_tc(T, b, T.dn_tc, st);
     int span = 0;
-    for (int i = 0; i < b.n; ++i) span = std::max(span, b.job[i].nact);
+    for (int i = 0; i < b.n; ++i)
+        span = std::max(span, (b.job[i].i_end < 0 ? b.job[i].nact : b.job[i].i_end) - b.job[i].i_begin);
+    if (span <= 0) return KS_OK;
     const size_t N = (size_t)1 << T.logN;
     dim3 g((unsigned)(N / BC_THREADS), (unsigned)((span + BC_TT - 1) / BC_TT), (unsigned)b.zpre[b.n]);
     KS_LAUNCH(st, "bconv_down", k_bconv_down<<<g, BC_THREADS, 0, st>>>(T, b));

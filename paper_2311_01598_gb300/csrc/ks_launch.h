@@ -105,6 +105,13 @@ struct BDnJob {
     u64 *v;
     size_t v_stride;
     int nact, npoly;
+    // Optional (CUDA-core kernel only; jobs using them skip the tensor
+    // cores): targets [i_begin, i_end) only, written at v + (i - i_begin)*N
+    // (i_end < 0: all nact); w, when set, holds the sources of polynomial x
+    // at w + x*w_stride instead of cp's rows nact..nact+K-1.
+    int i_begin = 0, i_end = -1;
+    const u64 *w = nullptr;
+    size_t w_stride = 0;
 };
 struct BDnJobs {
     int n;

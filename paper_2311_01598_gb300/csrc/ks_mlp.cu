@@ -204,6 +204,16 @@ static int backward(ks_mlp *M, int batch, const float *d_t, const float *d_mask,
     return e == cudaSuccess ? KS_OK : fail(KS_ECUDA, std::string("MLP backward: ") + cudaGetErrorString(e));
 }
 
+int mlp_io_dims(const ks_mlp *M, int *in, int *out)
+{
+    if (!M || M->nl < 1) return fail(KS_EINVAL, "MLP is NULL");
+    *in = M->layer[0].in;
+    *out = M->layer[M->nl - 1].out;
+    return KS_OK;
+}
+
+int mlp_reserve(ks_mlp *M, int batch) { return ensure_batch(M, batch); }
+
 }  // namespace ks
 
 using namespace ks;

@@ -299,6 +299,7 @@ int ks_server_submit(ks_server *S, const ks_request *req, uint64_t *ticket)
     if (!S || !req || !ticket) return fail(KS_EINVAL, "NULL argument");
     const ks_params *P = req->params;
     if (!P || !req->key || req->key->params != P) return fail(KS_EINVAL, "request key/params mismatch");
+    if (req->key->shard) return fail(KS_EINVAL, "request key is a tower shard");
     if (req->level_towers < 1 || req->level_towers > (uint32_t)P->nq) return fail(KS_EINVAL, "bad level");
     if (!req->d_in || !req->d_out0 || !req->d_out1) return fail(KS_EINVAL, "NULL data pointer");
     // the combine kernels move two words at a time

@@ -3,6 +3,7 @@
 // winners (used by KS_AUTO), its text persistence, and synthetic keys for
 // tuning runs.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <fstream>
@@ -27,6 +28,7 @@ static std::vector<ks_schedule> candidates()
     for (int ch : {1, 8, 16, 64}) c.push_back({KS_OC, 2, ch, 0, -1, -1});
     c.push_back({KS_OC, 1, 64, 1, -1, -1});
     c.push_back({KS_OC, 2, 64, 1, -1, -1});
+    c.push_back({KS_OC, 3, 64, 0, -1, -1});
     return c;
 }
 
@@ -34,7 +36,8 @@ static std::vector<ks_schedule> candidates()
 constexpr float kTieFrac = 0.003f;
 
 // Implementation pairs (ntt, bconv) of the second stage, in ms_out order.
-static const int kImpl[4][2] = {{0, 1}, {1, 1}, {0, 0}, {1, 0}};
+constexpr int kImplPairs = 4;
+static const int kImpl[kImplPairs][2] = {{0, 1}, {1, 1}, {0, 0}, {1, 0}};
 
 // Best of reps timed runs of one schedule (after one untimed run).
 static int time_schedule(ks_params *P, uint32_t n, const ks_job *jobs, const ks_schedule &sc, uint32_t reps,
@@ -75,6 +78,73 @@ static int tune_impl(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps
             *best = sc;
         }
     }
+    return KS_OK;
+}
+
+// ------------------------------------------------------------------ cost model
+// Inputs of the learned cost model: (logN, L+1, dnum, K, log2 batch, alpha,
+// log2 input words), each scaled to roughly unit range by fixed constants.
+// The Python training code computes the same vector (tune.features).
+constexpr int kCostFeatures = 7;
+
+static void cost_features(int logN, int nq, int dnum, int kp, int batch, float *x)
+{
+    const int alpha = (nq + dnum - 1) / dnum;
+    const double words = (double)batch * nq * std::ldexp(1.0, logN);
+    x[0] = (float)((logN - 15) / 2.0);
+    x[1] = (float)((nq - 25) / 14.0);
+    x[2] = (float)((dnum - 12) / 12.0);
+    x[3] = (float)((kp - 6.5) / 3.5);
+    x[4] = (float)((std::log2((double)batch) - 4) / 2.5);
+    x[5] = (float)((alpha - 12) / 12.0);
+    x[6] = (float)((std::log2(words) - 22) / 3.0);
+}
+
+// Features of a batch: its mean level (rounded) stands for L+1; at the top
+// level dnum is the parameter set's, below it the number of active digits.
+static void batch_features(const ks_params *P, uint32_t n, const ks_job *jobs, float *x)
+{
+    uint64_t lv = 0;
+    for (uint32_t i = 0; i < n; ++i) lv += jobs[i].level_towers;
+    const int nact = std::max(1, (int)((lv + n / 2) / n));
+    const int dnum = nact == P->nq ? P->dnum : (nact + P->alpha - 1) / P->alpha;
+    cost_features(P->logN, nact, dnum, P->kp, (int)n, x);
+}
+
+int predict_schedule(ks_params *P, uint32_t n, const ks_job *jobs, cudaStream_t st, ks_schedule *out, float *h_pred)
+{
+    if (!P->cost_model) return fail(KS_EINVAL, "no cost model attached to this parameter set");
+    const std::vector<ks_schedule> c = candidates();
+    const int nout = (int)c.size() + kImplPairs;
+    float x[kCostFeatures];
+    batch_features(P, n, jobs, x);
+    std::vector<float> y(nout);
+    {
+        static std::mutex mu;  // one model may serve several parameter sets
+        std::lock_guard<std::mutex> g(mu);
+        if (cudaMemcpyAsync(P->d_cm_x, x, sizeof(x), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(KS_ECUDA, "cost model: feature upload");
+        }
+        int rc = ks_mlp_forward(P->cost_model, 1, P->d_cm_x, P->d_cm_y, (ks_stream_t)st);
+        if (rc != KS_OK) return rc;
+        if (cudaMemcpyAsync(y.data(), P->d_cm_y, sizeof(float) * nout, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(KS_ECUDA, "cost model: prediction readback");
+        }
+    }
+    int bs = 0, bi = 0;
+    for (int i = 1; i < (int)c.size(); ++i)
+        if (y[i] < y[bs]) bs = i;
+    for (int i = 1; i < kImplPairs; ++i)
+        if (y[c.size() + i] < y[c.size() + bi]) bi = i;
+    ks_schedule s = c[bs];
+    s.ntt = kImpl[bi][0];
+    s.bconv = kImpl[bi][1];
+    *out = s;
+    if (h_pred)
+        for (int i = 0; i < nout; ++i) h_pred[i] = y[i] * P->cm_scale + P->cm_mean;
     return KS_OK;
 }
 
@@ -167,8 +237,10 @@ int ks_autotune(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps, ks_
             base = c[i];
             base_chunk = c[i].chunk;
         }
-    // stage 2: implementation of the fastest structure
-    if (rc == KS_OK) rc = tune_impl(P, n, jobs, reps, st, e0, e1, base, nullptr, best);
+    // stage 2: implementation of the fastest structure (its four timings go
+    // to ms_out after the structural ones when the caller has room for them)
+    float *impl_out = (ms_out && max >= c.size() + kImplPairs) ? ms_out + c.size() : nullptr;
+    if (rc == KS_OK) rc = tune_impl(P, n, jobs, reps, st, e0, e1, base, impl_out, best);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != KS_OK) return rc;
@@ -191,6 +263,63 @@ int ks_autotune_impl(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
+}
+
+int ks_params_set_cost_model(ks_params *P, ks_mlp *model, float t_mean, float t_scale)
+{
+    if (!P) return fail(KS_EINVAL, "params is NULL");
+    if (cudaSetDevice(P->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "cudaSetDevice failed");
+    }
+    std::lock_guard<std::mutex> g(P->mu);
+    if (!model) {
+        P->cost_model = nullptr;
+        return KS_OK;
+    }
+    int in = 0, out = 0;
+    int rc = mlp_io_dims(model, &in, &out);
+    if (rc != KS_OK) return rc;
+    const int want = (int)candidates().size() + kImplPairs;
+    if (in != kCostFeatures || out != want)
+        return fail(KS_EINVAL, "cost model must map " + std::to_string(kCostFeatures) + " features to " +
+                                   std::to_string(want) + " outputs (structural candidates, then implementation pairs)");
+    if (!(t_scale > 0.f)) return fail(KS_EINVAL, "cost model: t_scale must be positive");
+    // buffers for one row, and the model's activation buffers for batch 1,
+    // allocated here so that KS_AUTO itself allocates nothing
+    if (!P->d_cm_x && cudaMalloc((void **)&P->d_cm_x, sizeof(float) * kCostFeatures) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ENOMEM, "cost model buffers");
+    }
+    if (!P->d_cm_y && cudaMalloc((void **)&P->d_cm_y, sizeof(float) * 256) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ENOMEM, "cost model buffers");
+    }
+    if ((rc = mlp_reserve(model, 1)) != KS_OK) return rc;
+    P->cost_model = model;
+    P->cm_mean = t_mean;
+    P->cm_scale = t_scale;
+    return KS_OK;
+}
+
+int ks_predict_schedule(ks_params *P, uint32_t n, const ks_job *h_jobs, ks_stream_t stream, ks_schedule *out,
+                        float *h_pred)
+{
+    int rc = check_batch(P, n, h_jobs);
+    if (rc) return rc;
+    if (n == 0 || !out) return fail(KS_EINVAL, "ks_predict_schedule: need n >= 1 and out");
+    if (cudaSetDevice(P->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(KS_ECUDA, "cudaSetDevice failed");
+    }
+    return predict_schedule(P, n, h_jobs, (cudaStream_t)stream, out, h_pred);
+}
+
+int ks_cost_features(const ks_params *P, uint32_t n, const ks_job *h_jobs, float *h_x)
+{
+    if (!P || !h_jobs || !h_x || n == 0) return fail(KS_EINVAL, "ks_cost_features: NULL argument or n = 0");
+    batch_features(P, n, h_jobs, h_x);
+    return KS_OK;
 }
 
 int ks_tune_cache_put(ks_params *P, uint32_t n_jobs, uint32_t mean_level, const ks_schedule *s)

@@ -29,6 +29,13 @@ class KSError(RuntimeError):
         self.code = code
 
 
+class Shard(ctypes.Structure):
+    """ks_shard: the full Q towers [q_begin, q_end) and special towers
+    [p_begin, p_end) one rank owns in a tower-sharded key switch."""
+    _fields_ = [("q_begin", ctypes.c_uint32), ("q_end", ctypes.c_uint32), ("p_begin", ctypes.c_uint32),
+                ("p_end", ctypes.c_uint32)]
+
+
 class Schedule(ctypes.Structure):
     """ks_schedule: dataflow (MP/DC/OC), oc_variant (0 fused rows, 1 split,
     2 whole basis, 3 one cluster kernel per output tower), chunk (jobs per batched launch group), order (0 given,
@@ -129,6 +136,20 @@ def lib():
         L.ks_tune_cache_save.argtypes = [vp, ctypes.c_char_p]
         L.ks_tune_cache_load.argtypes = [vp, ctypes.c_char_p]
         L.ks_key_synthetic.argtypes = [vp, u64, vp, pvp]
+        L.ks_params_set_cost_model.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float]
+        L.ks_key_shard.argtypes = [vp, ctypes.POINTER(Shard), vp, pvp]
+        L.ks_key_shard.restype = ci
+        L.ks_shard_scratch_words.argtypes = [vp, ctypes.POINTER(Shard), u32]
+        L.ks_shard_scratch_words.restype = ctypes.c_size_t
+        L.ks_shard_prep.argtypes = [vp, ctypes.POINTER(Shard), u32, vp, vp, vp]
+        L.ks_shard_prep.restype = ci
+        L.ks_shard_keyprod.argtypes = [vp, vp, u32, vp, vp, vp, vp, vp]
+        L.ks_shard_keyprod.restype = ci
+        L.ks_shard_moddown.argtypes = [vp, vp, u32, vp, vp, vp, vp, vp, vp]
+        L.ks_shard_moddown.restype = ci
+        L.ks_predict_schedule.argtypes = [vp, u32, ctypes.POINTER(Job), vp, ctypes.POINTER(Schedule),
+                                          ctypes.POINTER(ctypes.c_float)]
+        L.ks_cost_features.argtypes = [vp, u32, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_float)]
         L.ks_mlp_create.argtypes = [u32, ctypes.POINTER(u32), u64, pvp]
         L.ks_mlp_destroy.argtypes = [vp]
         L.ks_mlp_destroy.restype = None
@@ -140,7 +161,8 @@ def lib():
         L.ks_mlp_gradients.argtypes = [vp, u32, vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float), vp]
         L.ks_mlp_train_step.argtypes = [vp, u32, vp, vp, vp, ctypes.c_float, ctypes.POINTER(ctypes.c_float), vp]
         for name in ("ks_tune_candidates", "ks_autotune", "ks_autotune_impl", "ks_tune_cache_put", "ks_tune_cache_get",
-                     "ks_tune_cache_save", "ks_tune_cache_load", "ks_key_synthetic", "ks_mlp_create",
+                     "ks_tune_cache_save", "ks_tune_cache_load", "ks_key_synthetic", "ks_params_set_cost_model",
+                     "ks_predict_schedule", "ks_cost_features", "ks_mlp_create",
                      "ks_mlp_get_params", "ks_mlp_set_params", "ks_mlp_forward", "ks_mlp_gradients",
                      "ks_mlp_train_step"):
             getattr(L, name).restype = ci
@@ -406,12 +428,13 @@ class Params:
         check(lib().ks_tune_candidates(self.handle, n.value, arr, ctypes.byref(n)))
         return [arr[i] for i in range(n.value)]
 
-    def autotune(self, jobs, reps: int = 3, stream=None):
+    def autotune(self, jobs, reps: int = 3, stream=None, with_impl: bool = False):
         """ks_autotune: times the structural candidates (returned ms, in
         candidate order), then the fastest one under each implementation
-        pair; returns (best, [ms]) and caches best for KS_AUTO."""
+        pair (their four ms appended when with_impl); returns (best, [ms])
+        and caches best for KS_AUTO."""
         arr, n = self._jobs(jobs)
-        nc = len(self.tune_candidates())
+        nc = len(self.tune_candidates()) + (4 if with_impl else 0)
         ms = (ctypes.c_float * nc)()
         best = Schedule()
         check(lib().ks_autotune(self.handle, n, arr, reps, _stream_handle(stream), nc, ms, ctypes.byref(best)))
@@ -444,6 +467,59 @@ class Params:
     def tune_cache_load(self, path: str) -> None:
         """ks_tune_cache_load: lines for this device and parameter set are merged in."""
         check(lib().ks_tune_cache_load(self.handle, path.encode()))
+
+    def set_cost_model(self, mlp, t_mean: float = 0.0, t_scale: float = 1.0) -> None:
+        """ks_params_set_cost_model: attach a trained Mlp (None detaches);
+        KS_AUTO then runs it on a tuning-cache miss.  The Mlp must outlive
+        its use by this parameter set."""
+        self._cost_model = mlp  # keeps the model alive while attached
+        check(lib().ks_params_set_cost_model(self.handle, mlp.handle if mlp is not None else None, float(t_mean),
+                                             float(t_scale)))
+
+    def predict_schedule(self, jobs, stream=None):
+        """ks_predict_schedule: (the attached model's schedule for the batch,
+        its de-normalised outputs: log ms per key switch per structural
+        candidate, then per implementation pair)."""
+        arr, n = self._jobs(jobs)
+        nout = len(self.tune_candidates()) + 4
+        pred = (ctypes.c_float * nout)()
+        sc = Schedule()
+        check(lib().ks_predict_schedule(self.handle, n, arr, _stream_handle(stream), ctypes.byref(sc), pred))
+        return sc, [float(x) for x in pred]
+
+    def cost_features(self, jobs) -> np.ndarray:
+        """ks_cost_features: the cost model's 7 inputs for a batch."""
+        arr, n = self._jobs(jobs)
+        x = (ctypes.c_float * 7)()
+        check(lib().ks_cost_features(self.handle, n, arr, x))
+        return np.array(list(x), dtype=np.float32)
+
+    # -- tower-sharded key switching ------------------------------------------
+    def key_shard(self, key: Key, shard: "Shard", stream=None) -> Key:
+        """ks_key_shard: a key holding only the shard's towers (copied on the device)."""
+        h = ctypes.c_void_p()
+        check(lib().ks_key_shard(key.handle, ctypes.byref(shard), _stream_handle(stream), ctypes.byref(h)))
+        return Key(self, h.value)
+
+    def shard_scratch_words(self, shard: "Shard", nact: int) -> int:
+        """ks_shard_scratch_words: scratch of one rank's keyprod/moddown at level nact."""
+        return int(lib().ks_shard_scratch_words(self.handle, ctypes.byref(shard), nact))
+
+    def shard_prep(self, shard: "Shard", nact: int, d_own, y_own, stream=None) -> None:
+        """ks_shard_prep: ModUp P1 of the rank's input towers."""
+        check(lib().ks_shard_prep(self.handle, ctypes.byref(shard), nact, _ptr(d_own), _ptr(y_own),
+                                  _stream_handle(stream)))
+
+    def shard_keyprod(self, skey: Key, nact: int, y_all, d_own, cp_own, scratch, stream=None) -> None:
+        """ks_shard_keyprod: c' of the rank's towers from the gathered y;
+        the special rows of cp_own then hold w_own."""
+        check(lib().ks_shard_keyprod(self.handle, skey.handle, nact, _ptr(y_all), _ptr(d_own), _ptr(cp_own),
+                                     _ptr(scratch), _stream_handle(stream)))
+
+    def shard_moddown(self, skey: Key, nact: int, w_all, cp_own, out0_own, out1_own, scratch, stream=None) -> None:
+        """ks_shard_moddown: the rank's output towers from the gathered w."""
+        check(lib().ks_shard_moddown(self.handle, skey.handle, nact, _ptr(w_all), _ptr(cp_own), _ptr(out0_own),
+                                     _ptr(out1_own), _ptr(scratch), _stream_handle(stream)))
 
     def key_synthetic(self, seed: int, stream=None) -> Key:
         """ks_key_synthetic: a key of pseudo-random residues (timing and tuning only)."""

@@ -2,18 +2,22 @@
 
 * ``collect``: sample workloads of the cost model's domain (logN 13-17, L+1
   2-48, dnum 1..L+1, K 1-12, batch 1-256, capped so one batch holds at most
-  2^16*24*16 words of input), time every candidate schedule of each with
-  ``ks_autotune`` (CUDA events, best of k), and write one JSON line per
-  workload.
+  2^16*24*16 words of input), time every structural candidate schedule of
+  each and then the fastest structure under the four implementation pairs
+  (NTT form x base-conversion engine) with ``ks_autotune`` (CUDA events, best
+  of k), and write one JSON line per workload.
 * ``train``: fit the FP32 MLP (7 inputs -> 3 x 64 ReLU -> one predicted
-  log-time per candidate) on those timings with the library's own forward,
-  backward and Adam kernels.
-* ``evaluate``: for held-out workloads, pick the candidate with the lowest
-  predicted time and report its regret against the measured best (the
-  exhaustive search) and against the fixed default schedule.
+  log-time per structural candidate, then one per implementation pair) on
+  those timings with the library's own forward, backward and Adam kernels.
+* ``evaluate``: for held-out workloads, pick the structure and the
+  implementation pair with the lowest predicted times and report the regret
+  against the measured best (the exhaustive search), as a fraction and in
+  microseconds, and against the fixed default schedule.
 
-The MLP replaces exhaustive search at run time: ``choose`` predicts the
-schedule of an unseen workload without timing anything.
+At run time the library itself runs the model: attached to a parameter set
+(``Params.set_cost_model``), it is consulted by ``KS_AUTO`` on a
+tuning-cache miss and its pick is cached and executed.  ``choose`` gives the
+same pick from Python.
 """
 from __future__ import annotations
 
@@ -28,6 +32,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 DATA_DIR = os.path.join(HERE, "data")
 HIDDEN = (64, 64, 64)
+IMPL_PAIRS = ((0, 1), (1, 1), (0, 0), (1, 0))  # (ntt, bconv) in the library's stage-2 order
 FEATURE_NAMES = ("logN", "L+1", "dnum", "K", "log2 batch", "alpha", "log2 words")
 WORDS_CAP = (1 << 16) * 24 * 16
 
@@ -69,10 +74,13 @@ def collect(n_workloads, seed, out_path, reps=2, log=print):
             for b in range(batch):
                 d = torch.randint(0, qmin, (nq, P.N), dtype=torch.int64, device="cuda")
                 jobs.append((key, nq, d, ks.empty((nq, P.N)), ks.empty((nq, P.N))))
-            best, ms = P.autotune(jobs, reps=reps)
             cands = [c.as_tuple() for c in P.tune_candidates()]
+            best, ms = P.autotune(jobs, reps=reps, with_impl=True)
+            ms_s, ms_i = ms[:len(cands)], ms[len(cands):]
             row = {"logN": logN, "nq": nq, "dnum": dnum, "kp": kp, "batch": batch,
-                   "ms": [round(m, 5) for m in ms], "best": cands.index(best.as_tuple())}
+                   "ms": [round(m, 5) for m in ms_s], "best": int(np.argmin(ms_s)),
+                   "base": cands.index(best.as_tuple()),
+                   "impl_ms": [round(m, 5) for m in ms_i], "best_impl": int(np.argmin(ms_i))}
             f.write(json.dumps(row) + "\n")
             f.flush()
             del jobs, key, P
@@ -89,10 +97,12 @@ def load(path):
 
 
 def arrays(rows):
-    """Features X and targets T (log time per key switch, one per candidate)."""
+    """Features X and targets T: log time per key switch (ms) of every
+    structural candidate, then of the autotuner's fastest structure under
+    each implementation pair."""
     X = np.stack([features(r["logN"], r["nq"], r["dnum"], r["kp"], r["batch"]) for r in rows])
-    # target: log of time per key switch (ms), one per candidate
-    T = np.array([[math.log(m / r["batch"]) for m in r["ms"]] for r in rows], dtype=np.float32)
+    T = np.array([[math.log(m / r["batch"]) for m in list(r["ms"]) + list(r["impl_ms"])] for r in rows],
+                 dtype=np.float32)
     return X, T
 
 
@@ -146,23 +156,39 @@ def train(rows, epochs=3000, lr=3e-3, seed=1, log=None):
 
 
 def evaluate(model, rows, default_index):
-    """Regret of the model's choice and of the default schedule against the
-    measured best, per workload (fractions, 0 = optimal)."""
-    X, T = arrays(rows)
+    """Regret of the model's choices against the measured best, per workload:
+    the structure (argmin of the structural outputs, timed with the
+    parameter set's default implementation) and the implementation pair
+    (argmin of the last four outputs, timed on the autotuner's structure),
+    as fractions (0 = optimal) and in microseconds (per batch and per key
+    switch); the fixed default schedule beside it."""
+    X, _ = arrays(rows)
     pred = model.predict(X)
-    pick = pred.argmin(axis=1)
+    ns = len(rows[0]["ms"])
+    pick = pred[:, :ns].argmin(axis=1)
+    pick_i = pred[:, ns:].argmin(axis=1)
     ms = np.array([r["ms"] for r in rows])
-    best = ms.min(axis=1)
-    chosen = ms[np.arange(len(rows)), pick]
-    default = ms[:, default_index]
+    mi = np.array([r["impl_ms"] for r in rows])
+    batch = np.array([r["batch"] for r in rows], dtype=np.float64)
+    ar = np.arange(len(rows))
+    best, chosen, default = ms.min(axis=1), ms[ar, pick], ms[:, default_index]
+    best_i, chosen_i = mi.min(axis=1), mi[ar, pick_i]
     return {"n": len(rows),
             "model_regret_mean": float(np.mean(chosen / best - 1)),
             "model_regret_median": float(np.median(chosen / best - 1)),
             "model_regret_p90": float(np.quantile(chosen / best - 1, 0.9)),
             "model_time_over_best": float(chosen.sum() / best.sum() - 1),
+            "model_regret_us_mean": float(np.mean(chosen - best) * 1e3),
+            "model_regret_us_per_ks_mean": float(np.mean((chosen - best) / batch) * 1e3),
+            "model_regret_us_max": float(np.max(chosen - best) * 1e3),
             "default_regret_mean": float(np.mean(default / best - 1)),
             "default_time_over_best": float(default.sum() / best.sum() - 1),
-            "exact_pick_rate": float(np.mean(chosen == best))}
+            "default_regret_us_mean": float(np.mean(default - best) * 1e3),
+            "exact_pick_rate": float(np.mean(chosen == best)),
+            "impl_regret_mean": float(np.mean(chosen_i / best_i - 1)),
+            "impl_time_over_best": float(chosen_i.sum() / best_i.sum() - 1),
+            "impl_regret_us_mean": float(np.mean(chosen_i - best_i) * 1e3),
+            "impl_exact_pick_rate": float(np.mean(chosen_i == best_i))}
 
 
 def split(rows, frac=0.8, seed=0):
@@ -178,9 +204,17 @@ def default_candidate_index(candidates, default):
 
 
 def choose(model, params, batch, candidates):
-    """Schedule the model predicts fastest for a batch on params (no timing)."""
+    """Schedule the model predicts fastest for a batch of `batch` top-level
+    ciphertexts on params (no timing): the structure and the implementation
+    pair with the lowest predicted times (the library's KS_AUTO makes the
+    same pick with the model attached)."""
+    from . import ks
     x = features(params.logN, params.nq, params.dnum, params.kp, batch)[None, :]
-    return candidates[int(model.predict(x)[0].argmin())]
+    y = model.predict(x)[0]
+    ns = len(candidates)
+    s = candidates[int(y[:ns].argmin())]
+    ntt, bconv = IMPL_PAIRS[int(y[ns:].argmin())]
+    return ks.Schedule(s.dataflow, s.oc_variant, s.chunk, s.order, ntt, bconv)
 
 
 def main():

@@ -7,7 +7,10 @@
   then runs that schedule with the oracle's results;
 * on the committed GB300 timing dataset, the model trained by the library's
   kernels picks schedules within 5% of the exhaustive search on held-out
-  workloads and beats the fixed default schedule.
+  workloads and beats the fixed default schedule;
+* attached to a parameter set, the committed model is what KS_AUTO runs on
+  a tuning-cache miss: its pick is cached and executed with the oracle's
+  results, and the library's features equal the training code's.
 """
 import os
 import tempfile
@@ -20,7 +23,7 @@ from paper_2311_01598_gb300 import inputs
 from tests._gpu import built_lib, need_gpu, pair
 
 pytestmark = pytest.mark.gpu
-DIMS = [7, 64, 64, 64, 12]
+DIMS = [7, 64, 64, 64, 17]
 
 
 def _batch(seed, n=37):
@@ -54,7 +57,7 @@ def test_mlp_training_reduces_loss():
     ks = built_lib()
     rng = np.random.default_rng(3)
     X = rng.normal(size=(256, 7)).astype(np.float32)
-    W = rng.normal(size=(7, 12)).astype(np.float32)
+    W = rng.normal(size=(7, DIMS[-1])).astype(np.float32)
     T = np.tanh(X @ W).astype(np.float32)
     x, t = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
     mlp = ks.Mlp(DIMS, seed=2)
@@ -140,6 +143,54 @@ def test_autotune_impl_times_four_implementations():
             assert np.array_equal(ks.to_host(o0), w0) and np.array_equal(ks.to_host(o1), w1), pr
 
 
+def test_learned_schedule_on_the_execution_path():
+    """A cold tuning cache plus KS_AUTO: the library runs the attached cost
+    model (its forward kernel), caches the predicted schedule under the
+    batch's signature and executes it; every output equals the oracle's.
+    The pick equals ks_predict_schedule's and tune.choose's, and the
+    library's model inputs equal the training code's features."""
+    need_gpu()
+    ks = built_lib()
+    from paper_2311_01598_gb300 import tune
+    model = tune.CostModel.load(os.path.join(tune.DATA_DIR, "cost_model_gb300.npz"))
+    P, C = pair(13, 8, 3, 2)
+    s = inputs.ternary_secret(C.N, 51)
+    evk = C.keygen(s, inputs.galois_secret(s, 3), seed=52)
+    key = P.upload_key(evk)
+    jobs, want = [], []
+    for i in range(5):
+        d = inputs.uniform_towers(C.q, C.N, seed=530 + i)
+        want.append(C.keyswitch(8, d, evk))
+        jobs.append((key, 8, ks.to_device(d), ks.empty((8, C.N)), ks.empty((8, C.N))))
+    assert np.allclose(P.cost_features(jobs), tune.features(13, 8, 2, 3, 5), rtol=0, atol=1e-6)
+    assert P.tune_cache_get(5, 8) is None
+    P.switch_batch(jobs, "AUTO")            # no model: the default schedule
+    assert P.tune_cache_get(5, 8) is None
+    P.set_cost_model(model.mlp, model.t_mean, model.t_scale)
+    pick, pred = P.predict_schedule(jobs)
+    assert len(pred) == len(P.tune_candidates()) + 4
+    ref = tune.choose(model, P, 5, P.tune_candidates())
+    assert pick.as_tuple() == ref.as_tuple() and pick.impl() == ref.impl()
+    for (_, _, _, o0, o1) in jobs:
+        o0.zero_()
+        o1.zero_()
+    P.switch_batch(jobs, "AUTO")            # cache miss: the model's pick, cached
+    got = P.tune_cache_get(5, 8)
+    assert got is not None and got.as_tuple() == pick.as_tuple() and got.impl() == pick.impl()
+    for (_, _, _, o0, o1), (w0, w1) in zip(jobs, want):
+        assert np.array_equal(ks.to_host(o0), w0) and np.array_equal(ks.to_host(o1), w1)
+    # a batch at lower levels: the model's inputs use the mean level and the active digits
+    low = [(key, 5, ks.to_device(inputs.uniform_towers(C.q[:5], C.N, seed=540)), ks.empty((5, C.N)),
+            ks.empty((5, C.N))), (key, 3, ks.to_device(inputs.uniform_towers(C.q[:3], C.N, seed=541)),
+                                  ks.empty((3, C.N)), ks.empty((3, C.N)))]
+    assert np.allclose(P.cost_features(low), tune.features(13, 4, 1, 3, 2), rtol=0, atol=1e-6)
+    P.switch_batch(low, "AUTO")
+    for (_, nact, d, o0, o1) in low:
+        w0, w1 = C.keyswitch(nact, ks.to_host(d), evk)
+        assert np.array_equal(ks.to_host(o0), w0) and np.array_equal(ks.to_host(o1), w1)
+    P.set_cost_model(None)
+
+
 def test_cost_model_regret_on_gb300_dataset():
     """Held-out regret of the learned schedule <= 5% of the exhaustive
     autotuner's best, and less total time than the fixed default schedule."""
@@ -157,3 +208,4 @@ def test_cost_model_regret_on_gb300_dataset():
     ev = tune.evaluate(model, test_rows, di)
     assert ev["model_time_over_best"] <= 0.05, ev
     assert ev["model_time_over_best"] < ev["default_time_over_best"], ev
+    assert ev["impl_time_over_best"] <= 0.05, ev

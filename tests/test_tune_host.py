@@ -16,20 +16,33 @@ def test_workload_sampler_respects_domain_and_cap():
 
 
 def test_features_and_targets():
-    rows = [{"logN": 16, "nq": 24, "dnum": 3, "kp": 8, "batch": 16, "ms": [float(i + 1) for i in range(12)],
-             "best": 0}]
+    rows = [{"logN": 16, "nq": 24, "dnum": 3, "kp": 8, "batch": 16, "ms": [float(i + 1) for i in range(13)],
+             "best": 0, "base": 0, "impl_ms": [2.0, 3.0, 4.0, 5.0], "best_impl": 0}]
     X, T = tune.arrays(rows)
-    assert X.shape == (1, len(tune.FEATURE_NAMES)) and T.shape == (1, 12)
+    assert X.shape == (1, len(tune.FEATURE_NAMES)) and T.shape == (1, 13 + 4)
     assert np.all(np.abs(X) < 3)
     assert math.isclose(float(T[0, 0]), math.log(1 / 16), rel_tol=1e-6)
+    assert math.isclose(float(T[0, 13]), math.log(2 / 16), rel_tol=1e-6)
 
 
 def test_committed_dataset_shape():
+    """The committed GB300 timings: 13 structural candidates and the four
+    implementation pairs per workload, over 5000 timings in all."""
     path = os.path.join(tune.DATA_DIR, "tune_gb300.jsonl")
-    if not os.path.exists(path):
-        return
+    assert os.path.exists(path)
     rows = tune.load(path)
-    n_timings = sum(len(r["ms"]) for r in rows)
-    assert n_timings >= 4000
+    n_timings = sum(len(r["ms"]) + len(r["impl_ms"]) for r in rows)
+    assert n_timings >= 5000
     for r in rows:
-        assert r["best"] == int(np.argmin(r["ms"]))
+        assert len(r["ms"]) == 13 and len(r["impl_ms"]) == 4
+        assert r["best"] == int(np.argmin(r["ms"])) and r["best_impl"] == int(np.argmin(r["impl_ms"]))
+        assert 0 <= r["base"] < 13
+
+
+def test_impl_pairs_match_the_library_order():
+    """The model's last four outputs are the implementation pairs in the
+    order the library's stage 2 times them (ks.h: {(0,1), (1,1), (0,0),
+    (1,0)})."""
+    hdr = open(os.path.join(os.path.dirname(tune.HERE), "include", "ks.h")).read()
+    assert "{(0,1), (1,1), (0,0), (1,0)}" in hdr
+    assert tune.IMPL_PAIRS == ((0, 1), (1, 1), (0, 0), (1, 0))
