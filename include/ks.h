@@ -386,7 +386,7 @@ int ks_mlp_train_step(ks_mlp *mlp, uint32_t batch, const float *d_x, const float
 
 /* Learned schedule choice (the cost model in place of exhaustive search;
  * the paper's dataflows are Sec. IV, the model is this library's).
- * Attach a trained MLP to a parameter set: 7 inputs (ks_cost_features) and
+ * Attach a trained MLP to a parameter set: 10 inputs (ks_cost_features) and
  * one output per structural candidate (ks_tune_candidates order) followed by
  * one per implementation pair (ntt, bconv) in the order {(0,1), (1,1),
  * (0,0), (1,0)}; outputs are normalised log ms per key switch, de-normalised
@@ -406,10 +406,12 @@ int ks_params_set_cost_model(ks_params *params, ks_mlp *model, float t_mean, flo
  * Synchronises `stream`.  KS_EINVAL when no model is attached. */
 int ks_predict_schedule(ks_params *params, uint32_t n, const ks_job *h_jobs, ks_stream_t stream,
                         ks_schedule *out, float *h_pred);
-/* The model's 7 inputs for a batch (host): logN, L+1 (the batch's mean
+/* The model's 10 inputs for a batch (host): logN, L+1 (the batch's mean
  * level, rounded), dnum (the parameter set's at the top level, else the
  * active digits), K, log2 batch, alpha = ceil((L+1)/dnum), log2 input words,
- * each scaled by fixed constants. */
+ * each scaled by fixed constants, then +-1 flags: tensor-core ModUp base
+ * conversion available (the parameter set's alpha <= 9), tensor-core ModDown
+ * (K <= 9), cluster NTT (logN not 13 or 17). */
 int ks_cost_features(const ks_params *params, uint32_t n, const ks_job *h_jobs, float *h_x);
 
 /* A key with pseudo-random residues generated on the device (for timing

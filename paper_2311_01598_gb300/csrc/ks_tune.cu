@@ -83,11 +83,16 @@ static int tune_impl(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps
 
 // ------------------------------------------------------------------ cost model
 // Inputs of the learned cost model: (logN, L+1, dnum, K, log2 batch, alpha,
-// log2 input words), each scaled to roughly unit range by fixed constants.
-// The Python training code computes the same vector (tune.features).
-constexpr int kCostFeatures = 7;
+// log2 input words), each scaled to roughly unit range by fixed constants,
+// then three +-1 flags of which implementations exist for the shape: the
+// tensor-core ModUp base conversion (at most 9 sources per digit), the
+// tensor-core ModDown one (at most 9 special towers), and the cluster NTT
+// (ring degrees other than 2^13 and 2^17); where one is missing, its
+// schedule field selects the same kernels as the other value.  The Python
+// training code computes the same vector (tune.features).
+constexpr int kCostFeatures = 10;
 
-static void cost_features(int logN, int nq, int dnum, int kp, int batch, float *x)
+static void cost_features(int logN, int nq, int dnum, int kp, int batch, int alpha_params, float *x)
 {
     const int alpha = (nq + dnum - 1) / dnum;
     const double words = (double)batch * nq * std::ldexp(1.0, logN);
@@ -98,6 +103,9 @@ static void cost_features(int logN, int nq, int dnum, int kp, int batch, float *
     x[4] = (float)((std::log2((double)batch) - 4) / 2.5);
     x[5] = (float)((alpha - 12) / 12.0);
     x[6] = (float)((std::log2(words) - 22) / 3.0);
+    x[7] = alpha_params <= 9 ? 1.f : -1.f;
+    x[8] = kp <= 9 ? 1.f : -1.f;
+    x[9] = (logN != 13 && logN != 17) ? 1.f : -1.f;
 }
 
 // Features of a batch: its mean level (rounded) stands for L+1; at the top
@@ -108,7 +116,7 @@ static void batch_features(const ks_params *P, uint32_t n, const ks_job *jobs, f
     for (uint32_t i = 0; i < n; ++i) lv += jobs[i].level_towers;
     const int nact = std::max(1, (int)((lv + n / 2) / n));
     const int dnum = nact == P->nq ? P->dnum : (nact + P->alpha - 1) / P->alpha;
-    cost_features(P->logN, nact, dnum, P->kp, (int)n, x);
+    cost_features(P->logN, nact, dnum, P->kp, (int)n, P->alpha, x);
 }
 
 int predict_schedule(ks_params *P, uint32_t n, const ks_job *jobs, cudaStream_t st, ks_schedule *out, float *h_pred)

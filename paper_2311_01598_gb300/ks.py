@@ -488,9 +488,9 @@ class Params:
         return sc, [float(x) for x in pred]
 
     def cost_features(self, jobs) -> np.ndarray:
-        """ks_cost_features: the cost model's 7 inputs for a batch."""
+        """ks_cost_features: the cost model's 10 inputs for a batch."""
         arr, n = self._jobs(jobs)
-        x = (ctypes.c_float * 7)()
+        x = (ctypes.c_float * 10)()
         check(lib().ks_cost_features(self.handle, n, arr, x))
         return np.array(list(x), dtype=np.float32)
 

@@ -33,16 +33,25 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 DATA_DIR = os.path.join(HERE, "data")
 HIDDEN = (64, 64, 64)
 IMPL_PAIRS = ((0, 1), (1, 1), (0, 0), (1, 0))  # (ntt, bconv) in the library's stage-2 order
-FEATURE_NAMES = ("logN", "L+1", "dnum", "K", "log2 batch", "alpha", "log2 words")
+FEATURE_NAMES = ("logN", "L+1", "dnum", "K", "log2 batch", "alpha", "log2 words", "tensor-core ModUp BConv",
+                 "tensor-core ModDown BConv", "cluster NTT")
 WORDS_CAP = (1 << 16) * 24 * 16
 
 
-def features(logN, nq, dnum, kp, batch):
-    """Model inputs, scaled to roughly unit range by fixed constants."""
+def features(logN, nq, dnum, kp, batch, alpha_params=None):
+    """Model inputs: the workload's sizes scaled to roughly unit range by
+    fixed constants, then +-1 flags of which implementations exist for the
+    shape (tensor-core ModUp base conversion: at most 9 sources per digit,
+    alpha_params being the parameter set's alpha, by default ceil(nq/dnum);
+    tensor-core ModDown: at most 9 special towers; cluster NTT: ring degrees
+    other than 2^13 and 2^17).  The library computes the same vector
+    (ks_cost_features)."""
     alpha = -(-nq // dnum)
+    ap = alpha if alpha_params is None else alpha_params
     words = batch * nq * (1 << logN)
     return np.array([(logN - 15) / 2.0, (nq - 25) / 14.0, (dnum - 12) / 12.0, (kp - 6.5) / 3.5,
-                     (math.log2(batch) - 4) / 2.5, (alpha - 12) / 12.0, (math.log2(words) - 22) / 3.0],
+                     (math.log2(batch) - 4) / 2.5, (alpha - 12) / 12.0, (math.log2(words) - 22) / 3.0,
+                     1.0 if ap <= 9 else -1.0, 1.0 if kp <= 9 else -1.0, 1.0 if logN not in (13, 17) else -1.0],
                     dtype=np.float32)
 
 
@@ -209,7 +218,7 @@ def choose(model, params, batch, candidates):
     pair with the lowest predicted times (the library's KS_AUTO makes the
     same pick with the model attached)."""
     from . import ks
-    x = features(params.logN, params.nq, params.dnum, params.kp, batch)[None, :]
+    x = features(params.logN, params.nq, params.dnum, params.kp, batch, params.alpha)[None, :]
     y = model.predict(x)[0]
     ns = len(candidates)
     s = candidates[int(y[:ns].argmin())]

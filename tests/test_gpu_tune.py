@@ -23,7 +23,7 @@ from paper_2311_01598_gb300 import inputs
 from tests._gpu import built_lib, need_gpu, pair
 
 pytestmark = pytest.mark.gpu
-DIMS = [7, 64, 64, 64, 17]
+DIMS = [10, 64, 64, 64, 17]
 
 
 def _batch(seed, n=37):
@@ -56,8 +56,8 @@ def test_mlp_training_reduces_loss():
     torch = need_gpu()
     ks = built_lib()
     rng = np.random.default_rng(3)
-    X = rng.normal(size=(256, 7)).astype(np.float32)
-    W = rng.normal(size=(7, DIMS[-1])).astype(np.float32)
+    X = rng.normal(size=(256, DIMS[0])).astype(np.float32)
+    W = rng.normal(size=(DIMS[0], DIMS[-1])).astype(np.float32)
     T = np.tanh(X @ W).astype(np.float32)
     x, t = torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda()
     mlp = ks.Mlp(DIMS, seed=2)
@@ -162,7 +162,7 @@ def test_learned_schedule_on_the_execution_path():
         d = inputs.uniform_towers(C.q, C.N, seed=530 + i)
         want.append(C.keyswitch(8, d, evk))
         jobs.append((key, 8, ks.to_device(d), ks.empty((8, C.N)), ks.empty((8, C.N))))
-    assert np.allclose(P.cost_features(jobs), tune.features(13, 8, 2, 3, 5), rtol=0, atol=1e-6)
+    assert np.allclose(P.cost_features(jobs), tune.features(13, 8, 2, 3, 5, P.alpha), rtol=0, atol=1e-6)
     assert P.tune_cache_get(5, 8) is None
     P.switch_batch(jobs, "AUTO")            # no model: the default schedule
     assert P.tune_cache_get(5, 8) is None
@@ -183,7 +183,7 @@ def test_learned_schedule_on_the_execution_path():
     low = [(key, 5, ks.to_device(inputs.uniform_towers(C.q[:5], C.N, seed=540)), ks.empty((5, C.N)),
             ks.empty((5, C.N))), (key, 3, ks.to_device(inputs.uniform_towers(C.q[:3], C.N, seed=541)),
                                   ks.empty((3, C.N)), ks.empty((3, C.N)))]
-    assert np.allclose(P.cost_features(low), tune.features(13, 4, 1, 3, 2), rtol=0, atol=1e-6)
+    assert np.allclose(P.cost_features(low), tune.features(13, 4, 1, 3, 2, P.alpha), rtol=0, atol=1e-6)
     P.switch_batch(low, "AUTO")
     for (_, nact, d, o0, o1) in low:
         w0, w1 = C.keyswitch(nact, ks.to_host(d), evk)
