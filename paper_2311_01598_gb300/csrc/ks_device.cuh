@@ -3,9 +3,12 @@
 // Modular arithmetic (all moduli q < 2^56, one uint64 per residue):
 //   * Shoup multiplication by a known constant w with w' = floor(w*2^64/q):
 //     a*w - floor(a*w'/2^64)*q lies in [0, 2q) for every a < 2^64 (Shoup).
+//     The NTT butterflies use an estimate of that quotient built from three
+//     of the four 32x32-bit partial products of a*w' (shoup_est), which
+//     widens the range to [0, 4q) and saves a full 64x64 high product.
 //   * Lazy butterflies (after Harvey): the forward (Cooley-Tukey) butterfly
-//     lets values grow by at most 2q per stage and is reduced once at the
-//     end; the inverse (Gentleman-Sande) one keeps them in [0, 2q).
+//     lets values grow by at most 4q per stage and is reduced once at the
+//     end; the inverse (Gentleman-Sande) one keeps them in [0, 4q).
 //   * Montgomery reduction (REDC) of a 128-bit sum of products with the
 //     stored key, whose factor 2^64 is folded in at upload.
 //   * Base conversion accumulates 28-bit-split partial products in three
@@ -51,14 +54,38 @@ __device__ __forceinline__ u64 reduce4(u64 x, u64 q, u64 q2)  // [0, 4q) -> [0, 
     return x >= q ? x - q : x;
 }
 
+// Shoup product with an estimated quotient.  Write a = a1*2^32 + a0 and
+// w' = floor(w*2^64/q) = p1*2^32 + p0 (32-bit halves).  The exact Shoup
+// quotient is Q = floor(a*w'/2^64), and
+//   a*w'/2^64 = a1*p1 + (a1*p0 + a0*p1)/2^32 + a0*p0/2^64.
+// The estimate E = a1*p1 + floor(a1*p0/2^32) + floor(a0*p1/2^32) drops two
+// fractional parts below 1 each and a term below 1, so a*w'/2^64 - E lies in
+// [0, 3) and Q - E is 0, 1 or 2.  Shoup's bound gives a*w - Q*q in [0, 2q),
+// hence t = a*w - E*q lies in [0, 4q) for every a < 2^64, w < q < 2^56; as
+// 4q < 2^64, t is computed exactly modulo 2^64 (nq = 2^64 - q).  Cost: one
+// 32x32->64 and two high 32x32 products for E instead of a 64x64 high
+// product (three partial products and their carries).
+__device__ __forceinline__ u64 shoup_est(u64 a, u64 w, u64 wp, u64 nq)
+{
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32), p0 = (u32)wp, p1 = (u32)(wp >> 32);
+    u64 e = (u64)a1 * p1 + __umulhi(a1, p0);
+    e += __umulhi(a0, p1);
+    return a * w + e * nq;
+}
+
+// Forward NTT outputs before the final reduction are below kFwdLazy * q:
+// inputs below 4q grow by less than 4q per stage, 4q + 17*4q = 72q for the
+// 17 stages of N = 2^17, and 76q < 2^63 for q < 2^56.
+constexpr u64 kFwdLazy = 72;
+
 // Forward Cooley-Tukey butterfly without a per-stage correction of X: with
-// X, Y < B the outputs are below B + 2q (the Shoup product is below 2q for
-// any 64-bit Y), so a transform of at most 17 stages fed with values below
-// 4q ends below 38q < 2^62 for q < 2^56.  Consumers reduce with reduce_any.
+// X, Y < B the outputs are below B + 4q (the estimated Shoup product is below
+// 4q for any 64-bit Y), so a transform of at most 17 stages fed with values
+// below 4q ends below kFwdLazy*q.  Consumers reduce with reduce_any.
 __device__ __forceinline__ void fwd_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2)
 {
-    const u64 t = shoup_lazy(Y, w, wp, q);
-    Y = X + q2 - t;
+    const u64 t = shoup_est(Y, w, wp, 0 - q);
+    Y = X + (q2 + q2) - t;
     X = X + t;
 }
 
@@ -69,14 +96,17 @@ __device__ __forceinline__ u64 reduce_any(u64 x, u64 q, u64 one_sh)
     return r >= q ? r - q : r;
 }
 
-// Inverse Harvey butterfly: X, Y in [0, 2q) -> [0, 2q).
+// Inverse Harvey butterfly on [0, 4q): X, Y in [0, 4q) -> [0, 4q) (the sum
+// below 8q takes one conditional subtraction of 4q; the difference plus 4q
+// is below 8q and its estimated Shoup product below 4q).
 __device__ __forceinline__ void inv_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2)
 {
+    const u64 q4 = q2 + q2;
     u64 s = X + Y;
-    s = s >= q2 ? s - q2 : s;
-    u64 d = X - Y + q2;
+    s = s >= q4 ? s - q4 : s;
+    const u64 d = X - Y + q4;
     X = s;
-    Y = shoup_lazy(d, w, wp, q);
+    Y = shoup_est(d, w, wp, 0 - q);
 }
 
 // 128-bit accumulator.

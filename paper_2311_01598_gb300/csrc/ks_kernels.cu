@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_fwd_col(Tables T, L
 }
 
 // Forward row pass (stages LA..logN-1).  grid (2^LA/ROWS, limbs).  Output
-// canonical (CANON) or lazy below 40q.  Loads and stores are coalesced (a
+// canonical (CANON) or lazy below kFwdLazy*q.  Loads and stores are coalesced (a
 // second shared-memory exchange returns the values to the first-round
 // layout; measured faster than storing each thread's consecutive values
 // with strided vector stores).
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_fwd_row(Tables T, L
 }
 
 // Inverse row pass (stages logN-1..LA), first half of the iNTT.  Input below
-// 2q; output below 2q.
+// 4q; output below 4q.
 template <class S>
 __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_inv_row(Tables T, LimbMaps ms)
 {
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_inv_col(Tables T, L
     for (int k = 0; k < S::REGA; ++k) {
         u64 v = x[k];
         if (SC != 0) v = shoup_lazy(v, w, wp, q);
-        L.dst[((size_t)(k * S::TA + tau) << S::LB) + c] = reduce2(v, q);
+        L.dst[((size_t)(k * S::TA + tau) << S::LB) + c] = reduce4(v, q, q2);
     }
 }
 
@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(256) k_apply_key(Tables T, int nact, int j0, i
         mac128(sb, dv, key_b<CK>(key, j, tf, n, nfull, T.logN));
         mac128(sa, dv, key_a<CK>(key, j, tf, n, nfull, T.logN, mc.q));
     }
-    // D below 40q: the REDC result is below q + 40*nd*q^2/2^64, reduced fully.
+    // D below kFwdLazy*q: the REDC result is below q + kFwdLazy*nd*q^2/2^64, reduced fully.
     u64 rb = reduce_any(redc(sb, mc.q, mc.mont), mc.q, mc.one_sh);
     u64 ra = key_a_finish<CK>(key, sa, mc, T.key_sc, tf);
     u64 *cb = cp + (size_t)t * N + n;
@@ -564,7 +564,7 @@ struct OutPtrs {
     u64 *p[2];
 };
 
-// ModDown P4: out = cp - v mod q (cp canonical, v lazy below 40q).
+// ModDown P4: out = cp - v mod q (cp canonical, v lazy below kFwdLazy*q).
 __global__ void __launch_bounds__(256) k_down_final(Tables T, const u64 *cp, size_t cp_stride, const u64 *v,
                                                     size_t v_stride, OutPtrs outs)
 {
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(256) k_down_final(Tables T, const u64 *cp, siz
     const size_t N = (size_t)1 << T.logN;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const ModC &mc = T.modc[i];
-    const u64 r = cp[x * cp_stride + (size_t)i * N + n] + 40 * mc.q - v[x * v_stride + (size_t)i * N + n];
+    const u64 r = cp[x * cp_stride + (size_t)i * N + n] + kFwdLazy * mc.q - v[x * v_stride + (size_t)i * N + n];
     outs.p[x][(size_t)i * N + n] = reduce_any(r, mc.q, mc.one_sh);
 }
 

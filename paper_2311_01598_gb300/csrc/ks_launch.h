@@ -60,12 +60,12 @@ LimbMaps one_map(const LimbMap &m, int nlimbs);
 void add_map(LimbMaps &ms, const LimbMap &m, int nlimbs);
 
 // Forward NTT (column pass src->dst, row pass in place on dst).  Input below
-// 4q.  canonical: output in [0, q); otherwise lazy, below 40q (every
+// 4q.  canonical: output in [0, q); otherwise lazy, below kFwdLazy*q = 72q (every
 // consumer of lazy output reduces it).
 int launch_ntt_fwd(const Tables &T, const LimbMaps &m, bool canonical, cudaStream_t st);
 // Inverse NTT without the N^-1 factor (row pass src->dst, column pass in
 // place); the column pass multiplies by the per-entry scale when the job's
-// map has one, or by N^-1 when scale_by_ninv; output canonical.  Input below 2q.
+// map has one, or by N^-1 when scale_by_ninv; output canonical.  Input below 4q.
 int launch_ntt_inv(const Tables &T, const LimbMaps &m, bool scale_by_ninv, cudaStream_t st);
 // One-launch forms over thread-block clusters (ks_ntt_cluster.cu): the same
 // contracts and bit-identical outputs; sc of the inverse: 0 none, 1 the

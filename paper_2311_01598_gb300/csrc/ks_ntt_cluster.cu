@@ -21,7 +21,7 @@ namespace ks {
 
 namespace {
 
-// Forward NTT (input below 4q; output canonical with CANON, else below 40q).
+// Forward NTT (input below 4q; output canonical with CANON, else below kFwdLazy*q).
 // grid (C, limbs), cluster (C, 1, 1): every CTA of a cluster has the same
 // limb, so the early exits below are uniform over the cluster.
 template <class S, int MUL, bool CANON>
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(Cl<S, MUL>::THREADS, Cl<S, MUL>::MINB) k_fwd_c
     for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = CANON ? reduce_any(x[k], q, one_sh) : x[k];
 }
 
-// Inverse NTT (input below 2q), then the scale (SC: 0 none, 1 the job's
+// Inverse NTT (input below 4q), then the scale (SC: 0 none, 1 the job's
 // per-entry scale, 2 N^-1); output canonical.
 template <class S, int MUL, int SC>
 __global__ void __launch_bounds__(Cl<S, MUL>::THREADS, Cl<S, MUL>::MINB) k_inv_cl(Tables T, LimbMaps ms)
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(Cl<S, MUL>::THREADS, Cl<S, MUL>::MINB) k_inv_c
     for (int k = 0; k < S::REGA; ++k) {
         u64 v = x[k];
         if (SC != 0) v = shoup_lazy(v, w, wp, q);
-        L.dst[((size_t)(k * S::TA + tau) << S::LB) + c] = reduce2(v, q);
+        L.dst[((size_t)(k * S::TA + tau) << S::LB) + c] = reduce4(v, q, q2);
     }
 }
 

@@ -23,8 +23,8 @@
 
 namespace ks {
 
-// x * e with the stored key word e: REDC of the 128-bit product; x < 40q,
-// so the result is below q + 40q^2/2^64 < 2q before the correction.
+// x * e with the stored key word e: REDC of the 128-bit product; x below
+// kFwdLazy*q, so the result is below q + 72q^2/2^64 < 2q before the correction.
 __device__ __forceinline__ u64 key_mul(u64 x, u64 e, u64 q, u64 mont)
 {
     U128 t = {0, 0};
@@ -88,11 +88,11 @@ __device__ __noinline__ void oc_down_store(const u64 *gin, const ulonglong2 *twt
 #pragma unroll
     for (int i = 0; i < S::REGB; ++i) v[i] = gin[i * S::TB + tau];
     row_fwd_core<S>(v, TwRow{twt, G}, srow, tau, q, 2 * q);
-    const u64 q40 = 40 * q;
+    const u64 qlz = kFwdLazy * q;
 #pragma unroll
     for (int i = 0; i < S::REGB; ++i) {
         const int c = i * S::TB + tau;
-        out[c] = reduce_any(acc[c] + q40 - v[i], q, one_sh);
+        out[c] = reduce_any(acc[c] + qlz - v[i], q, one_sh);
     }
 }
 
@@ -366,13 +366,13 @@ __global__ void __launch_bounds__(256) k_oc_comb_q(Tables T, OcJobs oj)
     u64 vb[V], va[V], o0[V], o1[V];
     ldv<V>(J.tmp + (size_t)(J.nd * nact + t) * N + n, vb);
     ldv<V>(J.tmp + (size_t)((J.nd + 1) * nact + t) * N + n, va);
-    const u64 q40 = 40 * mc.q;
+    const u64 qlz = kFwdLazy * mc.q;
 #pragma unroll
     for (int c = 0; c < V; ++c) {
         const u64 cb = reduce_any(redc(sb[c], mc.q, mc.mont), mc.q, mc.one_sh);
         const u64 ca = key_a_finish<CK>(J.key, sa[c], mc, T.key_sc, t);
-        o0[c] = reduce_any(cb + q40 - vb[c], mc.q, mc.one_sh);
-        o1[c] = reduce_any(ca + q40 - va[c], mc.q, mc.one_sh);
+        o0[c] = reduce_any(cb + qlz - vb[c], mc.q, mc.one_sh);
+        o1[c] = reduce_any(ca + qlz - va[c], mc.q, mc.one_sh);
     }
     stv<V>(J.out0 + (size_t)t * N + n, o0);
     stv<V>(J.out1 + (size_t)t * N + n, o1);
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(256) k_oc_comb_qg(Tables T, OcJobs oj, KeyGrou
                 }
             }
     }
-    const u64 q40 = 40 * mc.q;
+    const u64 qlz = kFwdLazy * mc.q;
 #pragma unroll
     for (int i = 0; i < kGroupJobs; ++i)
         if (i < cnt) {
@@ -527,8 +527,8 @@ __global__ void __launch_bounds__(256) k_oc_comb_qg(Tables T, OcJobs oj, KeyGrou
                 for (int c = 0; c < V; ++c) {
                     const u64 cb = reduce_any(redc(sb[i][c], mc.q, mc.mont), mc.q, mc.one_sh);
                     const u64 ca = key_a_finish<CK>(key, sa[i][c], mc, T.key_sc, t);
-                    o0[c] = reduce_any(cb + q40 - vb[c], mc.q, mc.one_sh);
-                    o1[c] = reduce_any(ca + q40 - va[c], mc.q, mc.one_sh);
+                    o0[c] = reduce_any(cb + qlz - vb[c], mc.q, mc.one_sh);
+                    o1[c] = reduce_any(ca + qlz - va[c], mc.q, mc.one_sh);
                 }
                 stv<V>(J.out0 + (size_t)t * N + n, o0);
                 stv<V>(J.out1 + (size_t)t * N + n, o1);
@@ -691,13 +691,13 @@ __global__ void __launch_bounds__(256) k_oc_comb_qw(Tables T, OcJobs oj)
     u64 vb[V], va[V], o0[V], o1[V];
     ldv<V>(v + (size_t)t * N + n, vb);
     ldv<V>(v + (size_t)(nact + t) * N + n, va);
-    const u64 q40 = 40 * mc.q;
+    const u64 qlz = kFwdLazy * mc.q;
 #pragma unroll
     for (int c = 0; c < V; ++c) {
         const u64 cb = reduce_any(redc(sb[c], mc.q, mc.mont), mc.q, mc.one_sh);
         const u64 ca = key_a_finish<CK>(J.key, sa[c], mc, T.key_sc, t);
-        o0[c] = reduce_any(cb + q40 - vb[c], mc.q, mc.one_sh);
-        o1[c] = reduce_any(ca + q40 - va[c], mc.q, mc.one_sh);
+        o0[c] = reduce_any(cb + qlz - vb[c], mc.q, mc.one_sh);
+        o1[c] = reduce_any(ca + qlz - va[c], mc.q, mc.one_sh);
     }
     stv<V>(J.out0 + (size_t)t * N + n, o0);
     stv<V>(J.out1 + (size_t)t * N + n, o1);

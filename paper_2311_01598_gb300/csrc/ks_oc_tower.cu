@@ -44,7 +44,7 @@ struct TowerShape {
 };
 
 // x * e (e a stored key word, Montgomery form with the tower's fold factor):
-// REDC of the 128-bit product; x below 40q gives a result below 2q.
+// REDC of the 128-bit product; x below kFwdLazy*q gives a result below 2q.
 __device__ __forceinline__ u64 key_prod(u64 x, u64 e, u64 q, u64 mont)
 {
     U128 t = {0, 0};
@@ -55,7 +55,7 @@ __device__ __forceinline__ u64 key_prod(u64 x, u64 e, u64 q, u64 mont)
 // Forward NTT of one limb of tower t spread over the cluster.  Enters with
 // xc[k] = element (row k*TA + tauc, column c) of the CTA's column block
 // (below 4q) and leaves with xr[k] = element k*TB + tau of row h (below
-// 40q).  Contains block and cluster barriers: every thread of every CTA of
+// kFwdLazy*q).  Contains block and cluster barriers: every thread of every CTA of
 // the cluster calls it.
 template <class S>
 __device__ __forceinline__ void tower_ntt(u64 (&xc)[S::REGA], u64 (&xr)[S::REGB], u64 *buf,
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(Cl<S, 1>::THREADS, 2) k_oc_tower(Tables T, OcJ
     // instruction fetch).
     u64 xc[S::REGA], xr[S::REGB];
     const int nup = J.nd - 1;
-    const u64 q40 = 40 * q;
+    const u64 qlz = kFwdLazy * q;
     for (int p = 0; p < nup + 2; ++p) {
         const bool down = p >= nup;
         const int j = down ? 0 : (p < j0 ? p : p + 1);
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(Cl<S, 1>::THREADS, 2) k_oc_tower(Tables T, OcJ
 #pragma unroll
             for (int k = 0; k < S::REGB; ++k) {
                 const int e = k * S::TB + tau;
-                out[e] = reduce_any(acc[e] + q40 - xr[k], q, mc.one_sh);
+                out[e] = reduce_any(acc[e] + qlz - xr[k], q, mc.one_sh);
             }
         }
     }

@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(256) k_shard_keyprod(Tables T, int nact, int n
 }
 
 // ModDown P4 of the rank's Q towers: out_x[s] = c'_x[s] - v_x[s] mod q (P^-1
-// folded into the key), v lazy NTT output below 40q.  grid (N/256, nq, 2).
+// folded into the key), v lazy NTT output below kFwdLazy*q.  grid (N/256, nq, 2).
 __global__ void __launch_bounds__(256) k_shard_final(Tables T, ShardLv L, const u64 *cp_own, const u64 *v, u64 *out0,
                                                      u64 *out1)
 {
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(256) k_shard_final(Tables T, ShardLv L, const 
     const size_t N = (size_t)1 << T.logN;
     const size_t n = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const ModC &mc = T.modc[L.q0 + s];
-    const u64 r = cp_own[((size_t)x * L.nown + s) * N + n] + 40 * mc.q - v[((size_t)x * L.nq + s) * N + n];
+    const u64 r = cp_own[((size_t)x * L.nown + s) * N + n] + kFwdLazy * mc.q - v[((size_t)x * L.nq + s) * N + n];
     (x == 0 ? out0 : out1)[(size_t)s * N + n] = reduce_any(r, mc.q, mc.one_sh);
 }
 

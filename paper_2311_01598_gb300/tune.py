@@ -2,7 +2,8 @@
 
 * ``collect``: sample workloads of the cost model's domain (logN 13-17, L+1
   2-48, dnum 1..L+1, K 1-12, batch 1-256, capped so one batch holds at most
-  2^16*24*16 words of input), time every structural candidate schedule of
+  2^16*24*16 words of input; uniformly, or near the paper-sized parameter
+  sets with ``--anchors``), time every structural candidate schedule of
   each and then the fastest structure under the four implementation pairs
   (NTT form x base-conversion engine) with ``ks_autotune`` (CUDA events, best
   of k), and write one JSON line per workload.
@@ -66,8 +67,27 @@ def sample_workload(rng):
     return logN, nq, dnum, kp, batch
 
 
-def collect(n_workloads, seed, out_path, reps=2, log=print):
-    """Time every candidate schedule on n_workloads sampled workloads."""
+# Parameter sets of the paper's size inside the model's domain (logN, L+1,
+# K, dnum): the benchmark set, ARK and DPRIVE (Table III), the serving mix's
+# N = 2^17 set.
+ANCHORS = ((16, 24, 8, 3), (16, 24, 6, 4), (16, 26, 7, 3), (17, 36, 12, 3))
+
+
+def sample_anchor(rng):
+    """One workload near a paper-sized parameter set: L+1 within 4 and K
+    within 2 of an anchor, dnum within 1, batch log-uniform 1..128."""
+    logN, nq0, kp0, d0 = ANCHORS[int(rng.integers(0, len(ANCHORS)))]
+    nq = int(np.clip(nq0 + rng.integers(-4, 5), 2, 48))
+    kp = int(np.clip(kp0 + rng.integers(-2, 3), 1, 12))
+    dnum = int(np.clip(d0 + rng.integers(-1, 2), 1, nq))
+    batch = int(round(2 ** rng.uniform(0, 7)))
+    batch = max(1, min(batch, WORDS_CAP // (nq << logN)))
+    return logN, nq, dnum, kp, batch
+
+
+def collect(n_workloads, seed, out_path, reps=2, log=print, anchors=False):
+    """Time every candidate schedule on n_workloads sampled workloads
+    (uniform over the domain, or near the paper-sized sets with anchors)."""
     import torch
 
     from . import ks
@@ -75,7 +95,7 @@ def collect(n_workloads, seed, out_path, reps=2, log=print):
     t0 = time.time()
     with open(out_path, "w") as f:
         for w in range(n_workloads):
-            logN, nq, dnum, kp, batch = sample_workload(rng)
+            logN, nq, dnum, kp, batch = (sample_anchor if anchors else sample_workload)(rng)
             P = ks.Params(logN, nq, kp, dnum)
             key = P.key_synthetic(seed * 1000 + w)
             qmin = min(P.q)
@@ -89,7 +109,8 @@ def collect(n_workloads, seed, out_path, reps=2, log=print):
             row = {"logN": logN, "nq": nq, "dnum": dnum, "kp": kp, "batch": batch,
                    "ms": [round(m, 5) for m in ms_s], "best": int(np.argmin(ms_s)),
                    "base": cands.index(best.as_tuple()),
-                   "impl_ms": [round(m, 5) for m in ms_i], "best_impl": int(np.argmin(ms_i))}
+                   "impl_ms": [round(m, 5) for m in ms_i], "best_impl": int(np.argmin(ms_i)),
+                   "sampler": "anchor" if anchors else "uniform"}
             f.write(json.dumps(row) + "\n")
             f.flush()
             del jobs, key, P
@@ -235,6 +256,7 @@ def main():
     c.add_argument("--seed", type=int, default=7)
     c.add_argument("--reps", type=int, default=2)
     c.add_argument("--out", default=os.path.join(DATA_DIR, "tune_gb300.jsonl"))
+    c.add_argument("--anchors", action="store_true", help="sample near the paper-sized parameter sets")
     t = sub.add_parser("train")
     t.add_argument("--data", default=os.path.join(DATA_DIR, "tune_gb300.jsonl"))
     t.add_argument("--epochs", type=int, default=3000)
@@ -242,7 +264,7 @@ def main():
     a = ap.parse_args()
     if a.cmd == "collect":
         os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
-        collect(a.n, a.seed, a.out, a.reps)
+        collect(a.n, a.seed, a.out, a.reps, anchors=a.anchors)
     else:
         from . import ks
         rows = load(a.data)
