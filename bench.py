@@ -479,11 +479,16 @@ def main():
     work = class_work()
     from paper_2311_01598_gb300 import launch_summary
     traffic_rec = launch_summary.recorded_traffic()  # ncu DRAM bytes per key switch, current sources only
+    pipes_rec = launch_summary.recorded_pipes()      # ncu integer-pipe utilisation, current sources only
 
     def class_roofline(name, cnt, tot_ms):
         secs_per_ks = tot_ms / 1e3 / (args.steps * B)
         out = {"kernel": name, "launches_per_step": cnt / args.steps, "per_launch_ms": round(tot_ms / cnt, 4),
                "share_of_step": round(tot_ms / ms_prof, 4), "traffic": None}
+        if name in pipes_rec:
+            out["pipe"] = {k: v for k, v in pipes_rec[name].items() if k != "capture"}
+            out["pipe"]["basis"] = ("ncu hardware counters of one launch (fmaheavy = the 32-bit integer multiply "
+                                    "pipe): paper_2311_01598_gb300/data/ncu_pipes_gb300.json")
         if name in traffic_rec:
             out["traffic"] = int(traffic_rec[name] * B * args.steps / cnt)
             out["traffic_basis"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per key switch "

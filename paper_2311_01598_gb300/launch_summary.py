@@ -18,6 +18,12 @@ them only while the sources are unchanged):
 
     python -m paper_2311_01598_gb300.launch_summary traffic prof.ncu-rep --key-switches 4 \
         --capture "<the ncu command>"
+
+`pipes` records a kernel's integer-pipe utilisation (fmaheavy = the 32-bit
+integer multiply pipe, ALU, issue) from an ncu report, the same way, in
+data/ncu_pipes_gb300.json:
+
+    python -m paper_2311_01598_gb300.launch_summary pipes prof.ncu-rep --capture "<the ncu command>"
 """
 from __future__ import annotations
 
@@ -32,9 +38,15 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 TRAFFIC_PATH = os.path.join(HERE, "data", "ncu_traffic_gb300.json")
+PIPES_PATH = os.path.join(HERE, "data", "ncu_pipes_gb300.json")
+PIPE_METRICS = {"fmaheavy_active": "sm__pipe_fmaheavy_cycles_active.avg.pct_of_peak_sustained_active",
+                "alu_active": "sm__pipe_alu_cycles_active.avg.pct_of_peak_sustained_active",
+                "issue_active": "smsp__issue_active.avg.pct_of_peak_sustained_active",
+                "warps_active": "sm__warps_active.avg.pct_of_peak_sustained_active"}
 # the device-code files whose change invalidates recorded per-kernel DRAM traffic
 KERNEL_SOURCES = ("csrc/ks_kernels.cu", "csrc/ks_oc.cu", "csrc/ks_bconv_tc.cu", "csrc/ks_ntt_cluster.cu",
-                  "csrc/ks_device.cuh", "csrc/ks_ntt_core.cuh", "csrc/ks_launch.h")
+                  "csrc/ks_device.cuh", "csrc/ks_ntt_core.cuh", "csrc/ks_launch.h", "csrc/ks_oc_tower.cu",
+                  "csrc/ks_cluster.cuh")
 
 
 def kernel_sources_sha() -> str:
@@ -56,6 +68,48 @@ def recorded_traffic():
     if rec.get("sources_sha256") != kernel_sources_sha():
         return {}
     return {k: v["dram_bytes_per_ks"] for k, v in rec.get("kernels", {}).items()}
+
+
+def recorded_pipes():
+    """{kernel library name: {fraction name: value in [0, 1]}} recorded on
+    the current sources, else {}."""
+    if not os.path.exists(PIPES_PATH):
+        return {}
+    with open(PIPES_PATH) as f:
+        rec = json.load(f)
+    if rec.get("sources_sha256") != kernel_sources_sha():
+        return {}
+    return {k: dict(v, capture=rec.get("capture")) for k, v in rec.get("kernels", {}).items()}
+
+
+def pipes_from_report(rep):
+    """Per library kernel name: the pipe fractions of its first captured
+    launch in an ncu report."""
+    out = subprocess.run(["ncu", "-i", rep, "--page", "raw", "--csv"], check=True, capture_output=True,
+                         text=True).stdout
+    rows = list(csv.reader(io.StringIO(out)))
+    hdr = rows[0]
+    ix = {h: i for i, h in enumerate(hdr)}
+    per = {}
+    for r in rows[2:]:
+        lib = lib_name(r[ix["Kernel Name"]])
+        if lib is None or lib in per:
+            continue
+        per[lib] = {k: round(float(r[ix[m]].replace(",", "")) / 100.0, 4) for k, m in PIPE_METRICS.items()
+                    if m in ix}
+    return per
+
+
+def main_pipes(argv):
+    """`pipes` subcommand: record pipe utilisation from an ncu report."""
+    ap = argparse.ArgumentParser()
+    ap.add_argument("report")
+    ap.add_argument("--capture", required=True, help="the command that made the report")
+    a = ap.parse_args(argv)
+    rec = {"sources_sha256": kernel_sources_sha(), "capture": a.capture, "kernels": pipes_from_report(a.report)}
+    with open(PIPES_PATH, "w") as f:
+        json.dump(rec, f, indent=1)
+    print(json.dumps(rec, indent=1))
 
 
 def read_launches(path):
@@ -108,7 +162,8 @@ LIB_NAMES = {"k_fwd_row": "ntt_fwd_row", "k_fwd_col": "ntt_fwd_col", "k_inv_row"
              "k_oc_comb_p": "oc_comb_p", "k_oc_comb_qg": "oc_comb_q", "k_oc_comb_pg": "oc_comb_p",
              "k_fwd_cl": "ntt_fwd_cl", "k_inv_cl": "ntt_inv_cl", "k_oc_rowP": "oc_row_p", "k_oc_rowQ": "oc_row_q",
              "k_apply_key": "apply_key", "k_down_final": "down_final", "k_automorph": "automorph",
-             "k_bypass_copy": "bypass_copy", "k_scale": "scale"}
+             "k_bypass_copy": "bypass_copy", "k_scale": "scale", "k_oc_tower": "oc_tower",
+             "k_shard_keyprod": "shard_keyprod", "k_shard_final": "shard_final"}
 
 
 def lib_name(kernel_name):
@@ -163,6 +218,8 @@ def main():
     import sys
     if len(sys.argv) > 1 and sys.argv[1] == "traffic":
         return main_traffic(sys.argv[2:])
+    if len(sys.argv) > 1 and sys.argv[1] == "pipes":
+        return main_pipes(sys.argv[2:])
     ap = argparse.ArgumentParser()
     ap.add_argument("csv")
     ap.add_argument("--first", type=int, default=0)
