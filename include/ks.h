@@ -107,15 +107,21 @@ int ks_params_info(const ks_params *params, uint64_t *h_q, uint64_t *h_p,
  *     column and row passes exchanging the limb through distributed shared
  *     memory, instead of two launches through device memory.  Ring degrees
  *     without a cluster form (2^13, 2^17) keep the two launches.
+ *   KS_OPT_NTT_ROW_STAGE (0 or 1): run the forward row passes as persistent
+ *     blocks whose row blocks are staged in shared memory by bulk copies
+ *     (the next block's copy in flight while the current one is
+ *     transformed).  Row-pass inputs that are not 16-byte aligned keep the
+ *     plain pass.  Same results.
  * Returns KS_EINVAL for an unknown option or value.  Not thread-safe with
  * concurrent calls on the same params object. */
-enum { KS_OPT_BCONV_TENSOR = 1, KS_OPT_BATCH_LANES = 2, KS_OPT_NTT_CLUSTER = 3 };
+enum { KS_OPT_BCONV_TENSOR = 1, KS_OPT_BATCH_LANES = 2, KS_OPT_NTT_CLUSTER = 3, KS_OPT_NTT_ROW_STAGE = 4 };
 int ks_params_set_option(ks_params *params, int option, int value);
 
 /* Device-side status of the library on the params object's GPU: bit 0 is set
- * when a tensor-core kernel gave up waiting for its MMAs (bounded wait) since
- * the last call with clear = 1; its outputs are then not valid.  Returns
- * KS_OK, or KS_ECUDA if the flag cannot be read. */
+ * when a tensor-core kernel gave up waiting for its MMAs, bit 1 when a staged
+ * row pass gave up waiting for a bulk copy (bounded waits), since the last
+ * call with clear = 1; the outputs of that work are then not valid.  Returns
+ * KS_OK, or KS_ECUDA if the flags cannot be read. */
 int ks_device_status(const ks_params *params, int clear, uint32_t *flags);
 
 /* Generate and upload an evaluation key switching s' -> s (hybrid key):

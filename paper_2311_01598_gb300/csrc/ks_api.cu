@@ -739,6 +739,11 @@ int ks_params_set_option(ks_params *P, int option, int value)
         P->tables.ntt_cluster = value;
         return KS_OK;
     }
+    if (option == KS_OPT_NTT_ROW_STAGE && (value == 0 || value == 1)) {
+        P->row_stage = value;
+        P->tables.row_stage = value;
+        return KS_OK;
+    }
     if (option == KS_OPT_BATCH_LANES && value >= 1 && value <= 4) {
         P->batch_lanes = value;
         return KS_OK;
@@ -753,8 +758,9 @@ int ks_device_status(const ks_params *P, int clear, uint32_t *flags)
     if (!flags) return fail(KS_EINVAL, "flags is NULL");
     if ((rc = set_device(P)) != KS_OK) return rc;
     const int v = tc_error_flag(clear != 0);
-    if (v < 0) return fail(KS_ECUDA, "device status unreadable");
-    *flags = v ? 1u : 0u;
+    const int w = ntt_error_flag(clear != 0);
+    if (v < 0 || w < 0) return fail(KS_ECUDA, "device status unreadable");
+    *flags = (v ? 1u : 0u) | (w ? 2u : 0u);
     return KS_OK;
 }
 

@@ -331,6 +331,7 @@ int build_tables(ks_params *P)
     T.up_tc_lvl = P->d_up_tc_lvl;
     T.dn_tc = P->bconv_tensor ? P->d_dn_tc : nullptr;
     T.ntt_cluster = P->ntt_cluster;
+    T.row_stage = P->row_stage;
     T.logN = P->logN;
     T.nq = P->nq;
     T.kp = P->kp;

@@ -77,6 +77,7 @@ struct Tables {
     const int *up_tc_lvl;
     const uint4 *dn_tc;
     int ntt_cluster;  // host side: NTTs as one cluster launch where supported
+    int row_stage;    // host side: forward row passes staged by bulk copies (k_fwd_row_st)
     int logN;
     int nq, kp, alpha, ndig;
 };
@@ -109,6 +110,7 @@ struct ks_params {
     int *d_up_tc_lvl = nullptr;
     int bconv_tensor = 1;                // use the tensor-core BConv where supported
     int ntt_cluster = 0;                 // NTTs as one cluster launch where supported
+    int row_stage = 0;                   // forward row passes staged by bulk copies
     int batch_lanes = 2;                 // internal streams a large Output-Centric batch is split over
     cudaStream_t lane_st[4] = {};        // created on first use
     cudaEvent_t lane_ev[5] = {};

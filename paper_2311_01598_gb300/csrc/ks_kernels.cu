@@ -80,6 +80,145 @@ __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_fwd_row(Tables T, L
     for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = CANON ? reduce_any(x[k], q, one_sh) : x[k];
 }
 
+// ------------------------------------------------------------------ staged row pass
+// Forward row pass with its row blocks staged in shared memory by the bulk
+// copy engine (TMA, one 1-D cp.async.bulk of ROWS contiguous rows per item).
+// Persistent CTAs of ROWS rows walk the launch's row blocks (item b = limb
+// b / (2^LA/ROWS), row block b % (2^LA/ROWS)) with stride gridDim.x: the
+// next item's rows are copied into the second buffer while the current item
+// is transformed, so the loads of a block overlap the butterflies of the
+// previous one instead of stalling its warps.  A buffer, once its values are
+// in registers, is the item's row-exchange buffer.  Same butterflies,
+// twiddles and output as k_fwd_row.
+__device__ int g_ntt_error;  // set when a staged load's wait gives up
+constexpr int kStageWaitLimit = 1 << 22;
+
+template <class S>
+struct StagedRow {
+    static constexpr int ROWW = S::ROWS * (1 << S::LB);  // words of one row block
+    static constexpr int BUFW = ROWW > S::ROWS * S::ROWPAD ? ROWW : S::ROWS * S::ROWPAD;
+    static constexpr int BYTES = ROWW * 8;
+    static constexpr int SMEM = 2 * BUFW * 8 + S::ROWS * S::REGB * 16 + 16;
+};
+
+__device__ __forceinline__ bool stage_wait(uint32_t mbar, uint32_t phase)
+{
+    uint32_t done = 0;
+    for (int it = 0; it < kStageWaitLimit && !done; ++it)
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase)
+            : "memory");
+    return done != 0;
+}
+
+// First item >= b whose limb is transformed (bypassed digit limbs are skipped).
+template <class S>
+__device__ __forceinline__ int staged_next(const Tables &T, const LimbMaps &ms, int b, int total, int nblk)
+{
+    for (; b < total; b += gridDim.x)
+        if (!limb_ref(ms, b / nblk, T.nq, T.alpha, S::LOGN).skip) return b;
+    return total;
+}
+
+template <class S>
+__device__ __forceinline__ void staged_issue(const Tables &T, const LimbMaps &ms, int b, int nblk, u64 *dst,
+                                             uint32_t mbar)
+{
+    const LimbRef L = limb_ref(ms, b / nblk, T.nq, T.alpha, S::LOGN);
+    const u64 *src = L.src + (((size_t)(b % nblk) * S::ROWS) << S::LB);
+    // the buffer was last read through the generic proxy: order those reads
+    // before the copy engine's writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"((uint32_t)StagedRow<S>::BYTES)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            (uint32_t)__cvta_generic_to_shared(dst)),
+        "l"(src), "r"((uint32_t)StagedRow<S>::BYTES), "r"(mbar)
+        : "memory");
+}
+
+// 12 resident CTAs per SM (18 KB of shared memory each at 2^16): at most 85
+// registers a thread.
+template <class S, bool CANON>
+__global__ void __launch_bounds__(S::THREADS_B, 12) k_fwd_row_st(Tables T, LimbMaps ms)
+{
+    typedef StagedRow<S> SR;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u64 *buf0 = reinterpret_cast<u64 *>(smem_raw);
+    ulonglong2 *tsh_all = reinterpret_cast<ulonglong2 *>(buf0 + 2 * SR::BUFW);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(tsh_all + S::ROWS * S::REGB);
+    constexpr int nblk = (1 << S::LA) / S::ROWS;
+    const int total = ms.pre[ms.n] * nblk;
+    const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
+    const uint32_t mb0 = (uint32_t)__cvta_generic_to_shared(&mbar[0]);
+    const uint32_t mb1 = (uint32_t)__cvta_generic_to_shared(&mbar[1]);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    int b = staged_next<S>(T, ms, blockIdx.x, total, nblk);
+    if (b < total && threadIdx.x == 0) staged_issue<S>(T, ms, b, nblk, buf0, mb0);
+    uint32_t phase = 0;  // bit k: parity of buffer k's next completion
+    int cur = 0;
+    bool ok = true;
+    while (b < total) {
+        const int nb = staged_next<S>(T, ms, b + gridDim.x, total, nblk);
+        // the other buffer's last reader (the previous item) finished at its
+        // final block barrier
+        if (nb < total && threadIdx.x == 0) staged_issue<S>(T, ms, nb, nblk, buf0 + (cur ^ 1) * SR::BUFW, cur ? mb0 : mb1);
+        u64 *sb = buf0 + cur * SR::BUFW;
+        if (!stage_wait(cur ? mb1 : mb0, (phase >> cur) & 1)) {
+            ok = false;
+            break;
+        }
+        phase ^= 1u << cur;
+        const LimbRef L = limb_ref(ms, b / nblk, T.nq, T.alpha, S::LOGN);
+        const ModC &mc = T.modc[L.tf];
+        const u64 q = mc.q, q2 = 2 * q;
+        const int h = (b % nblk) * S::ROWS + rr;
+        const int G = (1 << S::LA) + h;
+        const ulonglong2 *twt = T.tw + ((size_t)L.tf << S::LOGN);
+        ulonglong2 *tsh = tsh_all + rr * S::REGB;
+        u64 x[S::REGB];
+#pragma unroll
+        for (int k = 0; k < S::REGB; ++k) x[k] = sb[rr * (1 << S::LB) + k * S::TB + tau];
+        stage_row_round1<S>(tsh, twt, G, tau);
+        __syncthreads();  // every row is in registers before the buffer becomes the exchange buffer
+        row_fwd_core<S>(x, TwStaged<S>{tsh, twt, G}, sb + rr * S::ROWPAD, tau, q, q2);
+        u64 *gout = L.dst + ((size_t)h << S::LB);
+        const u64 one_sh = CANON ? mc.one_sh : 0;
+#pragma unroll
+        for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = CANON ? reduce_any(x[k], q, one_sh) : x[k];
+        b = nb;
+        cur ^= 1;
+    }
+    if (!ok && threadIdx.x == 0) {
+        atomicExch(&g_ntt_error, 1);
+        // bounded waits for the copies still in flight before the CTA exits
+        stage_wait(mb0, phase & 1);
+        stage_wait(mb1, (phase >> 1) & 1);
+    }
+}
+
+int ntt_error_flag(bool clear)
+{
+    int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_ntt_error, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+    }
+    if (clear && v) {
+        const int z = 0;
+        cudaMemcpyToSymbol(g_ntt_error, &z, sizeof(int));
+    }
+    return v;
+}
+
 // Inverse row pass (stages logN-1..LA), first half of the iNTT.  Input below
 // 4q; output below 4q.
 template <class S>
@@ -201,10 +340,53 @@ static void fwd_col_S(const Tables &T, const LimbMaps &m, cudaStream_t st)
               k_fwd_col<S><<<limb_grid((1 << S::LB) / S::COLS, m.pre[m.n]), S::THREADS_A, S::SMEM_A, st>>>(T, m));
 }
 
+// Persistent grid of the staged row pass: resident CTAs per SM x SMs, at
+// most one CTA per item.
+template <class S, bool CANON>
+static int staged_grid(int items)
+{
+    static std::atomic<uint64_t> done{0};
+    static int per_sm[64] = {0}, sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    once_per_device(done, [dev] {
+        cudaFuncSetAttribute(k_fwd_row_st<S, CANON>, cudaFuncAttributeMaxDynamicSharedMemorySize, StagedRow<S>::SMEM);
+        int n = 0, c = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fwd_row_st<S, CANON>, S::THREADS_B,
+                                                          StagedRow<S>::SMEM) != cudaSuccess ||
+            cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            n = 1;
+            c = 1;
+        }
+        per_sm[dev & 63] = std::max(1, n);
+        sms[dev & 63] = std::max(1, c);
+    });
+    return std::max(1, std::min(items, per_sm[dev & 63] * sms[dev & 63]));
+}
+
 template <class S>
 static void fwd_row_S(const Tables &T, const LimbMaps &m, bool canonical, cudaStream_t st)
 {
     set_smem_attrs<S>();
+    // the bulk copies need 16-byte aligned sources (row blocks of an aligned
+    // limb are); maps over caller buffers that are not run the plain pass
+    bool aligned = true;
+    for (int j = 0; j < m.n; ++j) aligned = aligned && (((uintptr_t)m.m[j].src & 15) == 0);
+    if (T.row_stage && aligned) {
+        const int items = m.pre[m.n] * ((1 << S::LA) / S::ROWS);
+        if (canonical)
+            KS_LAUNCH(st, "ntt_fwd_row",
+                      k_fwd_row_st<S, true><<<staged_grid<S, true>(items), S::THREADS_B, StagedRow<S>::SMEM, st>>>(T, m));
+        else
+            KS_LAUNCH(st, "ntt_fwd_row",
+                      k_fwd_row_st<S, false><<<staged_grid<S, false>(items), S::THREADS_B, StagedRow<S>::SMEM, st>>>(T,
+                                                                                                                   m));
+        return;
+    }
     const dim3 gb = limb_grid((1 << S::LA) / S::ROWS, m.pre[m.n]);
     if (canonical)
         KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));

@@ -132,6 +132,8 @@ int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, 
 void tc_slab(const std::vector<u64> &c, uint16_t *slab);
 // Device flag set by a tensor-core kernel whose MMA wait gave up (-1: unreadable).
 int tc_error_flag(bool clear);
+// Device flag set by a staged row pass whose bulk-copy wait gave up (-1: unreadable).
+int ntt_error_flag(bool clear);
 
 // ModUp P4+P5 (single job): cp[x][t] = sum_j D_{j,t} * evk_{j,x,t}, D_{j,t} = d_t
 // inside digit j; D holds lazy NTT output.  accumulate: add to cp.  galois

@@ -355,8 +355,14 @@ class Params:
         (distributed shared memory between its passes) where supported."""
         check(lib().ks_params_set_option(self.handle, 3, int(on)))
 
+    def set_row_stage(self, on: bool) -> None:
+        """KS_OPT_NTT_ROW_STAGE: forward row passes staged in shared memory by
+        bulk copies (persistent blocks, next block's copy in flight)."""
+        check(lib().ks_params_set_option(self.handle, 4, 1 if on else 0))
+
     def device_status(self, clear: bool = True) -> int:
-        """ks_device_status: bit 0 = a tensor-core kernel's bounded MMA wait gave up."""
+        """ks_device_status: bit 0 = a tensor-core kernel's bounded MMA wait
+        gave up, bit 1 = a staged row pass's bounded copy wait gave up."""
         f = ctypes.c_uint32()
         check(lib().ks_device_status(self.handle, 1 if clear else 0, ctypes.byref(f)))
         return int(f.value)
