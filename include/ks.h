@@ -399,8 +399,9 @@ int ks_mlp_train_step(ks_mlp *mlp, uint32_t batch, const float *d_x, const float
  * as y * t_scale + t_mean.  The model is not owned and must outlive its use;
  * NULL detaches.  Allocates the model's one-row buffers (so later
  * predictions allocate nothing).  KS_EINVAL when the widths do not match.
- * Once attached, ks_switch_batch with KS_AUTO on a batch whose signature is
- * not in the tuning cache runs the model on `stream` (its forward kernel),
+ * Once attached, ks_switch_batch (and each chunk of ks_switch_batch_host)
+ * with KS_AUTO on a batch whose signature is not in the tuning cache runs
+ * the model on `stream` (its forward kernel),
  * reads the prediction back (this synchronises `stream`: make the first
  * such call before any stream capture), stores the predicted schedule in
  * the cache and runs it; ks_autotune remains the exhaustive search whose
@@ -437,7 +438,7 @@ typedef struct {
  * device, key switch (results as ks_switch gives them), copy both outputs
  * back.  Jobs run in equal chunks of at most 8, each chunk one device batch
  * (ks_switch_batch with the same dataflow; KS_AUTO uses the tuned schedule of
- * the chunk's shape).  Copies in, compute and copies out run on three
+ * the chunk's shape, or on a miss the attached cost model's pick).  Copies in, compute and copies out run on three
  * library-owned streams over double-buffered device staging owned by the
  * params object, so chunk c computes while chunk c+1 is copied in and chunk
  * c-1 is copied out, and consecutive calls overlap the same way.  The call's

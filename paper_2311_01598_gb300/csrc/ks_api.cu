@@ -955,15 +955,22 @@ int ks_switch_batch(const ks_params *P, uint32_t n, const ks_job *jobs, ks_dataf
         uint64_t lv = 0;
         for (uint32_t i = 0; i < n; ++i) lv += jobs[i].level_towers;
         const auto sig = tune_signature(n, (uint32_t)(lv / n));
-        auto it = P->tune.find(sig);
-        if (it != P->tune.end()) {
-            sc = it->second;
-        } else if (P->cost_model) {
+        bool hit = false;
+        {
+            std::lock_guard<std::mutex> g(P->tune_mu);
+            auto it = P->tune.find(sig);
+            if (it != P->tune.end()) {
+                sc = it->second;
+                hit = true;
+            }
+        }
+        if (!hit && P->cost_model) {
             // learned schedule: the cost model's pick, cached for the signature
             ks_schedule pick;
             if ((rc = predict_schedule(const_cast<ks_params *>(P), n, jobs, (cudaStream_t)stream, &pick, nullptr)) !=
                 KS_OK)
                 return rc;
+            std::lock_guard<std::mutex> g(P->tune_mu);
             const_cast<ks_params *>(P)->tune[sig] = pick;
             sc = pick;
         }
@@ -1078,10 +1085,25 @@ int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs
             if (dataflow == KS_MP || dataflow == KS_DC) sc.dataflow = dataflow;
             if (dataflow == KS_OC) sc.dataflow = KS_OC;
             if (dataflow == KS_AUTO) {
-                auto it = P->tune.find(tune_signature(m, (uint32_t)(lv / m)));
-                if (it != P->tune.end()) sc = it->second;
+                const auto sig = tune_signature(m, (uint32_t)(lv / m));
+                bool hit = false;
+                {
+                    std::lock_guard<std::mutex> g(P->tune_mu);
+                    auto it = P->tune.find(sig);
+                    if (it != P->tune.end()) {
+                        sc = it->second;
+                        hit = true;
+                    }
+                }
+                // as ks_switch_batch: the cost model's pick on a miss, cached
+                ks_schedule pick;
+                if (!hit && P->cost_model && (rc = predict_schedule(PP, m, dj, cs, &pick, nullptr)) == KS_OK) {
+                    std::lock_guard<std::mutex> g(P->tune_mu);
+                    PP->tune[sig] = pick;
+                    sc = pick;
+                }
             }
-            rc = run_batch(PP, m, dj, sc, cs);
+            if (rc == KS_OK) rc = run_batch(PP, m, dj, sc, cs);
         }
         if (rc == KS_OK) rc = cuda_check(cudaEventRecord(h->comp[s], cs), "record");
         // copy out

@@ -124,8 +124,10 @@ struct ks_params {
     std::map<void *, ks::Workspace *> ws;
     // default schedule (KS_OC / KS_AUTO without a tuned entry)
     ks_schedule sched{KS_OC, 1, 64, 0, -1, -1};
-    // tuning cache: (job-count bucket, mean-level bucket) -> schedule
+    // tuning cache: (job-count bucket, mean-level bucket) -> schedule;
+    // every access holds tune_mu (KS_AUTO calls on several threads share it)
     std::map<std::pair<uint32_t, uint32_t>, ks_schedule> tune;
+    mutable std::mutex tune_mu;
     // learned cost model consulted by KS_AUTO on a tuning-cache miss (not
     // owned), its target normalisation and its one-row input/output buffers
     ks_mlp *cost_model = nullptr;

@@ -254,6 +254,7 @@ int ks_autotune(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps, ks_
     if (rc != KS_OK) return rc;
     uint64_t lv = 0;
     for (uint32_t i = 0; i < n; ++i) lv += jobs[i].level_towers;
+    std::lock_guard<std::mutex> g(P->tune_mu);
     P->tune[tune_signature(n, (uint32_t)(lv / n))] = *best;
     return KS_OK;
 }
@@ -335,6 +336,7 @@ int ks_tune_cache_put(ks_params *P, uint32_t n_jobs, uint32_t mean_level, const 
     if (!P) return fail(KS_EINVAL, "params is NULL");
     int rc = check_schedule(s);
     if (rc) return rc;
+    std::lock_guard<std::mutex> g(P->tune_mu);
     P->tune[tune_signature(n_jobs, mean_level)] = *s;
     return KS_OK;
 }
@@ -342,6 +344,7 @@ int ks_tune_cache_put(ks_params *P, uint32_t n_jobs, uint32_t mean_level, const 
 int ks_tune_cache_get(const ks_params *P, uint32_t n_jobs, uint32_t mean_level, ks_schedule *out)
 {
     if (!P || !out) return fail(KS_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> g(P->tune_mu);
     auto it = P->tune.find(tune_signature(n_jobs, mean_level));
     if (it == P->tune.end()) return fail(KS_EINVAL, "no tuned schedule for this signature");
     *out = it->second;
@@ -355,6 +358,7 @@ int ks_tune_cache_save(const ks_params *P, const char *path)
     if (!f) return fail(KS_EINVAL, std::string("cannot write ") + path);
     f << "# ks tuning cache v2 (sched=dataflow,oc_variant,chunk,order,ntt,bconv)\n";
     const std::string tag = params_tag(P), dev = device_name(P->device);
+    std::lock_guard<std::mutex> g(P->tune_mu);
     for (const auto &kv : P->tune)
         f << dev << " " << tag << " n=" << kv.first.first << " level=" << kv.first.second
           << " sched=" << kv.second.dataflow << "," << kv.second.oc_variant << "," << kv.second.chunk << ","
@@ -380,6 +384,7 @@ int ks_tune_cache_load(ks_params *P, const char *path)
         if (got != 6 && got != 8) continue;
         ks_schedule s{d, v, ch, o, nt, bc};
         if (check_schedule(&s) != KS_OK) continue;
+        std::lock_guard<std::mutex> g(P->tune_mu);
         P->tune[{n, lvl}] = s;
     }
     set_error("");

@@ -188,6 +188,21 @@ def test_learned_schedule_on_the_execution_path():
     for (_, nact, d, o0, o1) in low:
         w0, w1 = C.keyswitch(nact, ks.to_host(d), evk)
         assert np.array_equal(ks.to_host(o0), w0) and np.array_equal(ks.to_host(o1), w1)
+    # the host-buffer path consults the model per chunk the same way
+    torch = need_gpu()
+    hjobs, hwant = [], []
+    for i in range(3):
+        d = inputs.uniform_towers(C.q[:6], C.N, seed=550 + i)
+        hwant.append(C.keyswitch(6, d, evk))
+        hjobs.append((key, 6, torch.from_numpy(d.view(np.int64)).pin_memory(),
+                      torch.zeros((6, C.N), dtype=torch.int64).pin_memory(),
+                      torch.zeros((6, C.N), dtype=torch.int64).pin_memory()))
+    assert P.tune_cache_get(3, 6) is None
+    P.switch_batch_host(hjobs, "AUTO")
+    torch.cuda.synchronize()
+    assert P.tune_cache_get(3, 6) is not None
+    for (_, _, _, h0, h1), (w0, w1) in zip(hjobs, hwant):
+        assert np.array_equal(h0.numpy().view(np.uint64), w0) and np.array_equal(h1.numpy().view(np.uint64), w1)
     P.set_cost_model(None)
 
 
