@@ -438,6 +438,20 @@ def main():
                   "schedule": list(ctuned.as_tuple() + ctuned.impl())}
     del cjobs, ckeys
 
+    # ---- the same step with moduli of the special form k*2^32 + 1 (explicit
+    # primes: the 32 largest below 2^54; the two-pass NTTs' cheaper product)
+    sp_all = ks.special_primes(BITS, NQ + KP)
+    Psp = ks.Params(LOGN, NQ, KP, DNUM, q=sp_all[KP:], p=sp_all[:KP])
+    sp_keys = [Psp.keygen(s, inputs.galois_secret(s, g), seed=inputs.SEED_BASE + 100 + i) for i, g in enumerate(gals)]
+    sp_jobs = [(sp_keys[i], NQ, ks.to_device(inputs.uniform_towers(Psp.q, N, seed=inputs.SEED_BASE + 5000 + i)),
+                ks.empty((NQ, N)), ks.empty((NQ, N))) for i in range(B)]
+    sp_tuned, _ = Psp.autotune(sp_jobs, reps=2, stream=stream)
+    t_sp = timed(lambda: Psp.switch_batch(sp_jobs, "AUTO", stream), args.steps, 2)
+    special = {"value": round(world * B * args.steps / (t_sp / 1e3), 2), "unit": UNIT,
+               "primes": "the 32 largest primes k*2^32+1 below 2^54 (explicit lists; 8 special, 24 Q)",
+               "schedule": list(sp_tuned.as_tuple() + sp_tuned.impl())}
+    del sp_jobs, sp_keys, Psp
+
     # ---- the paper's parameter sets (Table III): 4 ciphertexts a step, own keys
     table3 = table3_sets(stream, timed, world, steps=max(3, args.steps // 2), seed=inputs.SEED_BASE + 9)
 
@@ -555,6 +569,7 @@ def main():
             "table3_sets": table3,
             "hoisted_rotations": hoisted,
             "compressed_keys": compressed,
+            "special_form_moduli": special,
             "schedule": {"tuned": list(tuned.as_tuple() + tuned.impl()),
                          "fields": "dataflow, oc_variant, chunk, order, ntt, bconv",
                          "source": "fixed by --schedule" if args.schedule else "ks_autotune",

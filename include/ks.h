@@ -87,6 +87,16 @@ int ks_params_create(uint32_t logN, uint32_t n_q, uint32_t k_p, uint32_t dnum,
                      ks_params **out);
 void ks_params_destroy(ks_params *params);
 
+/* The count largest primes below 2^bits of the special form k*2^32 + 1
+ * (descending; each is 1 mod 2N for every supported N), for explicit prime
+ * lists (h_q/h_p of ks_params_create).  The paper fixes no primes; the
+ * default rule of ks_params_create (largest primes = 1 mod 2N) does not
+ * produce this form.  When every prime of a parameter set has it, the
+ * two-pass NTT kernels use a cheaper butterfly product (q*E mod 2^64 is
+ * E + ((E mod 2^32)*k mod 2^32)*2^32), with identical results.  Host only
+ * (no device work).  bits in 33..56; KS_EINVAL when fewer than count exist. */
+int ks_special_primes(uint32_t bits, uint32_t count, uint64_t *h_out);
+
 /* Read back the primes (h_q: n_q words, h_p: k_p words; either may be NULL)
  * and the digit geometry. */
 int ks_params_info(const ks_params *params, uint64_t *h_q, uint64_t *h_p,

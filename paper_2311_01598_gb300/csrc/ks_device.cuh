@@ -73,6 +73,22 @@ __device__ __forceinline__ u64 shoup_est(u64 a, u64 w, u64 wp, u64 nq)
     return a * w + e * nq;
 }
 
+// The same product for a modulus of the special form q = q1*2^32 + 1
+// (every prime of such a parameter set; ks_special_primes lists them):
+// E*q mod 2^64 = E + ((E0*q1 mod 2^32) << 32), one 32-bit multiply instead of
+// a 64-bit one, so t = a*w - E*q is the low 64 bits of a*w (one 32x32->64
+// and two 32-bit products) with E and E0*q1 subtracted.  Same range [0, 4q).
+__device__ __forceinline__ u64 shoup_est_sp(u64 a, u64 w, u64 wp, u64 q)
+{
+    const u32 a0 = (u32)a, a1 = (u32)(a >> 32), p0 = (u32)wp, p1 = (u32)(wp >> 32);
+    u64 e = (u64)a1 * p1 + __umulhi(a1, p0);
+    e += __umulhi(a0, p1);
+    const u32 w0 = (u32)w, w1 = (u32)(w >> 32);
+    const u64 lo = (u64)a0 * w0;
+    const u32 hi = (u32)(lo >> 32) + a0 * w1 + a1 * w0 + (u32)e * (0u - (u32)(q >> 32));
+    return ((((u64)hi) << 32) | (u32)lo) - e;
+}
+
 // Forward NTT outputs before the final reduction are below kFwdLazy * q:
 // inputs below 4q grow by less than 4q per stage, 4q + 17*4q = 72q for the
 // 17 stages of N = 2^17, and 76q < 2^63 for q < 2^56.
@@ -81,10 +97,12 @@ constexpr u64 kFwdLazy = 72;
 // Forward Cooley-Tukey butterfly without a per-stage correction of X: with
 // X, Y < B the outputs are below B + 4q (the estimated Shoup product is below
 // 4q for any 64-bit Y), so a transform of at most 17 stages fed with values
-// below 4q ends below kFwdLazy*q.  Consumers reduce with reduce_any.
+// below 4q ends below kFwdLazy*q.  Consumers reduce with reduce_any.  SP:
+// the modulus has the special form (shoup_est_sp).
+template <bool SP = false>
 __device__ __forceinline__ void fwd_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2)
 {
-    const u64 t = shoup_est(Y, w, wp, 0 - q);
+    const u64 t = SP ? shoup_est_sp(Y, w, wp, q) : shoup_est(Y, w, wp, 0 - q);
     Y = X + (q2 + q2) - t;
     X = X + t;
 }
@@ -99,6 +117,7 @@ __device__ __forceinline__ u64 reduce_any(u64 x, u64 q, u64 one_sh)
 // Inverse Harvey butterfly on [0, 4q): X, Y in [0, 4q) -> [0, 4q) (the sum
 // below 8q takes one conditional subtraction of 4q; the difference plus 4q
 // is below 8q and its estimated Shoup product below 4q).
+template <bool SP = false>
 __device__ __forceinline__ void inv_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2)
 {
     const u64 q4 = q2 + q2;
@@ -106,7 +125,7 @@ __device__ __forceinline__ void inv_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u
     s = s >= q4 ? s - q4 : s;
     const u64 d = X - Y + q4;
     X = s;
-    Y = shoup_est(d, w, wp, 0 - q);
+    Y = SP ? shoup_est_sp(d, w, wp, q) : shoup_est(d, w, wp, 0 - q);
 }
 
 // 128-bit accumulator.
@@ -279,7 +298,7 @@ template <> struct ShapeOf<17> { typedef Shape<9, 8> T; };
 // ------------------------------------------------------------------ rounds
 // Round 1 in registers: x[k], k = the high RR bits of the sub-transform index.
 // tw(s, i) returns the (w, w') pair of local stage s, local group i.
-template <int RR, class TW>
+template <int RR, bool SP = false, class TW>
 __device__ __forceinline__ void fwd_round1(u64 (&x)[1 << RR], const TW &tw, u64 q, u64 q2)
 {
 #pragma unroll
@@ -289,14 +308,14 @@ __device__ __forceinline__ void fwd_round1(u64 (&x)[1 << RR], const TW &tw, u64 
         for (int g = 0; g < (1 << s); ++g) {
             const ulonglong2 W = tw(s, g);
 #pragma unroll
-            for (int k = 0; k < half; ++k) fwd_bfly(x[g * 2 * half + k], x[g * 2 * half + k + half], W.x, W.y, q, q2);
+            for (int k = 0; k < half; ++k) fwd_bfly<SP>(x[g * 2 * half + k], x[g * 2 * half + k + half], W.x, W.y, q, q2);
         }
     }
 }
 
 // Round 2 in registers: NG groups of M = 2^(L-RR) values; group gg has
 // global group id gid0 + gg (the high RR bits of the index).
-template <int L, int RR, class TW>
+template <int L, int RR, bool SP = false, class TW>
 __device__ __forceinline__ void fwd_round2(u64 (&x)[1 << RR], int gid0, const TW &tw, u64 q, u64 q2)
 {
     constexpr int M = 1 << (L - RR);
@@ -311,14 +330,14 @@ __device__ __forceinline__ void fwd_round2(u64 (&x)[1 << RR], int gid0, const TW
                 const ulonglong2 W = tw(RR + s2, ((gid0 + gg) << s2) + g2);
 #pragma unroll
                 for (int k = 0; k < half; ++k)
-                    fwd_bfly(x[gg * M + g2 * 2 * half + k], x[gg * M + g2 * 2 * half + k + half], W.x, W.y, q, q2);
+                    fwd_bfly<SP>(x[gg * M + g2 * 2 * half + k], x[gg * M + g2 * 2 * half + k + half], W.x, W.y, q, q2);
             }
         }
     }
 }
 
 // Inverse of fwd_round2: local stages L-1 .. RR on the low bits.
-template <int L, int RR, class TW>
+template <int L, int RR, bool SP = false, class TW>
 __device__ __forceinline__ void inv_round2(u64 (&x)[1 << RR], int gid0, const TW &tw, u64 q, u64 q2)
 {
     constexpr int M = 1 << (L - RR);
@@ -333,14 +352,14 @@ __device__ __forceinline__ void inv_round2(u64 (&x)[1 << RR], int gid0, const TW
                 const ulonglong2 W = tw(RR + s2, ((gid0 + gg) << s2) + g2);
 #pragma unroll
                 for (int k = 0; k < half; ++k)
-                    inv_bfly(x[gg * M + g2 * 2 * half + k], x[gg * M + g2 * 2 * half + k + half], W.x, W.y, q, q2);
+                    inv_bfly<SP>(x[gg * M + g2 * 2 * half + k], x[gg * M + g2 * 2 * half + k + half], W.x, W.y, q, q2);
             }
         }
     }
 }
 
 // Inverse of fwd_round1: local stages RR-1 .. 0 on the high bits.
-template <int RR, class TW>
+template <int RR, bool SP = false, class TW>
 __device__ __forceinline__ void inv_round1(u64 (&x)[1 << RR], const TW &tw, u64 q, u64 q2)
 {
 #pragma unroll
@@ -350,7 +369,7 @@ __device__ __forceinline__ void inv_round1(u64 (&x)[1 << RR], const TW &tw, u64 
         for (int g = 0; g < (1 << s); ++g) {
             const ulonglong2 W = tw(s, g);
 #pragma unroll
-            for (int k = 0; k < half; ++k) inv_bfly(x[g * 2 * half + k], x[g * 2 * half + k + half], W.x, W.y, q, q2);
+            for (int k = 0; k < half; ++k) inv_bfly<SP>(x[g * 2 * half + k], x[g * 2 * half + k + half], W.x, W.y, q, q2);
         }
     }
 }

@@ -61,6 +61,21 @@ bool is_prime_u64(u64 n)
     return true;
 }
 
+// The count largest primes below 2^bits of the form k*2^32 + 1, descending
+// (each is 1 mod 2N for every supported N).
+int gen_special_primes(int bits, int count, std::vector<u64> &out)
+{
+    out.clear();
+    if (bits <= 32) return -1;
+    u64 k = (((u64)1 << bits) - 2) >> 32;
+    while ((int)out.size() < count && k > 0) {
+        const u64 c = (k << 32) + 1;
+        if (is_prime_u64(c)) out.push_back(c);
+        --k;
+    }
+    return (int)out.size() == count ? 0 : -1;
+}
+
 int gen_primes(int logN, int bits, int count, std::vector<u64> &out)
 {
     out.clear();
@@ -332,6 +347,9 @@ int build_tables(ks_params *P)
     T.dn_tc = P->bconv_tensor ? P->d_dn_tc : nullptr;
     T.ntt_cluster = P->ntt_cluster;
     T.row_stage = P->row_stage;
+    T.spq = 1;
+    for (u64 q : P->q) T.spq = T.spq && (q & 0xFFFFFFFFull) == 1;
+    for (u64 p : P->p) T.spq = T.spq && (p & 0xFFFFFFFFull) == 1;
     T.logN = P->logN;
     T.nq = P->nq;
     T.kp = P->kp;
@@ -356,3 +374,14 @@ void free_tables(ks_params *P)
 }
 
 }  // namespace ks
+
+extern "C" int ks_special_primes(uint32_t bits, uint32_t count, uint64_t *h_out)
+{
+    if (!h_out || count == 0) return ks::fail(KS_EINVAL, "ks_special_primes: NULL output or count 0");
+    if (bits < 33 || bits > (uint32_t)ks::kMaxPrimeBits) return ks::fail(KS_EINVAL, "ks_special_primes: bits must be in 33..56");
+    std::vector<ks::u64> v;
+    if (ks::gen_special_primes((int)bits, (int)count, v) != 0)
+        return ks::fail(KS_EINVAL, "ks_special_primes: not enough primes of the form k*2^32 + 1 below 2^bits");
+    for (uint32_t i = 0; i < count; ++i) h_out[i] = v[i];
+    return KS_OK;
+}

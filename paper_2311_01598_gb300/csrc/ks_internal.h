@@ -78,6 +78,7 @@ struct Tables {
     const uint4 *dn_tc;
     int ntt_cluster;  // host side: NTTs as one cluster launch where supported
     int row_stage;    // host side: forward row passes staged by bulk copies (k_fwd_row_st)
+    int spq;          // every modulus is q1*2^32 + 1: two-pass NTTs use shoup_est_sp
     int logN;
     int nq, kp, alpha, ndig;
 };
@@ -210,6 +211,7 @@ int fail(int code, const std::string &msg);
 // Host number theory (ks_host.cpp).
 bool is_prime_u64(u64 n);
 int gen_primes(int logN, int bits, int count, std::vector<u64> &out);
+int gen_special_primes(int bits, int count, std::vector<u64> &out);
 u64 find_psi(u64 q, int logN);
 u64 mulmod_h(u64 a, u64 b, u64 m);
 u64 powmod_h(u64 b, u64 e, u64 m);

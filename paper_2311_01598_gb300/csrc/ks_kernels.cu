@@ -9,8 +9,9 @@
 namespace ks {
 
 // ------------------------------------------------------------------ NTT passes
-// Forward column pass (stages 0..LA-1).  grid (2^LB/COLS, limbs).
-template <class S>
+// Forward column pass (stages 0..LA-1).  grid (2^LB/COLS, limbs).  SP: every
+// modulus has the special form q1*2^32 + 1 (cheaper butterfly product).
+template <class S, bool SP>
 __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_fwd_col(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -29,7 +30,7 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_fwd_col(Tables T, L
 #pragma unroll
     for (int k = 0; k < S::REGA; ++k) x[k] = L.src[((size_t)(k * S::TA + tau) << S::LB) + c];
     __syncthreads();
-    fwd_round1<S::RA>(x, TwSmem{tws}, q, q2);
+    fwd_round1<S::RA, SP>(x, TwSmem{tws}, q, q2);
 #pragma unroll
     for (int k = 0; k < S::REGA; ++k) sm[(k * S::TA + tau) * S::COLS + cc] = x[k];
     __syncthreads();
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_fwd_col(Tables T, L
     for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
         for (int k2 = 0; k2 < M; ++k2) x[gg * M + k2] = sm[((tau * NG + gg) * M + k2) * S::COLS + cc];
-    fwd_round2<S::LA, S::RA>(x, tau * NG, TwSmem{tws}, q, q2);
+    fwd_round2<S::LA, S::RA, SP>(x, tau * NG, TwSmem{tws}, q, q2);
 #pragma unroll
     for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_fwd_col(Tables T, L
 // second shared-memory exchange returns the values to the first-round
 // layout; measured faster than storing each thread's consecutive values
 // with strided vector stores).
-template <class S, bool CANON>
+template <class S, bool CANON, bool SP>
 __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_fwd_row(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_fwd_row(Tables T, L
     stage_row_round1<S>(tsh, twt, G, tau);
     static_assert(S::TB <= 32, "a row's threads share one warp");
     __syncwarp();
-    row_fwd_core<S>(x, TwStaged<S>{tsh, twt, G}, sm + rr * S::ROWPAD, tau, q, q2);
+    row_fwd_core<S, SP>(x, TwStaged<S>{tsh, twt, G}, sm + rr * S::ROWPAD, tau, q, q2);
     const u64 one_sh = CANON ? mc.one_sh : 0;
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = CANON ? reduce_any(x[k], q, one_sh) : x[k];
@@ -221,7 +222,7 @@ int ntt_error_flag(bool clear)
 
 // Inverse row pass (stages logN-1..LA), first half of the iNTT.  Input below
 // 4q; output below 4q.
-template <class S>
+template <class S, bool SP>
 __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_inv_row(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -239,14 +240,14 @@ __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_inv_row(Tables T, L
     u64 x[S::REGB];
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) x[k] = gin[k * S::TB + tau];
-    row_inv_core<S>(x, tw, sm + rr * S::ROWPAD, tau, q, q2);
+    row_inv_core<S, SP>(x, tw, sm + rr * S::ROWPAD, tau, q, q2);
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = x[k];
 }
 
 // Inverse column pass (stages LA-1..0), second half of the iNTT, then the
 // scale (SC: 0 none, 1 the job's per-entry scale, 2 N^-1); output canonical.
-template <class S, int SC>
+template <class S, int SC, bool SP>
 __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_inv_col(Tables T, LimbMaps ms)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_inv_col(Tables T, L
 #pragma unroll
         for (int k2 = 0; k2 < M; ++k2) x[gg * M + k2] = L.src[((size_t)((tau * NG + gg) * M + k2) << S::LB) + c];
     __syncthreads();
-    inv_round2<S::LA, S::RA>(x, tau * NG, TwSmem{tws}, q, q2);
+    inv_round2<S::LA, S::RA, SP>(x, tau * NG, TwSmem{tws}, q, q2);
 #pragma unroll
     for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
@@ -277,7 +278,7 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_inv_col(Tables T, L
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < S::REGA; ++k) x[k] = sm[(k * S::TA + tau) * S::COLS + cc];
-    inv_round1<S::RA>(x, TwSmem{tws}, q, q2);
+    inv_round1<S::RA, SP>(x, TwSmem{tws}, q, q2);
     u64 w = 0, wp = 0;
     if (SC == 1) {
         const ulonglong2 f = L.scale[L.b];
@@ -295,18 +296,25 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_inv_col(Tables T, L
     }
 }
 
+template <class S, bool SP>
+static void set_smem_attrs_sp()
+{
+    cudaFuncSetAttribute(k_fwd_col<S, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+    cudaFuncSetAttribute(k_inv_col<S, 0, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+    cudaFuncSetAttribute(k_inv_col<S, 1, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+    cudaFuncSetAttribute(k_inv_col<S, 2, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
+    cudaFuncSetAttribute(k_fwd_row<S, true, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
+    cudaFuncSetAttribute(k_fwd_row<S, false, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
+    cudaFuncSetAttribute(k_inv_row<S, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+}
+
 template <class S>
 static void set_smem_attrs()
 {
     static std::atomic<uint64_t> done{0};  // per instantiation, per device
     once_per_device(done, [] {
-        cudaFuncSetAttribute(k_fwd_col<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-        cudaFuncSetAttribute(k_inv_col<S, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-        cudaFuncSetAttribute(k_inv_col<S, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-        cudaFuncSetAttribute(k_inv_col<S, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
-        cudaFuncSetAttribute(k_fwd_row<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
-        cudaFuncSetAttribute(k_fwd_row<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
-        cudaFuncSetAttribute(k_inv_row<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+        set_smem_attrs_sp<S, false>();
+        set_smem_attrs_sp<S, true>();
     });
 }
 
@@ -336,8 +344,11 @@ template <class S>
 static void fwd_col_S(const Tables &T, const LimbMaps &m, cudaStream_t st)
 {
     set_smem_attrs<S>();
-    KS_LAUNCH(st, "ntt_fwd_col",
-              k_fwd_col<S><<<limb_grid((1 << S::LB) / S::COLS, m.pre[m.n]), S::THREADS_A, S::SMEM_A, st>>>(T, m));
+    const dim3 ga = limb_grid((1 << S::LB) / S::COLS, m.pre[m.n]);
+    if (T.spq)
+        KS_LAUNCH(st, "ntt_fwd_col", k_fwd_col<S, true><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+    else
+        KS_LAUNCH(st, "ntt_fwd_col", k_fwd_col<S, false><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
 }
 
 // Persistent grid of the staged row pass: resident CTAs per SM x SMs, at
@@ -388,18 +399,25 @@ static void fwd_row_S(const Tables &T, const LimbMaps &m, bool canonical, cudaSt
         return;
     }
     const dim3 gb = limb_grid((1 << S::LA) / S::ROWS, m.pre[m.n]);
-    if (canonical)
-        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
+    if (canonical && T.spq)
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true, true><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
+    else if (canonical)
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, true, false><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
+    else if (T.spq)
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, false, true><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
     else
-        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, false><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
+        KS_LAUNCH(st, "ntt_fwd_row", k_fwd_row<S, false, false><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
 }
 
 template <class S>
 static void inv_row_S(const Tables &T, const LimbMaps &m, cudaStream_t st)
 {
     set_smem_attrs<S>();
-    KS_LAUNCH(st, "ntt_inv_row",
-              k_inv_row<S><<<limb_grid((1 << S::LA) / S::ROWS, m.pre[m.n]), S::THREADS_B, S::SMEM_B, st>>>(T, m));
+    const dim3 gb = limb_grid((1 << S::LA) / S::ROWS, m.pre[m.n]);
+    if (T.spq)
+        KS_LAUNCH(st, "ntt_inv_row", k_inv_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
+    else
+        KS_LAUNCH(st, "ntt_inv_row", k_inv_row<S, false><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
 }
 
 template <class S>
@@ -407,12 +425,22 @@ static void inv_col_S(const Tables &T, const LimbMaps &m, bool ninv, cudaStream_
 {
     set_smem_attrs<S>();
     const dim3 ga = limb_grid((1 << S::LB) / S::COLS, m.pre[m.n]);
-    if (any_scale(m))
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
-    else if (ninv)
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 2><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
-    else
-        KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 0><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+    const int sc = any_scale(m) ? 1 : ninv ? 2 : 0;
+    if (T.spq) {
+        if (sc == 1)
+            KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1, true><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+        else if (sc == 2)
+            KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 2, true><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+        else
+            KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 0, true><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+    } else {
+        if (sc == 1)
+            KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 1, false><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+        else if (sc == 2)
+            KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 2, false><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+        else
+            KS_LAUNCH(st, "ntt_inv_col", k_inv_col<S, 0, false><<<ga, S::THREADS_A, S::SMEM_A, st>>>(T, m));
+    }
 }
 
 #define KS_DISPATCH_LOGN(logN, FN, ...)                                                                   \

@@ -75,11 +75,11 @@ struct TwStaged {
 // leaves in the first-round layout (x[k] is element k*TB + tau of the row),
 // srow is the row's padded shared-memory buffer.  Contains block barriers:
 // every thread of the block must call it.
-template <class S, class TW>
+template <class S, bool SP = false, class TW>
 __device__ __forceinline__ void row_fwd_core(u64 (&x)[S::REGB], const TW &tw, u64 *srow, int tau, u64 q, u64 q2)
 {
     constexpr int M = S::MB, NG = S::REGB / S::MB;
-    fwd_round1<S::RB>(x, tw, q, q2);
+    fwd_round1<S::RB, SP>(x, tw, q, q2);
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) srow[rpad<S>(k * S::TB + tau)] = x[k];
     __syncthreads();
@@ -87,7 +87,7 @@ __device__ __forceinline__ void row_fwd_core(u64 (&x)[S::REGB], const TW &tw, u6
     for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
         for (int k2 = 0; k2 < M; ++k2) x[gg * M + k2] = srow[rpad<S>((tau * NG + gg) * M + k2)];
-    fwd_round2<S::LB, S::RB>(x, tau * NG, tw, q, q2);
+    fwd_round2<S::LB, S::RB, SP>(x, tau * NG, tw, q, q2);
     __syncthreads();
 #pragma unroll
     for (int gg = 0; gg < NG; ++gg)
@@ -100,7 +100,7 @@ __device__ __forceinline__ void row_fwd_core(u64 (&x)[S::REGB], const TW &tw, u6
 }
 
 // Row pass of the inverse NTT (stages logN-1 .. LA), same layout contract.
-template <class S, class TW>
+template <class S, bool SP = false, class TW>
 __device__ __forceinline__ void row_inv_core(u64 (&x)[S::REGB], const TW &tw, u64 *srow, int tau, u64 q, u64 q2)
 {
     constexpr int M = S::MB, NG = S::REGB / S::MB;
@@ -111,7 +111,7 @@ __device__ __forceinline__ void row_inv_core(u64 (&x)[S::REGB], const TW &tw, u6
     for (int gg = 0; gg < NG; ++gg)
 #pragma unroll
         for (int k2 = 0; k2 < M; ++k2) x[gg * M + k2] = srow[rpad<S>((tau * NG + gg) * M + k2)];
-    inv_round2<S::LB, S::RB>(x, tau * NG, tw, q, q2);
+    inv_round2<S::LB, S::RB, SP>(x, tau * NG, tw, q, q2);
     __syncthreads();
 #pragma unroll
     for (int gg = 0; gg < NG; ++gg)
@@ -121,7 +121,7 @@ __device__ __forceinline__ void row_inv_core(u64 (&x)[S::REGB], const TW &tw, u6
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) x[k] = srow[rpad<S>(k * S::TB + tau)];
     __syncthreads();
-    inv_round1<S::RB>(x, tw, q, q2);
+    inv_round1<S::RB, SP>(x, tw, q, q2);
 }
 
 }  // namespace ks

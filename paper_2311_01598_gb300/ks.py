@@ -137,6 +137,8 @@ def lib():
         L.ks_tune_cache_load.argtypes = [vp, ctypes.c_char_p]
         L.ks_key_synthetic.argtypes = [vp, u64, vp, pvp]
         L.ks_params_set_cost_model.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float]
+        L.ks_special_primes.argtypes = [u32, u32, ctypes.POINTER(ctypes.c_uint64)]
+        L.ks_special_primes.restype = ci
         L.ks_key_shard.argtypes = [vp, ctypes.POINTER(Shard), vp, pvp]
         L.ks_key_shard.restype = ci
         L.ks_shard_scratch_words.argtypes = [vp, ctypes.POINTER(Shard), u32]
@@ -731,6 +733,15 @@ def profile_collect(max_names: int = 64) -> dict:
 
 
 # -- torch helpers (device memory only) ------------------------------------------
+def special_primes(bits: int, count: int) -> list:
+    """ks_special_primes: the count largest primes k*2^32 + 1 below 2^bits,
+    descending (for explicit prime lists; the two-pass NTTs use a cheaper
+    butterfly product when every prime of a parameter set has this form)."""
+    out = (ctypes.c_uint64 * count)()
+    check(lib().ks_special_primes(bits, count, out))
+    return [int(x) for x in out]
+
+
 def to_device(a: np.ndarray, device="cuda"):
     """uint64 numpy array -> int64 torch tensor on the GPU (same bits)."""
     import torch

@@ -215,3 +215,35 @@ def test_moddown_extreme_56bit(kind):
                 P.moddown(nact, ks.to_device(cp[x]), out)
                 assert np.array_equal(ks.to_host(out), want), (kind, nact, x, tensor)
     P.set_bconv_tensor(True)
+
+
+@pytest.mark.parametrize("logN,nq,kp,dnum,levels", [(12, 6, 2, 3, [6, 2]), (16, 24, 8, 3, [24, 11]),
+                                                     (17, 20, 6, 2, [20, 7])])
+def test_special_form_primes(logN, nq, kp, dnum, levels):
+    """Explicit primes of the form k*2^32 + 1 (ks_special_primes): the
+    two-pass NTT kernels take the cheaper butterfly product; forward and
+    inverse NTTs and every key-switch path equal the oracle's on the same
+    primes, both base-conversion engines."""
+    need_gpu()
+    ks = built_lib()
+    allp = ks.special_primes(54, nq + kp)
+    p, q = allp[:kp], allp[kp:]
+    P = ks.Params(logN, nq, kp, dnum, q=q, p=p)
+    C = orc.Ctx(logN, nq, kp, dnum, q=q, p=p)
+    assert P.q == C.q == q and P.p == C.p == p
+    towers = C.q + C.p
+    psis = C.psi_q + C.psi_p
+    a = inputs.uniform_towers(towers[:6], C.N, seed=900 + logN)
+    t = ks.to_device(a)
+    P.ntt(0, t, inverse=False)
+    got = ks.to_host(t)
+    for i in range(6):
+        assert np.array_equal(got[i], orc.ntt(a[i], logN, towers[i], psis[i])), i
+    P.ntt(0, t, inverse=True)
+    assert np.array_equal(ks.to_host(t), a)
+    evk = random_evk(C, seed=910)
+    key = P.upload_key(evk)
+    for nact in levels:
+        d = inputs.uniform_towers(C.q[:nact], C.N, seed=920 + nact)
+        w0, w1 = C.keyswitch(nact, d, evk)
+        check_all_paths(ks, P, C, key, nact, d, w0, w1, engines=(True, False), what="special-form")
