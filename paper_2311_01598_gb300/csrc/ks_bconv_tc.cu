@@ -1,25 +1,28 @@
 // ks_bconv_tc.cu -- fast base conversion (ModUp P2, ModDown P2) on the
 // 5th-generation tensor cores (tcgen05, accumulators in tensor memory).
 //
-// The conversion z_t = sum_i y_i c_{i,t} is a product of a [coefficients x
-// sources] matrix by a [sources x targets] matrix of constants below 2^56.
-// Exactness with f16 operands: y_i (canonical, < 2^56) is cut into 7 bytes
-// y_{i,a} and each constant into 7 bytes c_{i,t,b}; then
-//   sum_i y_i c_{i,t} = sum_{s=0}^{12} 2^(8s) P_{t,s},
-//   P_{t,s} = sum_i sum_{a+b=s} y_{i,a} c_{i,t,b},
-// and every P_{t,s} (at most 9 sources x 7 byte pairs x 255^2 < 2^22) is an
-// exact integer in the fp32 accumulator.  One MMA of M=128 coefficients,
-// K = 7*(sources) padded to 64, N = 16 per target (13 shifts used) computes
-// all P_{t,s} of 16 targets: the A tile holds the byte slices of y (built by
-// the CTA from the source limbs), the B tile the per-target slabs
-// B[s][7i+a] = c_{i,t,s-a} (precomputed on the host, 2 KB each).  The
-// epilogue reads P_{t,s} from tensor memory, recombines the 128-bit sum and
-// reduces it with one Montgomery reduction (constants carry 2^64), giving the
-// same lazy [0, 2r) output as the CUDA-core kernels.
+// The conversion z_t = sum_i y_i c_{i,t} mod r_t is a product of a
+// [coefficients x sources] matrix by a [sources x targets] matrix of
+// constants below 2^56.  Exactness with f16 operands: y_i (canonical, < 2^56)
+// is cut into 7 bytes y_{i,a}, so y_i c_{i,t} = sum_a y_{i,a} 2^(8a) c_{i,t}.
+// The shift of byte a is folded into the constant, c'_{i,a,t} = 2^(8a)
+// c_{i,t} mod r_t, and each c' is cut into 7 bytes c'_{i,a,t,b}; then
+//   z_t == sum_{b=0}^{6} 2^(8b) P_{t,b}  (mod r_t),
+//   P_{t,b} = sum_i sum_a y_{i,a} c'_{i,a,t,b},
+// and every P_{t,b} (at most 9 sources x 7 bytes x 255^2 < 2^22) is an exact
+// integer in the fp32 accumulator.  One MMA of M=128 coefficients,
+// K = 7*(sources) padded to 64, N = 8 per target (7 byte rows used) computes
+// all P_{t,b} of up to 32 targets: the A tile holds the byte slices of y
+// (built by the CTA from the source limbs), the B tile the per-target slabs
+// B[b][7i+a] = c'_{i,a,t,b} (precomputed on the host, 1 KB each).  The
+// epilogue reads the 7 sums from tensor memory, recombines them into a sum
+// below 2^70 and reduces it with one Montgomery reduction (constants carry
+// 2^64), giving a lazy [0, 2r) output like the CUDA-core kernels (the same
+// residue; the representative may differ).
 //
 // Operand layout: the canonical K-major layout without swizzle: 8x16-byte
 // core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row
-// groups 1024 bytes apart (SBO); B slabs of 16 rows concatenate.
+// groups 1024 bytes apart (SBO); B slabs of 8 rows concatenate.
 #include <cstdio>
 
 #include "ks_device.cuh"
@@ -31,10 +34,11 @@ namespace {
 
 constexpr int TC_M = 128;            // coefficients per MMA tile
 constexpr int TC_K = 64;             // padded K (7 x up to 9 sources)
-constexpr int TC_TB = 16;            // targets per CTA
+constexpr int TC_TB = 32;            // targets per MMA (8 accumulator columns each)
 constexpr uint32_t TC_LBO = 128;
 constexpr uint32_t TC_SBO = (TC_K / 8) * 128;
-constexpr int TC_SLAB = 16 * TC_K * 2;  // bytes of one target slab
+constexpr int TC_SLAB = 8 * TC_K * 2;  // bytes of one target slab
+static_assert(TC_SLAB == 2 * kTcSlabHalves, "slab size");
 constexpr int TC_WAIT_LIMIT = 1 << 24;  // mbarrier polls before giving up
 
 __device__ int g_tc_error;  // set when an MMA completion wait gives up
@@ -73,26 +77,21 @@ __device__ __forceinline__ uint32_t f16x2_bytes(uint32_t x, uint32_t y, uint32_t
     return r;
 }
 
-// 128-bit sum of the 13 shifted partial sums of one target, Montgomery-reduced.
-// v[s] are the raw accumulator bits 0x4B000000 + P_s (bias column); the bias
-// is removed once per 64-bit group.
-__device__ __forceinline__ u64 tc_reduce(const uint32_t (&v)[16], u64 q, u64 mont)
+// Sum of the 7 shifted partial sums of one target, Montgomery-reduced.
+// v[b] are the raw accumulator bits 0x4B000000 + P_b (bias column); the bias
+// is removed once per group.  S = a0 + a1*2^40 < 2^70.
+__device__ __forceinline__ u64 tc_reduce(const uint32_t *v, u64 q, u64 mont)
 {
     constexpr u64 B = 0x4B000000ull;
-    u64 a0 = 0, a1 = 0, a2 = 0;
+    u64 a0 = 0, a1 = 0;
 #pragma unroll
-    for (int s = 0; s < 5; ++s) a0 += (u64)v[s] << (8 * s);
-#pragma unroll
-    for (int s = 5; s < 10; ++s) a1 += (u64)v[s] << (8 * (s - 5));
-#pragma unroll
-    for (int s = 10; s < 13; ++s) a2 += (u64)v[s] << (8 * (s - 10));
+    for (int b = 0; b < 5; ++b) a0 += (u64)v[b] << (8 * b);
+    a1 = (u64)v[5] + ((u64)v[6] << 8);
     a0 -= B * 0x0101010101ull;  // B * (1 + 2^8 + ... + 2^32)
-    a1 -= B * 0x0101010101ull;
-    a2 -= B * 0x010101ull;
-    // S = a0 + a1*2^40 + a2*2^80
+    a1 -= B * 0x0101ull;
     const u64 t1 = a1 << 40;
     const u64 lo = a0 + t1;
-    const u64 hi = (a1 >> 24) + (a2 << 16) + (lo < t1 ? 1 : 0);
+    const u64 hi = (a1 >> 24) + (lo < t1 ? 1 : 0);
     return redc(U128{lo, hi}, q, mont);
 }
 
@@ -350,12 +349,19 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
                 break;
             }
             if (restage) {
+                // G slabs, and a zero slab after an odd G (the MMA's N is a
+                // multiple of 16 columns: two targets)
                 constexpr int W = TC_SLAB / 16;
-                for (int idx = tid; idx < it.G * W; idx += TC_PROD) {
+                const int Gp = (it.G + 1) & ~1;
+                for (int idx = tid; idx < Gp * W; idx += TC_PROD) {
                     const int g = idx / W, w = idx % W;
-                    int t, tf, slab;
-                    tc_target<MODE>(T, it, g, t, tf, slab);
-                    reinterpret_cast<uint4 *>(sb)[idx] = slabs[(size_t)slab * W + w];
+                    uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                    if (g < it.G) {
+                        int t, tf, slab;
+                        tc_target<MODE>(T, it, g, t, tf, slab);
+                        val = slabs[(size_t)slab * W + w];
+                    }
+                    reinterpret_cast<uint4 *>(sb)[idx] = val;
                 }
                 cur_r = cur.r;
             }
@@ -378,7 +384,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
             producers_sync();
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t idesc = tc_idesc(16 * it.G);
+                const uint32_t idesc = tc_idesc(8 * ((it.G + 1) & ~1));
                 const uint32_t dcol = tbase + (uint32_t)(buf * 256);
 #pragma unroll
                 for (int kk = 0; kk < TC_K / 16; ++kk) {
@@ -419,18 +425,23 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int G = s_G[buf];
-            // targets strided over the four warps of a lane quarter, two
-            // tensor-memory loads in flight per wait
-            for (int g = part; g < G; g += 8) {
-                const bool two = g + 4 < G;
+            const int G = s_G[buf], NP = (G + 1) / 2;
+            // target pairs (2p, 2p+1: 16 columns) strided over the four warps
+            // of a lane quarter, two tensor-memory loads in flight per wait
+            for (int p = part; p < NP; p += 8) {
+                const bool two = p + 4 < NP;
                 uint32_t v[16], w[16];
-                const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + 16 * g);
+                const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256 + 16 * p);
                 tmem_ld16(taddr, v);
                 if (two) tmem_ld16(taddr + 64, w);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int g = 2 * p;
                 s_dst[buf][g][row] = tc_reduce(v, s_q[buf][g], s_mont[buf][g]);
-                if (two) s_dst[buf][g + 4][row] = tc_reduce(w, s_q[buf][g + 4], s_mont[buf][g + 4]);
+                if (g + 1 < G) s_dst[buf][g + 1][row] = tc_reduce(v + 8, s_q[buf][g + 1], s_mont[buf][g + 1]);
+                if (two) {
+                    s_dst[buf][g + 8][row] = tc_reduce(w, s_q[buf][g + 8], s_mont[buf][g + 8]);
+                    if (g + 9 < G) s_dst[buf][g + 9][row] = tc_reduce(w + 8, s_q[buf][g + 9], s_mont[buf][g + 9]);
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
             __syncwarp();
@@ -532,15 +543,16 @@ int tc_error_flag(bool clear)
     return v;
 }
 
-// Host: the B slab of one target: rows s = 0..15 (shift; 13..15 zero),
-// columns k = 7i + a (source i, byte a of y): byte s - a of constant c_i.
-void tc_slab(const std::vector<u64> &c, uint16_t *slab)
+// Host: the B slab of one target of modulus r: rows b = 0..7 (byte of the
+// folded constant; row 7 zero), columns k = 7i + a (source i, byte a of y):
+// byte b of c_i * 2^(8a) mod r.
+void tc_slab(const std::vector<u64> &c, u64 r, uint16_t *slab)
 {
-    for (int r = 0; r < 16; ++r)
-        for (int k = 0; k < TC_K; ++k) {
-            const int i = k / 7, a = k % 7, b = r - a;
-            uint32_t byte = 0;
-            if (i < (int)c.size() && b >= 0 && b <= 6) byte = (uint32_t)((c[i] >> (8 * b)) & 0xFF);
+    for (int k = 0; k < TC_K; ++k) {
+        const int i = k / 7, a = k % 7;
+        const u64 cf = i < (int)c.size() ? mulmod_h(c[i] % r, powmod_h(2, 8 * (u64)a, r), r) : 0;
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t byte = b < 7 ? (uint32_t)((cf >> (8 * b)) & 0xFF) : 0u;
             // f16 of an integer below 256
             uint16_t bits = 0;
             if (byte) {
@@ -548,12 +560,13 @@ void tc_slab(const std::vector<u64> &c, uint16_t *slab)
                 uint32_t mant = (byte << (10 - e)) & 0x3FF;        // 10 fraction bits
                 bits = (uint16_t)(((15 + e) << 10) | mant);
             }
-            slab[tc_off(r, k) / 2] = bits;
+            slab[tc_off(b, k) / 2] = bits;
         }
-    // column 63 (never a slice: 9 sources use 0..62) holds 4096 in the 13 used
-    // shift rows; times the A tile's 2048 there it adds 2^23, so the fp32
+    }
+    // column 63 (never a slice: 9 sources use 0..62) holds 4096 in the 7 used
+    // byte rows; times the A tile's 2048 there it adds 2^23, so the fp32
     // accumulator of P (< 2^22) reads 2^23 + P: its bits are 0x4B000000 + P
-    for (int r = 0; r < 13; ++r) slab[tc_off(r, 63) / 2] = (uint16_t)((15 + 12) << 10);
+    for (int b = 0; b < 7; ++b) slab[tc_off(b, 63) / 2] = (uint16_t)((15 + 12) << 10);
 }
 
 }  // namespace ks

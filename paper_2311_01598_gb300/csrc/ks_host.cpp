@@ -253,7 +253,7 @@ int build_tables(ks_params *P)
     // full tower t) for ModUp and per Q tower for ModDown (<= 9 sources)
     std::vector<uint16_t> up_tc, dn_tc;
     std::vector<int> up_tc_lvl((size_t)P->nq * P->ndig, 0);
-    constexpr size_t SLAB = 16 * 64;
+    constexpr size_t SLAB = kTcSlabHalves;
     if (A <= 9) {
         std::vector<int> off((size_t)P->ndig * (A + 1), -1);
         for (int j = 0; j < P->ndig; ++j) {
@@ -271,7 +271,7 @@ int build_tables(ks_params *P)
                         c[i] = to_mont(hat, r);
                     }
                     up_tc.resize(up_tc.size() + SLAB);
-                    tc_slab(c, up_tc.data() + up_tc.size() - SLAB);
+                    tc_slab(c, r, up_tc.data() + up_tc.size() - SLAB);
                 }
             }
         }
@@ -284,7 +284,7 @@ int build_tables(ks_params *P)
         for (int i = 0; i < P->nq; ++i) {
             std::vector<u64> c(P->kp);
             for (int k = 0; k < P->kp; ++k) c[k] = to_mont(invmod_h(P->p[k] % P->q[i], P->q[i]), P->q[i]);
-            tc_slab(c, dn_tc.data() + (size_t)i * SLAB);
+            tc_slab(c, P->q[i], dn_tc.data() + (size_t)i * SLAB);
         }
     }
 
