@@ -448,7 +448,8 @@ typedef struct {
  * device, key switch (results as ks_switch gives them), copy both outputs
  * back.  Jobs run in equal chunks of at most 8, each chunk one device batch
  * (ks_switch_batch with the same dataflow; KS_AUTO uses the tuned schedule of
- * the chunk's shape, or on a miss the attached cost model's pick).  Copies in, compute and copies out run on three
+ * the chunk's shape, else the one tuned for the whole call's shape, else the
+ * attached cost model's pick).  Copies in, compute and copies out run on three
  * library-owned streams over double-buffered device staging owned by the
  * params object, so chunk c computes while chunk c+1 is copied in and chunk
  * c-1 is copied out, and consecutive calls overlap the same way.  The call's

@@ -1055,6 +1055,9 @@ int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs
     const size_t N = P->N;
     const size_t slot_words = (size_t)P->nq * N;
     const std::vector<uint32_t> chunks = host_chunks(n);
+    uint64_t call_lv = 0;
+    for (uint32_t i = 0; i < n; ++i) call_lv += jobs[i].level_towers;
+    const uint32_t call_mean = n ? (uint32_t)(call_lv / n) : 0;
     uint32_t i0 = 0;
     for (size_t c = 0; c < chunks.size(); i0 += chunks[c], ++c) {
         const int s = (int)((h->next + c) & 1);
@@ -1088,8 +1091,11 @@ int ks_switch_batch_host(const ks_params *P, uint32_t n, const ks_host_job *jobs
                 const auto sig = tune_signature(m, (uint32_t)(lv / m));
                 bool hit = false;
                 {
+                    // the chunk's shape, else the whole call's (tuned on the
+                    // device batch these jobs form)
                     std::lock_guard<std::mutex> g(P->tune_mu);
                     auto it = P->tune.find(sig);
+                    if (it == P->tune.end()) it = P->tune.find(tune_signature(n, call_mean));
                     if (it != P->tune.end()) {
                         sc = it->second;
                         hit = true;

@@ -206,6 +206,45 @@ def test_learned_schedule_on_the_execution_path():
     P.set_cost_model(None)
 
 
+def test_host_auto_takes_the_whole_calls_schedule():
+    """ks_switch_batch_host with KS_AUTO: chunks whose own shape has no tuned
+    entry run the schedule tuned for the whole call (here MP, told apart from
+    the default schedule by its launch count), with the oracle's results."""
+    torch = need_gpu()
+    ks = built_lib()
+    P, C = pair(12, 5, 2, 2)
+    s = inputs.ternary_secret(C.N, 41)
+    evk = C.keygen(s, inputs.galois_secret(s, 5), seed=6)
+    key = P.upload_key(evk)
+    n = 10  # two chunks of 5
+    hjobs, djobs, want = [], [], []
+    for i in range(n):
+        d = inputs.uniform_towers(C.q, C.N, seed=700 + i)
+        want.append(C.keyswitch(5, d, evk))
+        hjobs.append((key, 5, torch.from_numpy(d.view(np.int64)).pin_memory(),
+                      torch.zeros((5, C.N), dtype=torch.int64).pin_memory(),
+                      torch.zeros((5, C.N), dtype=torch.int64).pin_memory()))
+        djobs.append((key, 5, ks.to_device(d), ks.empty((5, C.N)), ks.empty((5, C.N))))
+    mp = ks.Schedule(ks.MP, 1, 64, 0)
+    P.tune_cache_put(n, 5, mp)
+    assert P.tune_cache_get(5, 5) is None
+
+    def launches(fn):
+        torch.cuda.synchronize()
+        l0 = ks.kernel_launches()
+        fn()
+        torch.cuda.synchronize()
+        return ks.kernel_launches() - l0
+
+    per_chunk = {name: launches(lambda sc=sc: P.switch_batch_sched(djobs[:5], sc))
+                 for name, sc in (("mp", mp), ("default", P.default_schedule()))}
+    assert per_chunk["mp"] != per_chunk["default"]
+    assert launches(lambda: P.switch_batch_host(hjobs, "AUTO")) == 2 * per_chunk["mp"]
+    assert P.tune_cache_get(5, 5) is None
+    for (_, _, _, h0, h1), (w0, w1) in zip(hjobs, want):
+        assert np.array_equal(h0.numpy().view(np.uint64), w0) and np.array_equal(h1.numpy().view(np.uint64), w1)
+
+
 def test_cost_model_regret_on_gb300_dataset():
     """Held-out regret of the learned schedule <= 5% of the exhaustive
     autotuner's best, and less total time than the fixed default schedule."""
