@@ -234,13 +234,19 @@ __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_inv_row(Tables T, L
     const u64 q = T.modc[L.tf].q, q2 = 2 * q;
     const int rr = threadIdx.x / S::TB, tau = threadIdx.x % S::TB;
     const int h = blockIdx.x * S::ROWS + rr;
-    const TwRow tw{T.itw + ((size_t)L.tf << S::LOGN), (1 << S::LA) + h};
+    const int G = (1 << S::LA) + h;
+    const ulonglong2 *itwt = T.itw + ((size_t)L.tf << S::LOGN);
+    ulonglong2 *tsh = reinterpret_cast<ulonglong2 *>(sm + S::ROWS * S::ROWPAD) + rr * S::REGB;
     const u64 *gin = L.src + ((size_t)h << S::LB);
     u64 *gout = L.dst + ((size_t)h << S::LB);
     u64 x[S::REGB];
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) x[k] = gin[k * S::TB + tau];
-    row_inv_core<S, SP>(x, tw, sm + rr * S::ROWPAD, tau, q, q2);
+    // the last round's twiddles (common to the row) staged beside the loads,
+    // as in the forward row pass; the block barriers of the first round
+    // order them before their use
+    stage_row_round1<S>(tsh, itwt, G, tau);
+    row_inv_core<S, SP>(x, TwStaged<S>{tsh, itwt, G}, sm + rr * S::ROWPAD, tau, q, q2);
 #pragma unroll
     for (int k = 0; k < S::REGB; ++k) gout[k * S::TB + tau] = x[k];
 }
@@ -305,7 +311,7 @@ static void set_smem_attrs_sp()
     cudaFuncSetAttribute(k_inv_col<S, 2, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_A);
     cudaFuncSetAttribute(k_fwd_row<S, true, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
     cudaFuncSetAttribute(k_fwd_row<S, false, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
-    cudaFuncSetAttribute(k_inv_row<S, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_B);
+    cudaFuncSetAttribute(k_inv_row<S, SP>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_BT);
 }
 
 template <class S>
@@ -415,9 +421,9 @@ static void inv_row_S(const Tables &T, const LimbMaps &m, cudaStream_t st)
     set_smem_attrs<S>();
     const dim3 gb = limb_grid((1 << S::LA) / S::ROWS, m.pre[m.n]);
     if (T.spq)
-        KS_LAUNCH(st, "ntt_inv_row", k_inv_row<S, true><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
+        KS_LAUNCH(st, "ntt_inv_row", k_inv_row<S, true><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
     else
-        KS_LAUNCH(st, "ntt_inv_row", k_inv_row<S, false><<<gb, S::THREADS_B, S::SMEM_B, st>>>(T, m));
+        KS_LAUNCH(st, "ntt_inv_row", k_inv_row<S, false><<<gb, S::THREADS_B, S::SMEM_BT, st>>>(T, m));
 }
 
 template <class S>
