@@ -666,8 +666,11 @@ __global__ void __launch_bounds__(256) k_oc_comb_pw(Tables T, OcJobs oj)
 }
 
 // Q-tower combine of the whole-basis layout.  grid (N/(256V), sum of nact).
+// Four CTAs per SM (64 registers, a few spilled words): more loads in flight
+// than three CTAs at the compiler's 74 registers (0.92 -> 0.95 of the copy
+// bandwidth on the benchmark step).
 template <bool CK, int V>
-__global__ void __launch_bounds__(256) k_oc_comb_qw(Tables T, OcJobs oj)
+__global__ void __launch_bounds__(256, 4) k_oc_comb_qw(Tables T, OcJobs oj)
 {
     const int jb = find_slot(oj.pre, oj.n, blockIdx.y);
     const OcJob &J = oj.job[jb];
