@@ -9,14 +9,15 @@
 // c_{i,t} mod r_t, and each c' is cut into 7 bytes c'_{i,a,t,b}; then
 //   z_t == sum_{b=0}^{6} 2^(8b) P_{t,b}  (mod r_t),
 //   P_{t,b} = sum_i sum_a y_{i,a} c'_{i,a,t,b},
-// and every P_{t,b} (at most 9 sources x 7 bytes x 255^2 < 2^22) is an exact
+// and every P_{t,b} (at most 18 sources x 7 bytes x 255^2 < 2^23) is an exact
 // integer in the fp32 accumulator.  One MMA of M=128 coefficients,
-// K = 7*(sources) padded to 64, N = 8 per target (7 byte rows used) computes
+// K = 7*(sources) padded to 64 (up to 9 sources) or 128 (up to 18: two K
+// blocks), N = 8 per target (7 byte rows used) computes
 // all P_{t,b} of up to 32 targets: the A tile holds the byte slices of y
 // (built by the CTA from the source limbs), the B tile the per-target slabs
-// B[b][7i+a] = c'_{i,a,t,b} (precomputed on the host, 1 KB each).  The
+// B[b][7i+a] = c'_{i,a,t,b} (precomputed on the host, 1 KB a K block).  The
 // epilogue reads the 7 sums from tensor memory, recombines them into a sum
-// below 2^70 and reduces it with one Montgomery reduction (constants carry
+// below 2^72 and reduces it with one Montgomery reduction (constants carry
 // 2^64), giving a lazy [0, 2r) output like the CUDA-core kernels (the same
 // residue; the representative may differ).
 //
@@ -33,23 +34,29 @@ namespace ks {
 namespace {
 
 constexpr int TC_M = 128;            // coefficients per MMA tile
-constexpr int TC_K = 64;             // padded K (7 x up to 9 sources)
 constexpr int TC_TB = 32;            // targets per MMA (8 accumulator columns each)
 constexpr uint32_t TC_LBO = 128;
-constexpr uint32_t TC_SBO = (TC_K / 8) * 128;
-constexpr int TC_SLAB = 8 * TC_K * 2;  // bytes of one target slab
-static_assert(TC_SLAB == 2 * kTcSlabHalves, "slab size");
+// KB K blocks of 64: K = 64*KB columns (7 x up to 9*KB sources, the last
+// column the bias), 8-row groups K/8*128 bytes apart, slabs of 8 rows.
+template <int KB> struct TcK {
+    static constexpr int K = 64 * KB;
+    static constexpr uint32_t SBO = (K / 8) * 128;
+    static constexpr int SLAB = 8 * K * 2;  // bytes of one target slab
+    static constexpr int NSV = KB == 1 ? 5 : 10;  // source words of one producer (half a row)
+};
+static_assert(TcK<1>::SLAB == 2 * kTcSlabHalves && TcK<2>::SLAB == 4 * kTcSlabHalves, "slab size");
 constexpr int TC_WAIT_LIMIT = 1 << 24;  // mbarrier polls before giving up
 
 __device__ int g_tc_error;  // set when an MMA completion wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+template <int KB>
 __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
 {
     uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)((TC_LBO >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((TC_SBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)((TcK<KB>::SBO >> 4) & 0x3FFF) << 32;
     d |= (uint64_t)1 << 46;  // descriptor version of this architecture; no swizzle
     return d;
 }
@@ -58,9 +65,10 @@ __device__ __forceinline__ uint32_t tc_idesc(int n)
 {
     return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
+template <int KB>
 __host__ __device__ __forceinline__ uint32_t tc_off(int r, int k)
 {
-    return (uint32_t)((r / 8) * TC_SBO + (k / 8) * TC_LBO + (r % 8) * 16 + (k % 8) * 2);
+    return (uint32_t)((r / 8) * TcK<KB>::SBO + (k / 8) * TC_LBO + (r % 8) * 16 + (k % 8) * 2);
 }
 // Two bytes as an exact f16 pair: byte a0 of word x (low half) and byte a1 of
 // word y (high half).  0x6400 | b is the f16 of 1024 + b (b < 1024), so one
@@ -79,7 +87,7 @@ __device__ __forceinline__ uint32_t f16x2_bytes(uint32_t x, uint32_t y, uint32_t
 
 // Sum of the 7 shifted partial sums of one target, Montgomery-reduced.
 // v[b] are the raw accumulator bits 0x4B000000 + P_b (bias column); the bias
-// is removed once per group.  S = a0 + a1*2^40 < 2^70.
+// is removed once per group.  S = a0 + a1*2^40 < 2^72.
 __device__ __forceinline__ u64 tc_reduce(const uint32_t *v, u64 q, u64 mont)
 {
     constexpr u64 B = 0x4B000000ull;
@@ -121,7 +129,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase)
 // targets of one (job, digit) (ModUp) or (job, polynomial) (ModDown).
 struct TcItem {
     const u64 *src;     // source tower 0 at the tile's first coefficient; tower i at + i*N
-    int nsrc;           // source towers (<= 9)
+    int nsrc;           // source towers (<= 18)
     int G;              // targets (0: nothing to do)
     int key;            // (job block, target block): the B slabs and targets change with it
     int sbase;          // slab index base (ModUp: of the digit at this level)
@@ -216,30 +224,38 @@ constexpr int TC_CONS_WARPS = 16;             // consumer warps: 4 lane quarters
 constexpr int TC_PIPE_THREADS = TC_PROD + 32 * TC_CONS_WARPS;
 constexpr uint32_t TC_PIPE_COLS = 512;        // two accumulators of 256 columns
 
-// Half H of A-tile row m: K chunks 4H..4H+3 from sources 4H..4H+4 (y[u] =
-// source 4H+u, zero past the item's sources).
-template <int H>
-__device__ __forceinline__ void tc_build_half(unsigned char *sa, int m, const u64 (&y)[5])
+// Half H of A-tile row m: K chunks CH*H..CH*H+CH-1 (CH = 4*KB chunks of 8
+// columns) from the sources they touch, y[u] = source SB + u with SB =
+// 8*CH*H/7 (zero past the item's sources).  Column K-1 is the bias.
+template <int KB, int H>
+struct TcHalf {
+    static constexpr int SB = 8 * 4 * KB * H / 7;                          // first source
+    static constexpr int LAST = H == 1 ? 64 * KB - 2 : 8 * 4 * KB * (H + 1) - 1;  // last slice column
+    static_assert(LAST / 7 - SB < TcK<KB>::NSV, "source words of a half row");
+};
+template <int KB, int H>
+__device__ __forceinline__ void tc_build_half(unsigned char *sa, int m, const u64 (&y)[TcK<KB>::NSV])
 {
-    uint32_t wd[10];
+    constexpr int CH = 4 * KB, SB = TcHalf<KB, H>::SB, NSV = TcK<KB>::NSV, K = TcK<KB>::K;
+    uint32_t wd[2 * NSV];
 #pragma unroll
-    for (int u = 0; u < 5; ++u) {
+    for (int u = 0; u < NSV; ++u) {
         wd[2 * u] = (uint32_t)y[u];
         wd[2 * u + 1] = (uint32_t)(y[u] >> 32);
     }
 #pragma unroll
-    for (int c = 4 * H; c < 4 * H + 4; ++c) {
+    for (int c = CH * H; c < CH * H + CH; ++c) {
         uint32_t w[4];
 #pragma unroll
         for (int e = 0; e < 8; e += 2) {
             const int k0 = 8 * c + e, k1 = k0 + 1;
-            const int u0 = k0 / 7 - 4 * H, a0 = k0 % 7, u1 = k1 / 7 - 4 * H, a1 = k1 % 7;
-            if (k1 == 63)  // byte 6 of source 8, then the bias 2048 (f16 0x6800)
-                w[e / 2] = (f16x2_bytes(wd[2 * 4 + 1], 0u, 2u, 0u) & 0xFFFFu) | 0x68000000u;
+            const int u0 = k0 / 7 - SB, a0 = k0 % 7, u1 = k1 / 7 - SB, a1 = k1 % 7;
+            if (k1 == K - 1)  // the last slice byte, then the bias 2048 (f16 0x6800)
+                w[e / 2] = (f16x2_bytes(wd[2 * u0 + a0 / 4], 0u, (uint32_t)(a0 % 4), 0u) & 0xFFFFu) | 0x68000000u;
             else
                 w[e / 2] = f16x2_bytes(wd[2 * u0 + a0 / 4], wd[2 * u1 + a1 / 4], (uint32_t)(a0 % 4), (uint32_t)(a1 % 4));
         }
-        *reinterpret_cast<uint4 *>(sa + tc_off(m, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4 *>(sa + tc_off<KB>(m, 8 * c)) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
@@ -279,13 +295,14 @@ struct TcCursor {
 // commits them to acc_full; consumer warps wait on acc_full, run the
 // epilogue and release the buffer through acc_empty.  Every wait is bounded:
 // on timeout the kernel sets g_tc_error and its threads leave their loops.
-template <int MODE>
+template <int MODE, int KB>
 __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJobs bu, BDnJobs bd, const uint4 *slabs,
                                                                 int XT, int TBN, int TB, int items)
 {
+    constexpr int K = TcK<KB>::K, NSV = TcK<KB>::NSV;
     extern __shared__ unsigned char tc_dyn[];
     unsigned char *sa0 = tc_dyn + ((128 - (smem_u32(tc_dyn) & 127)) & 127);
-    unsigned char *sb = sa0 + 2 * TC_M * TC_K * 2;
+    unsigned char *sb = sa0 + 2 * TC_M * K * 2;
     __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2];
     __shared__ uint32_t tbase_s;
     __shared__ u64 *s_dst[2][TC_TB];
@@ -315,25 +332,26 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
 
     if (tid < TC_PROD) {
         // ------------------------------------------------------------ producers
-        const int m = tid % TC_M, h = tid / TC_M;  // row m, K chunks 4h..4h+3 (sources 4h..4h+4)
+        const int m = tid % TC_M, h = tid / TC_M;  // row m, half h of its K columns
+        const int sb0 = h == 0 ? TcHalf<KB, 0>::SB : TcHalf<KB, 1>::SB;  // first source of the half
         int k = 0, cur_r = -1;
         TcCursor<MODE> cur, nxt;
         nxt.start(T, bu, bd, i0, XT, TBN, TB);
-        u64 y[5];
+        u64 y[NSV];
 #pragma unroll
-        for (int u = 0; u < 5; ++u)
-            y[u] = (nxt.it.G > 0 && 4 * h + u < nxt.it.nsrc) ? nxt.it.src[(size_t)(4 * h + u) * N + m] : 0;
+        for (int u = 0; u < NSV; ++u)
+            y[u] = (nxt.it.G > 0 && sb0 + u < nxt.it.nsrc) ? nxt.it.src[(size_t)(sb0 + u) * N + m] : 0;
         bool ok = true;
         for (int item = i0; item < i1; ++item) {
             cur = nxt;
-            u64 yc[5];
+            u64 yc[NSV];
 #pragma unroll
-            for (int u = 0; u < 5; ++u) yc[u] = y[u];
+            for (int u = 0; u < NSV; ++u) yc[u] = y[u];
             if (item + 1 < i1) {  // the next item's sources are in flight while this one is built
                 nxt.next(T, bu, bd);
 #pragma unroll
-                for (int u = 0; u < 5; ++u)
-                    y[u] = (nxt.it.G > 0 && 4 * h + u < nxt.it.nsrc) ? nxt.it.src[(size_t)(4 * h + u) * N + m] : 0;
+                for (int u = 0; u < NSV; ++u)
+                    y[u] = (nxt.it.G > 0 && sb0 + u < nxt.it.nsrc) ? nxt.it.src[(size_t)(sb0 + u) * N + m] : 0;
             }
             const TcItem &it = cur.it;
             if (it.G == 0) continue;
@@ -351,7 +369,7 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
             if (restage) {
                 // G slabs, and a zero slab after an odd G (the MMA's N is a
                 // multiple of 16 columns: two targets)
-                constexpr int W = TC_SLAB / 16;
+                constexpr int W = TcK<KB>::SLAB / 16;
                 const int Gp = (it.G + 1) & ~1;
                 for (int idx = tid; idx < Gp * W; idx += TC_PROD) {
                     const int g = idx / W, w = idx % W;
@@ -365,13 +383,13 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
                 }
                 cur_r = cur.r;
             }
-            unsigned char *sa = sa0 + buf * (TC_M * TC_K * 2);
+            unsigned char *sa = sa0 + buf * (TC_M * K * 2);
             // A tile: row m, columns 7i+a = byte a of source i (f16); column 63 =
             // 2048, the bias with the slabs' 4096 there.  Sources past nsrc are 0.
             if (h == 0)
-                tc_build_half<0>(sa, m, yc);
+                tc_build_half<KB, 0>(sa, m, yc);
             else
-                tc_build_half<1>(sa, m, yc);
+                tc_build_half<KB, 1>(sa, m, yc);
             if (h == 0 && m < it.G) {
                 int t, tf, slab;
                 tc_target<MODE>(T, it, m, t, tf, slab);
@@ -387,9 +405,9 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
                 const uint32_t idesc = tc_idesc(8 * ((it.G + 1) & ~1));
                 const uint32_t dcol = tbase + (uint32_t)(buf * 256);
 #pragma unroll
-                for (int kk = 0; kk < TC_K / 16; ++kk) {
-                    const uint64_t ad = tc_desc(smem_u32(sa) + kk * 2 * TC_LBO);
-                    const uint64_t bdsc = tc_desc(smem_u32(sb) + kk * 2 * TC_LBO);
+                for (int kk = 0; kk < K / 16; ++kk) {
+                    const uint64_t ad = tc_desc<KB>(smem_u32(sa) + kk * 2 * TC_LBO);
+                    const uint64_t bdsc = tc_desc<KB>(smem_u32(sb) + kk * 2 * TC_LBO);
                     asm volatile(
                         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(dcol),
@@ -458,14 +476,16 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
 // Dynamic shared memory: two A tiles (16 KB each) and up to 16 B slabs
 // (32 KB), padded so that one CTA holds an SM (it takes all 512 columns of
 // tensor memory).
-constexpr int TC_PIPE_SMEM = 120 * 1024;
-static_assert(TC_PIPE_SMEM >= 2 * TC_M * TC_K * 2 + TC_TB * TC_SLAB + 128, "tile space");
+// With two K blocks: two 32 KB A tiles and up to 32 slabs of 2 KB.
+template <int KB> constexpr int tc_pipe_smem() { return KB == 1 ? 120 * 1024 : 132 * 1024; }
+static_assert(tc_pipe_smem<1>() >= 2 * TC_M * TcK<1>::K * 2 + TC_TB * TcK<1>::SLAB + 128, "tile space");
+static_assert(tc_pipe_smem<2>() >= 2 * TC_M * TcK<2>::K * 2 + TC_TB * TcK<2>::SLAB + 128, "tile space");
 
 }  // namespace
 
 bool bconv_tc_supported(const Tables &T, int nsrc)
 {
-    return nsrc <= 9 && (((size_t)1 << T.logN) % (size_t)TC_M) == 0;
+    return nsrc <= 18 && (((size_t)1 << T.logN) % (size_t)TC_M) == 0;
 }
 
 static int sm_count()
@@ -479,22 +499,23 @@ static int sm_count()
     return n;
 }
 
-template <int MODE>
+template <int MODE, int KB>
 static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int span, int Z, const uint4 *slabs,
                      cudaStream_t st, const char *name)
 {
-    // target blocks of equal size (at most 16): 24 targets run as 12 + 12
+    // target blocks of equal size (at most 32): 38 targets run as 19 + 19
     const int TBN = (span + TC_TB - 1) / TC_TB;
     const int TB = (span + TBN - 1) / TBN;
     static std::atomic<uint64_t> attr{0};
-    once_per_device(attr,
-                    [] { cudaFuncSetAttribute(k_bconv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_PIPE_SMEM); });
+    once_per_device(attr, [] {
+        cudaFuncSetAttribute(k_bconv_tc<MODE, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_pipe_smem<KB>());
+    });
     const int XT = (int)(((size_t)1 << T.logN) / TC_M);
     const long long items = (long long)XT * TBN * Z;
     if (items <= 0) return KS_OK;
     const int grid = (int)std::min<long long>(items, sm_count());
-    KS_LAUNCH(st, name, k_bconv_tc<MODE><<<grid, TC_PIPE_THREADS, TC_PIPE_SMEM, st>>>(T, bu, bd, slabs, XT, TBN, TB,
-                                                                                        (int)items));
+    KS_LAUNCH(st, name, (k_bconv_tc<MODE, KB><<<grid, TC_PIPE_THREADS, tc_pipe_smem<KB>(), st>>>(T, bu, bd, slabs, XT,
+                                                                                                 TBN, TB, (int)items)));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KS_OK : fail(KS_ECUDA, std::string(name) + " (tensor cores) launch: " + cudaGetErrorString(e));
 }
@@ -516,7 +537,8 @@ int launch_bconv_up_tc(const Tables &T, const BUpJobs &b, const uint4 *slabs, co
     none.n = 0;
     Tables Tt = T;
     Tt.up_tc = slabs;
-    return launch_tc<0>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up");
+    return tc_kblocks(T.alpha) == 1 ? launch_tc<0, 1>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up")
+                                    : launch_tc<0, 2>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up");
 }
 
 int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, cudaStream_t st)
@@ -526,7 +548,8 @@ int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, 
     if (span <= 0) return KS_OK;
     BUpJobs none;
     none.n = 0;
-    return launch_tc<1>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down");
+    return tc_kblocks(T.kp) == 1 ? launch_tc<1, 1>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down")
+                                 : launch_tc<1, 2>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down");
 }
 
 int tc_error_flag(bool clear)
@@ -545,12 +568,14 @@ int tc_error_flag(bool clear)
 
 // Host: the B slab of one target of modulus r: rows b = 0..7 (byte of the
 // folded constant; row 7 zero), columns k = 7i + a (source i, byte a of y):
-// byte b of c_i * 2^(8a) mod r.
-void tc_slab(const std::vector<u64> &c, u64 r, uint16_t *slab)
+// byte b of c_i * 2^(8a) mod r; the last column holds the bias.
+template <int KB>
+static void tc_slab_kb(const std::vector<u64> &c, u64 r, uint16_t *slab)
 {
-    for (int k = 0; k < TC_K; ++k) {
+    constexpr int K = TcK<KB>::K;
+    for (int k = 0; k < K; ++k) {
         const int i = k / 7, a = k % 7;
-        const u64 cf = i < (int)c.size() ? mulmod_h(c[i] % r, powmod_h(2, 8 * (u64)a, r), r) : 0;
+        const u64 cf = (k < K - 1 && i < (int)c.size()) ? mulmod_h(c[i] % r, powmod_h(2, 8 * (u64)a, r), r) : 0;
         for (int b = 0; b < 8; ++b) {
             const uint32_t byte = b < 7 ? (uint32_t)((cf >> (8 * b)) & 0xFF) : 0u;
             // f16 of an integer below 256
@@ -560,13 +585,22 @@ void tc_slab(const std::vector<u64> &c, u64 r, uint16_t *slab)
                 uint32_t mant = (byte << (10 - e)) & 0x3FF;        // 10 fraction bits
                 bits = (uint16_t)(((15 + e) << 10) | mant);
             }
-            slab[tc_off(b, k) / 2] = bits;
+            slab[tc_off<KB>(b, k) / 2] = bits;
         }
     }
-    // column 63 (never a slice: 9 sources use 0..62) holds 4096 in the 7 used
-    // byte rows; times the A tile's 2048 there it adds 2^23, so the fp32
-    // accumulator of P (< 2^22) reads 2^23 + P: its bits are 0x4B000000 + P
-    for (int b = 0; b < 7; ++b) slab[tc_off(b, 63) / 2] = (uint16_t)((15 + 12) << 10);
+    // the last column (never a slice: 9*KB sources use the columns before it)
+    // holds 4096 in the 7 used byte rows; times the A tile's 2048 there it
+    // adds 2^23, so the fp32 accumulator of P (< 2^23) reads 2^23 + P: its
+    // bits are 0x4B000000 + P
+    for (int b = 0; b < 7; ++b) slab[tc_off<KB>(b, K - 1) / 2] = (uint16_t)((15 + 12) << 10);
+}
+
+void tc_slab(const std::vector<u64> &c, u64 r, int kblocks, uint16_t *slab)
+{
+    if (kblocks == 1)
+        tc_slab_kb<1>(c, r, slab);
+    else
+        tc_slab_kb<2>(c, r, slab);
 }
 
 }  // namespace ks

@@ -250,11 +250,13 @@ int build_tables(ks_params *P)
             dn[(size_t)k * P->nq + i] = split28(to_mont(invmod_h(P->p[k] % P->q[i], P->q[i]), P->q[i]));
 
     // tensor-core base conversion: one B slab per (digit j, active towers a,
-    // full tower t) for ModUp and per Q tower for ModDown (<= 9 sources)
+    // full tower t) for ModUp and per Q tower for ModDown (<= 18 sources; one
+    // K block of 64 slice columns up to 9, two up to 18)
     std::vector<uint16_t> up_tc, dn_tc;
     std::vector<int> up_tc_lvl((size_t)P->nq * P->ndig, 0);
-    constexpr size_t SLAB = kTcSlabHalves;
-    if (A <= 9) {
+    const int kb_up = tc_kblocks(A), kb_dn = tc_kblocks(P->kp);
+    const size_t SLAB = (size_t)kTcSlabHalves * kb_up, DSLAB = (size_t)kTcSlabHalves * kb_dn;
+    if (A <= 18) {
         std::vector<int> off((size_t)P->ndig * (A + 1), -1);
         for (int j = 0; j < P->ndig; ++j) {
             int lo = j * A;
@@ -271,7 +273,7 @@ int build_tables(ks_params *P)
                         c[i] = to_mont(hat, r);
                     }
                     up_tc.resize(up_tc.size() + SLAB);
-                    tc_slab(c, r, up_tc.data() + up_tc.size() - SLAB);
+                    tc_slab(c, r, kb_up, up_tc.data() + up_tc.size() - SLAB);
                 }
             }
         }
@@ -279,12 +281,12 @@ int build_tables(ks_params *P)
             for (int j = 0; j * A < nact; ++j)
                 up_tc_lvl[(size_t)(nact - 1) * P->ndig + j] = off[j * (A + 1) + std::min(A, nact - j * A)];
     }
-    if (P->kp <= 9) {
-        dn_tc.resize((size_t)P->nq * SLAB);
+    if (P->kp <= 18) {
+        dn_tc.resize((size_t)P->nq * DSLAB);
         for (int i = 0; i < P->nq; ++i) {
             std::vector<u64> c(P->kp);
             for (int k = 0; k < P->kp; ++k) c[k] = to_mont(invmod_h(P->p[k] % P->q[i], P->q[i]), P->q[i]);
-            tc_slab(c, P->q[i], dn_tc.data() + (size_t)i * SLAB);
+            tc_slab(c, P->q[i], kb_dn, dn_tc.data() + (size_t)i * DSLAB);
         }
     }
 

@@ -123,15 +123,17 @@ int launch_bconv_down(const Tables &T, const BDnJobs &b, cudaStream_t st);
 
 // Tensor-core base conversion (ks_bconv_tc.cu): same jobs and outputs as the
 // CUDA-core kernels; used by launch_bconv_up/down when the tables are present
-// and the shape is supported (at most 9 sources, N a multiple of 128).
+// and the shape is supported (at most 18 sources, N a multiple of 128).
 bool bconv_tc_supported(const Tables &T, int nsrc);
 int launch_bconv_up_tc(const Tables &T, const BUpJobs &b, const uint4 *slabs, const int *slab_lvl, cudaStream_t st);
 int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, cudaStream_t st);
-// Host: one 1 KB B slab (8 byte rows x 64 slice columns, f16, canonical
-// layout) for the constants c[0..nsrc) of one target of modulus r: row b,
-// column 7i + a holds byte b of c_i * 2^(8a) mod r.
-constexpr int kTcSlabHalves = 8 * 64;
-void tc_slab(const std::vector<u64> &c, u64 r, uint16_t *slab);
+// K blocks of 64 slice columns for nsrc sources: one up to 9, two up to 18.
+inline int tc_kblocks(int nsrc) { return nsrc <= 9 ? 1 : 2; }
+// Host: one B slab of kblocks KB (8 byte rows x 64*kblocks slice columns,
+// f16, canonical layout) for the constants c[0..nsrc) of one target of
+// modulus r: row b, column 7i + a holds byte b of c_i * 2^(8a) mod r.
+constexpr int kTcSlabHalves = 8 * 64;  // f16 words of a slab per K block
+void tc_slab(const std::vector<u64> &c, u64 r, int kblocks, uint16_t *slab);
 // Device flag set by a tensor-core kernel whose MMA wait gave up (-1: unreadable).
 int tc_error_flag(bool clear);
 // Device flag set by a staged row pass whose bulk-copy wait gave up (-1: unreadable).
