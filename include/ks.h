@@ -427,8 +427,8 @@ int ks_predict_schedule(ks_params *params, uint32_t n, const ks_job *h_jobs, ks_
  * level, rounded), dnum (the parameter set's at the top level, else the
  * active digits), K, log2 batch, alpha = ceil((L+1)/dnum), log2 input words,
  * each scaled by fixed constants, then +-1 flags: tensor-core ModUp base
- * conversion available (the parameter set's alpha <= 9), tensor-core ModDown
- * (K <= 9), cluster NTT (logN not 13 or 17). */
+ * conversion available (the parameter set's alpha <= 18), tensor-core ModDown
+ * (K <= 18), cluster NTT (logN not 13 or 17). */
 int ks_cost_features(const ks_params *params, uint32_t n, const ks_job *h_jobs, float *h_x);
 
 /* A key with pseudo-random residues generated on the device (for timing

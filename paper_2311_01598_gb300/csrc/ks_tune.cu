@@ -85,8 +85,8 @@ static int tune_impl(ks_params *P, uint32_t n, const ks_job *jobs, uint32_t reps
 // Inputs of the learned cost model: (logN, L+1, dnum, K, log2 batch, alpha,
 // log2 input words), each scaled to roughly unit range by fixed constants,
 // then three +-1 flags of which implementations exist for the shape: the
-// tensor-core ModUp base conversion (at most 9 sources per digit), the
-// tensor-core ModDown one (at most 9 special towers), and the cluster NTT
+// tensor-core ModUp base conversion (at most 18 sources per digit), the
+// tensor-core ModDown one (at most 18 special towers), and the cluster NTT
 // (ring degrees other than 2^13 and 2^17); where one is missing, its
 // schedule field selects the same kernels as the other value.  The Python
 // training code computes the same vector (tune.features).
@@ -103,8 +103,8 @@ static void cost_features(int logN, int nq, int dnum, int kp, int batch, int alp
     x[4] = (float)((std::log2((double)batch) - 4) / 2.5);
     x[5] = (float)((alpha - 12) / 12.0);
     x[6] = (float)((std::log2(words) - 22) / 3.0);
-    x[7] = alpha_params <= 9 ? 1.f : -1.f;
-    x[8] = kp <= 9 ? 1.f : -1.f;
+    x[7] = alpha_params <= 18 ? 1.f : -1.f;
+    x[8] = kp <= 18 ? 1.f : -1.f;
     x[9] = (logN != 13 && logN != 17) ? 1.f : -1.f;
 }
 

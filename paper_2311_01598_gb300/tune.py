@@ -42,9 +42,9 @@ WORDS_CAP = (1 << 16) * 24 * 16
 def features(logN, nq, dnum, kp, batch, alpha_params=None):
     """Model inputs: the workload's sizes scaled to roughly unit range by
     fixed constants, then +-1 flags of which implementations exist for the
-    shape (tensor-core ModUp base conversion: at most 9 sources per digit,
+    shape (tensor-core ModUp base conversion: at most 18 sources per digit,
     alpha_params being the parameter set's alpha, by default ceil(nq/dnum);
-    tensor-core ModDown: at most 9 special towers; cluster NTT: ring degrees
+    tensor-core ModDown: at most 18 special towers; cluster NTT: ring degrees
     other than 2^13 and 2^17).  The library computes the same vector
     (ks_cost_features)."""
     alpha = -(-nq // dnum)
@@ -52,7 +52,7 @@ def features(logN, nq, dnum, kp, batch, alpha_params=None):
     words = batch * nq * (1 << logN)
     return np.array([(logN - 15) / 2.0, (nq - 25) / 14.0, (dnum - 12) / 12.0, (kp - 6.5) / 3.5,
                      (math.log2(batch) - 4) / 2.5, (alpha - 12) / 12.0, (math.log2(words) - 22) / 3.0,
-                     1.0 if ap <= 9 else -1.0, 1.0 if kp <= 9 else -1.0, 1.0 if logN not in (13, 17) else -1.0],
+                     1.0 if ap <= 18 else -1.0, 1.0 if kp <= 18 else -1.0, 1.0 if logN not in (13, 17) else -1.0],
                     dtype=np.float32)
 
 
