@@ -23,7 +23,7 @@
 //
 // Operand layout: the canonical K-major layout without swizzle: 8x16-byte
 // core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row
-// groups 1024 bytes apart (SBO); B slabs of 8 rows concatenate.
+// groups 1024 bytes a K block apart (SBO); B slabs of 8 rows concatenate.
 #include <cstdio>
 
 #include "ks_device.cuh"
