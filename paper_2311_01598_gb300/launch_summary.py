@@ -157,7 +157,8 @@ def to_markdown(table, total, n):
 # library launch names (KS_LAUNCH) of the key-switching kernels
 LIB_NAMES = {"k_fwd_row": "ntt_fwd_row", "k_fwd_col": "ntt_fwd_col", "k_inv_row": "ntt_inv_row",
              "k_inv_col": "ntt_inv_col", "k_bconv_up": "bconv_up", "k_bconv_down": "bconv_down",
-             "k_bconv_tc<0>": "bconv_up", "k_bconv_tc<1>": "bconv_down",
+             "k_bconv_tc<0, 1>": "bconv_up", "k_bconv_tc<0, 2>": "bconv_up", "k_bconv_tc<1, 1>": "bconv_down",
+             "k_bconv_tc<1, 2>": "bconv_down",
              "k_oc_comb_qw": "oc_comb_q", "k_oc_comb_pw": "oc_comb_p", "k_oc_comb_q": "oc_comb_q",
              "k_oc_comb_p": "oc_comb_p", "k_oc_comb_qg": "oc_comb_q", "k_oc_comb_pg": "oc_comb_p",
              "k_fwd_cl": "ntt_fwd_cl", "k_inv_cl": "ntt_inv_cl", "k_oc_rowP": "oc_row_p", "k_oc_rowQ": "oc_row_q",

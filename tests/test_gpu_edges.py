@@ -174,13 +174,21 @@ def test_extreme_inputs_56bit(kind, key_kind):
         check_all_paths(ks, P, C, key, nact, d, w0, w1, engines=(True, False), what=(kind, key_kind))
 
 
+# (logN, nq, kp, dnum, levels): one K block of the tensor-core base conversion
+# (8 sources), and two at their limit (18 sources: partial sums up to
+# 7*18*255^2, just below the 2^23 of the accumulator's fixed read-out)
+EXTREME_SHAPES = [(16, 24, 8, 3, (24, 9)), (13, 36, 18, 2, (36, 19))]
+
+
+@pytest.mark.parametrize("shape", EXTREME_SHAPES, ids=["8src", "18src"])
 @pytest.mark.parametrize("kind", ["all_q_minus_1", "max_y"])
-def test_modup_extreme_56bit(kind):
+def test_modup_extreme_56bit(kind, shape):
     """ModUp P1-P3 stage (Sec. III-B) with the largest inputs, 56-bit primes."""
     need_gpu()
     ks = built_lib()
-    P, C = pair(16, 24, 8, 3, 56)
-    for nact in (24, 9):
+    logN, nq, kp, dnum, levels = shape
+    P, C = pair(logN, nq, kp, dnum, 56)
+    for nact in levels:
         if kind == "all_q_minus_1":
             d = np.ones((nact, C.N), dtype=np.uint64) * (np.array(C.q[:nact], dtype=np.uint64) - 1)[:, None]
         else:
@@ -194,14 +202,16 @@ def test_modup_extreme_56bit(kind):
     P.set_bconv_tensor(True)
 
 
+@pytest.mark.parametrize("shape", EXTREME_SHAPES, ids=["8src", "18src"])
 @pytest.mark.parametrize("kind", ["all_r_minus_1", "max_w"])
-def test_moddown_extreme_56bit(kind):
+def test_moddown_extreme_56bit(kind, shape):
     """ModDown P1-P4 stage (Sec. III-C) with c' of all r-1, or with every
     pre-scaled special-tower coefficient p_k - 1, 56-bit primes."""
     need_gpu()
     ks = built_lib()
-    P, C = pair(16, 24, 8, 3, 56)
-    for nact in (24, 9):
+    logN, nq, kp, dnum, levels = shape
+    P, C = pair(logN, nq, kp, dnum, 56)
+    for nact in levels:
         if kind == "all_r_minus_1":
             towers = np.array(C.towers(nact), dtype=np.uint64)
             cp = np.ones((2, nact + C.kp, C.N), dtype=np.uint64) * (towers - 1)[None, :, None]

@@ -9,7 +9,7 @@ CSV = '''==PROF== Connected to process 123
 "ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size","Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"
 "0","1","python","h","void at::native::elementwise_kernel<128, 2>(int, F)","1","7","(128, 1, 1)","(4, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","us","3.10"
 "1","1","python","h","void ks::k_inv_row<ks::Shape<8, 8>>(ks::Tables, ks::LimbMaps)","1","7","(64, 1, 1)","(64, 384, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","us","120.5"
-"2","1","python","h","void ks::(anonymous namespace)::k_bconv_tc<0>(ks::Tables, ks::BUpJobs, ks::BDnJobs, const uint4 *, int, int, int, int)","1","7","(768, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","ms","0.21"
+"2","1","python","h","void ks::(anonymous namespace)::k_bconv_tc<0, 1>(ks::Tables, ks::BUpJobs, ks::BDnJobs, const uint4 *, int, int, int, int)","1","7","(768, 1, 1)","(152, 1, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","ms","0.21"
 "3","1","python","h","void ks::k_fwd_row<ks::Shape<8, 8>, false>(ks::Tables, ks::LimbMaps)","1","7","(64, 1, 1)","(64, 1152, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","ns","300,000"
 "4","1","python","h","void ks::k_fwd_row<ks::Shape<8, 8>, false>(ks::Tables, ks::LimbMaps)","1","7","(64, 1, 1)","(64, 768, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","ns","200,000"
 "5","1","python","h","void ks::k_oc_comb_qw<false, 4>(ks::Tables, ks::OcJobs)","1","7","(256, 1, 1)","(64, 384, 1)","0","10.3","Command line profiler metrics","gpu__time_duration.sum","us","100"
@@ -20,7 +20,7 @@ def test_read_launches_keeps_library_kernels_and_units(tmp_path):
     p = tmp_path / "launches.csv"
     p.write_text(CSV)
     rows = L.read_launches(str(p))
-    assert [r[0] for r in rows] == ["k_inv_row<ks::Shape<8, 8>>", "k_bconv_tc<0>", "k_fwd_row<ks::Shape<8, 8>, false>",
+    assert [r[0] for r in rows] == ["k_inv_row<ks::Shape<8, 8>>", "k_bconv_tc<0, 1>", "k_fwd_row<ks::Shape<8, 8>, false>",
                                    "k_fwd_row<ks::Shape<8, 8>, false>", "k_oc_comb_qw<false, 4>"]
     assert [r[2] for r in rows] == [120500.0, 210000.0, 300000.0, 200000.0, 100000.0]
 
@@ -34,11 +34,12 @@ def test_summarise_window_and_shares(tmp_path):
     assert table[0][0] == "k_fwd_row<ks::Shape<8, 8>, false>" and table[0][1] == 2
     assert abs(sum(t[3] for t in table) - 1.0) < 1e-12
     md = L.to_markdown(table, total, n)
-    assert "3 launches, 710.0 us total" in md and "| `k_bconv_tc<0>` | 1 | 210.0 | 29.6% |" in md
+    assert "3 launches, 710.0 us total" in md and "| `k_bconv_tc<0, 1>` | 1 | 210.0 | 29.6% |" in md
 
 
 def test_library_names():
-    assert L.lib_name("void ks::(anonymous namespace)::k_bconv_tc<1>(ks::Tables)") == "bconv_down"
+    assert L.lib_name("void ks::(anonymous namespace)::k_bconv_tc<1, 1>(ks::Tables)") == "bconv_down"
+    assert L.lib_name("void ks::(anonymous namespace)::k_bconv_tc<0, 2>(ks::Tables)") == "bconv_up"
     assert L.lib_name("void ks::k_fwd_row<ks::Shape<8, 8>, true>(ks::Tables, ks::LimbMaps)") == "ntt_fwd_row"
     assert L.lib_name("void ks::k_oc_comb_qg<false, true, 2>(ks::Tables)") == "oc_comb_q"
     assert L.lib_name("void at::native::vectorized_elementwise_kernel<4>(int)") is None
