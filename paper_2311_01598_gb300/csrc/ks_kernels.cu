@@ -56,8 +56,11 @@ __global__ void __launch_bounds__(S::THREADS_B, S::MINB_B) k_fwd_row(Tables T, L
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
-    const int lg = blockIdx.y + blockIdx.z * gridDim.y;
-    if (lg >= ms.pre[ms.n]) return;
+    const int lz = blockIdx.y + blockIdx.z * gridDim.y;
+    if (lz >= ms.pre[ms.n]) return;
+    // limbs in reverse order: the column pass wrote the last ones most
+    // recently, so the first blocks find their rows in L2
+    const int lg = ms.pre[ms.n] - 1 - lz;
     const LimbRef L = limb_ref(ms, lg, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
     const ModC &mc = T.modc[L.tf];
@@ -259,8 +262,10 @@ __global__ void __launch_bounds__(S::THREADS_A, S::MINB_A) k_inv_col(Tables T, L
     extern __shared__ __align__(16) unsigned char smem_raw[];
     u64 *sm = reinterpret_cast<u64 *>(smem_raw);
     ulonglong2 *tws = reinterpret_cast<ulonglong2 *>(sm + (1 << S::LA) * S::COLS);
-    const int lg = blockIdx.y + blockIdx.z * gridDim.y;
-    if (lg >= ms.pre[ms.n]) return;
+    const int lz = blockIdx.y + blockIdx.z * gridDim.y;
+    if (lz >= ms.pre[ms.n]) return;
+    // limbs in reverse order: the row pass wrote the last ones most recently
+    const int lg = ms.pre[ms.n] - 1 - lz;
     const LimbRef L = limb_ref(ms, lg, T.nq, T.alpha, S::LOGN);
     if (L.skip) return;
     const ModC &mc = T.modc[L.tf];
