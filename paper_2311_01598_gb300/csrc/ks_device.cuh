@@ -182,6 +182,32 @@ __device__ __forceinline__ u64 key_a_word(u64 seed, int j, int t, size_t n, int 
     }
     return v % r;
 }
+// The same words for V consecutive slots n..n+V-1.  Slot n's first draw is
+// output 64n' of the stream (n' the slot's global index), whose state is
+// x + (64n'+1)*gamma: consecutive slots' first states differ by 64*gamma, so
+// one multiply serves the V slots and each further slot costs an addition.
+// A first draw that is rejected (at least r) takes the per-slot path for the
+// remaining draws.
+template <int V>
+__device__ __forceinline__ void key_a_words(u64 seed, int j, int t, size_t n, int logN, int nfull, u64 r,
+                                            u64 (&out)[V])
+{
+    constexpr u64 kGamma = 0x9E3779B97F4A7C15ull;
+    const int b = 64 - __clzll((long long)r);
+    const u64 mask = b >= 64 ? ~0ull : ((1ull << b) - 1);
+    const u64 base = (((((u64)j * (u64)nfull + (u64)t) << logN) + (u64)n) * 64);
+    u64 st = (seed ^ 2) + (base + 1) * kGamma;
+#pragma unroll
+    for (int c = 0; c < V; ++c) {
+        u64 z = st;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        u64 v = (z ^ (z >> 31)) & mask;
+        if (v >= r) v = key_a_word(seed, j, t, n + c, logN, nfull, r);
+        out[c] = v;
+        st += 64 * kGamma;
+    }
+}
 // Key words of digit j, full tower t, slot n.  Full keys hold both halves
 // times the tower's fold factor and 2^64; a compressed key's a-word is
 // canonical, so its sum of products is multiplied by that factor once per

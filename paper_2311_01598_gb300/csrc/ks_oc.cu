@@ -271,8 +271,7 @@ __device__ __forceinline__ void key_macv(const KeyView &K, int j, int t, size_t 
     u64 kb[V], ka[V];
     if (CK && K.comp) {
         ldv<V>(K.evk + ((size_t)j * nfull + t) * N + n, kb);
-#pragma unroll
-        for (int c = 0; c < V; ++c) ka[c] = key_a_word(K.a_seed, j, t, n + c, logN, nfull, q);
+        key_a_words<V>(K.a_seed, j, t, n, logN, nfull, q, ka);
     } else {
         ldv<V>(K.evk + ((size_t)(2 * j) * nfull + t) * N + n, kb);
         ldv<V>(K.evk + ((size_t)(2 * j + 1) * nfull + t) * N + n, ka);
@@ -292,8 +291,7 @@ __device__ __forceinline__ void key_words(const KeyView &K, int j, int t, size_t
     const size_t N = (size_t)1 << logN;
     if (CK && K.comp) {
         ldv<V>(K.evk + ((size_t)j * nfull + t) * N + n, kb);
-#pragma unroll
-        for (int c = 0; c < V; ++c) ka[c] = key_a_word(K.a_seed, j, t, n + c, logN, nfull, q);
+        key_a_words<V>(K.a_seed, j, t, n, logN, nfull, q, ka);
     } else {
         ldv<V>(K.evk + ((size_t)(2 * j) * nfull + t) * N + n, kb);
         ldv<V>(K.evk + ((size_t)(2 * j + 1) * nfull + t) * N + n, ka);

@@ -7,6 +7,7 @@ Used under ncu (the launch list and single-kernel captures under profiles/):
     python -m paper_2311_01598_gb300.profile_ks --hoisted 4      # hoisted rotations + automorphism
     python -m paper_2311_01598_gb300.profile_ks --shard 4        # tower-sharded key switch, 4 ranks emulated
     python -m paper_2311_01598_gb300.profile_ks --mlp            # cost-model MLP forward, backward, Adam
+    python -m paper_2311_01598_gb300.profile_ks --batch 4 --keys 4 --compressed --schedule 2,2,64,0
 Key generation runs first (a few launches), then one key switch per
 dataflow listed (or one batched call per dataflow with --batch B > 1), or
 the workload one of the other options names.
@@ -36,6 +37,7 @@ def main():
     ap.add_argument("--hoisted", type=int, default=0, help="R hoisted rotations of one ciphertext, then the automorphism")
     ap.add_argument("--shard", type=int, default=0, help="one key switch sharded by tower over G emulated ranks")
     ap.add_argument("--mlp", action="store_true", help="one training step and one forward pass of the cost model")
+    ap.add_argument("--compressed", action="store_true", help="compressed keys (a halves regenerated on chip)")
     ap.add_argument("--schedule", default=None,
                     help="'dataflow,oc_variant,chunk,order': one batched call with this schedule")
     a = ap.parse_args()
@@ -44,7 +46,10 @@ def main():
         P.set_row_stage(True)
     nact = a.level or a.nq
     s = inputs.ternary_secret(P.N, 1)
-    keys = [P.key_synthetic(7 + k) if k else P.keygen(s, inputs.galois_secret(s, 5), 7) for k in range(a.keys)]
+    if a.compressed:
+        keys = [P.keygen_compressed(s, inputs.galois_secret(s, 5 + 2 * k), 7 + k) for k in range(a.keys)]
+    else:
+        keys = [P.key_synthetic(7 + k) if k else P.keygen(s, inputs.galois_secret(s, 5), 7) for k in range(a.keys)]
     jobs = []
     for i in range(a.batch):
         d = ks.to_device(inputs.uniform_towers(P.q[:nact], P.N, 3 + i))
