@@ -6,20 +6,23 @@
 // constants below 2^56.  Exactness with f16 operands: y_i (canonical, < 2^56)
 // is cut into 7 bytes y_{i,a}, so y_i c_{i,t} = sum_a y_{i,a} 2^(8a) c_{i,t}.
 // The shift of byte a is folded into the constant, c'_{i,a,t} = 2^(8a)
-// c_{i,t} mod r_t, and each c' is cut into 7 bytes c'_{i,a,t,b}; then
-//   z_t == sum_{b=0}^{6} 2^(8b) P_{t,b}  (mod r_t),
+// c_{i,t} mod r_t, and each c' is cut into W-bit slices c'_{i,a,t,b}
+// (W = 8: 7 slices; W = 9: 6 slices, when every modulus is below 2^54 and the
+// sources fit one K block); then
+//   z_t == sum_b 2^(Wb) P_{t,b}  (mod r_t),
 //   P_{t,b} = sum_i sum_a y_{i,a} c'_{i,a,t,b},
-// and every P_{t,b} (at most 18 sources x 7 bytes x 255^2 < 2^23) is an exact
-// integer in the fp32 accumulator.  One MMA of M=128 coefficients,
+// and every P_{t,b} (at most 18 sources x 7 bytes x 255^2, or 9 x 7 x 255 x
+// 511 with W = 9, below 2^23) is an exact integer in the fp32 accumulator.  One MMA of M=128 coefficients,
 // K = 7*(sources) padded to 64 (up to 9 sources) or 128 (up to 18: two K
 // blocks), N = 8 per target (7 byte rows used) computes
 // all P_{t,b} of up to 32 targets: the A tile holds the byte slices of y
 // (built by the CTA from the source limbs), the B tile the per-target slabs
 // B[b][7i+a] = c'_{i,a,t,b} (precomputed on the host, 1 KB a K block).  The
-// epilogue reads the 7 sums from tensor memory, recombines them into a sum
-// below 2^72 and reduces it with one Montgomery reduction (constants carry
-// 2^64), giving a lazy [0, 2r) output like the CUDA-core kernels (the same
-// residue; the representative may differ).
+// epilogue reads the 6 or 7 sums from tensor memory and recombines them into
+// S = sum_{i,a} y_{i,a} c'_{i,a,t} exactly; S <= 126*255*r < 2^15 r, so one
+// Montgomery step by 2^32 (constants carry 2^32) leaves (S + m r)/2^32 below
+// 2r: a lazy [0, 2r) output like the CUDA-core kernels (the same residue; the
+// representative may differ).
 //
 // Operand layout: the canonical K-major layout without swizzle: 8x16-byte
 // core matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row
@@ -85,22 +88,32 @@ __device__ __forceinline__ uint32_t f16x2_bytes(uint32_t x, uint32_t y, uint32_t
     return r;
 }
 
-// Sum of the 7 shifted partial sums of one target, Montgomery-reduced.
-// v[b] are the raw accumulator bits 0x4B000000 + P_b (bias column); the bias
-// is removed once per group.  S = a0 + a1*2^40 < 2^72.
-__device__ __forceinline__ u64 tc_reduce(const uint32_t *v, u64 q, u64 mont)
+// The shifted partial sums of one target (W-bit slices: 7 for W = 8, 6 for
+// W = 9), recombined and reduced by one Montgomery step by 2^32.  v[b] are the
+// raw accumulator bits 0x4B000000 + P_b (bias column); the bias is removed
+// once per group (modulo 2^64: the exact sums fit).  qinv = -q^-1 mod 2^32.
+template <int W>
+__device__ __forceinline__ u64 tc_reduce(const uint32_t *v, u64 q, uint32_t qinv)
 {
     constexpr u64 B = 0x4B000000ull;
-    u64 a0 = 0, a1 = 0;
+    constexpr u64 B5 = B * (1ull + (1ull << W) + (1ull << (2 * W)) + (1ull << (3 * W)) + (1ull << (4 * W)));
+    u64 a0 = 0;
 #pragma unroll
-    for (int b = 0; b < 5; ++b) a0 += (u64)v[b] << (8 * b);
-    a1 = (u64)v[5] + ((u64)v[6] << 8);
-    a0 -= B * 0x0101010101ull;  // B * (1 + 2^8 + ... + 2^32)
-    a1 -= B * 0x0101ull;
-    const u64 t1 = a1 << 40;
+    for (int b = 0; b < 5; ++b) a0 += (u64)v[b] << (W * b);
+    a0 -= B5;                           // P_0 + ... + P_4 2^(4W) < 2^(23 + 4W + 1)
+    u64 a1;                             // the sums above, at 2^(5W)
+    if constexpr (W == 8)
+        a1 = (u64)v[5] + ((u64)v[6] << 8) - B * 0x0101ull;
+    else
+        a1 = (u64)v[5] - B;
+    const u64 t1 = a1 << (5 * W);
     const u64 lo = a0 + t1;
-    const u64 hi = (a1 >> 24) + (lo < t1 ? 1 : 0);
-    return redc(U128{lo, hi}, q, mont);
+    const uint32_t hi = (uint32_t)(a1 >> (64 - 5 * W)) + (lo < t1 ? 1u : 0u);  // S = lo + hi 2^64
+    // (S + m q) / 2^32 with m = -S q^-1 mod 2^32: the low word of S + m q is 0
+    const uint32_t l0 = (uint32_t)lo, l1 = (uint32_t)(lo >> 32);
+    const uint32_t m = l0 * qinv;
+    const u64 w = (u64)m * (uint32_t)q + l0;
+    return (u64)m * (uint32_t)(q >> 32) + (w >> 32) + l1 + ((u64)hi << 32);
 }
 
 // 16 consecutive accumulator columns of this warp's 32 lanes (no wait).
@@ -295,7 +308,7 @@ struct TcCursor {
 // commits them to acc_full; consumer warps wait on acc_full, run the
 // epilogue and release the buffer through acc_empty.  Every wait is bounded:
 // on timeout the kernel sets g_tc_error and its threads leave their loops.
-template <int MODE, int KB>
+template <int MODE, int KB, int W>
 __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJobs bu, BDnJobs bd, const uint4 *slabs,
                                                                 int XT, int TBN, int TB, int items)
 {
@@ -454,11 +467,12 @@ __global__ void __launch_bounds__(TC_PIPE_THREADS, 1) k_bconv_tc(Tables T, BUpJo
                 if (two) tmem_ld16(taddr + 64, w);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 const int g = 2 * p;
-                s_dst[buf][g][row] = tc_reduce(v, s_q[buf][g], s_mont[buf][g]);
-                if (g + 1 < G) s_dst[buf][g + 1][row] = tc_reduce(v + 8, s_q[buf][g + 1], s_mont[buf][g + 1]);
+                s_dst[buf][g][row] = tc_reduce<W>(v, s_q[buf][g], (uint32_t)s_mont[buf][g]);
+                if (g + 1 < G) s_dst[buf][g + 1][row] = tc_reduce<W>(v + 8, s_q[buf][g + 1], (uint32_t)s_mont[buf][g + 1]);
                 if (two) {
-                    s_dst[buf][g + 8][row] = tc_reduce(w, s_q[buf][g + 8], s_mont[buf][g + 8]);
-                    if (g + 9 < G) s_dst[buf][g + 9][row] = tc_reduce(w + 8, s_q[buf][g + 9], s_mont[buf][g + 9]);
+                    s_dst[buf][g + 8][row] = tc_reduce<W>(w, s_q[buf][g + 8], (uint32_t)s_mont[buf][g + 8]);
+                    if (g + 9 < G)
+                        s_dst[buf][g + 9][row] = tc_reduce<W>(w + 8, s_q[buf][g + 9], (uint32_t)s_mont[buf][g + 9]);
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -499,7 +513,7 @@ static int sm_count()
     return n;
 }
 
-template <int MODE, int KB>
+template <int MODE, int KB, int W>
 static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int span, int Z, const uint4 *slabs,
                      cudaStream_t st, const char *name)
 {
@@ -508,13 +522,13 @@ static int launch_tc(const Tables &T, const BUpJobs &bu, const BDnJobs &bd, int 
     const int TB = (span + TBN - 1) / TBN;
     static std::atomic<uint64_t> attr{0};
     once_per_device(attr, [] {
-        cudaFuncSetAttribute(k_bconv_tc<MODE, KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_pipe_smem<KB>());
+        cudaFuncSetAttribute(k_bconv_tc<MODE, KB, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_pipe_smem<KB>());
     });
     const int XT = (int)(((size_t)1 << T.logN) / TC_M);
     const long long items = (long long)XT * TBN * Z;
     if (items <= 0) return KS_OK;
     const int grid = (int)std::min<long long>(items, sm_count());
-    KS_LAUNCH(st, name, (k_bconv_tc<MODE, KB><<<grid, TC_PIPE_THREADS, tc_pipe_smem<KB>(), st>>>(T, bu, bd, slabs, XT,
+    KS_LAUNCH(st, name, (k_bconv_tc<MODE, KB, W><<<grid, TC_PIPE_THREADS, tc_pipe_smem<KB>(), st>>>(T, bu, bd, slabs, XT,
                                                                                                  TBN, TB, (int)items)));
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? KS_OK : fail(KS_ECUDA, std::string(name) + " (tensor cores) launch: " + cudaGetErrorString(e));
@@ -537,8 +551,9 @@ int launch_bconv_up_tc(const Tables &T, const BUpJobs &b, const uint4 *slabs, co
     none.n = 0;
     Tables Tt = T;
     Tt.up_tc = slabs;
-    return tc_kblocks(T.alpha) == 1 ? launch_tc<0, 1>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up")
-                                    : launch_tc<0, 2>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up");
+    if (tc_kblocks(T.alpha) == 2) return launch_tc<0, 2, 8>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up");
+    return tc_slice_bits(1, T.tc_below54) == 9 ? launch_tc<0, 1, 9>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up")
+                                               : launch_tc<0, 1, 8>(Tt, b, none, span, b.zpre[b.n], slabs, st, "bconv_up");
 }
 
 int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, cudaStream_t st)
@@ -548,8 +563,9 @@ int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, 
     if (span <= 0) return KS_OK;
     BUpJobs none;
     none.n = 0;
-    return tc_kblocks(T.kp) == 1 ? launch_tc<1, 1>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down")
-                                 : launch_tc<1, 2>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down");
+    if (tc_kblocks(T.kp) == 2) return launch_tc<1, 2, 8>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down");
+    return tc_slice_bits(1, T.tc_below54) == 9 ? launch_tc<1, 1, 9>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down")
+                                               : launch_tc<1, 1, 8>(T, none, b, span, b.zpre[b.n], slabs, st, "bconv_down");
 }
 
 int tc_error_flag(bool clear)
@@ -566,41 +582,45 @@ int tc_error_flag(bool clear)
     return v;
 }
 
-// Host: the B slab of one target of modulus r: rows b = 0..7 (byte of the
-// folded constant; row 7 zero), columns k = 7i + a (source i, byte a of y):
-// byte b of c_i * 2^(8a) mod r; the last column holds the bias.
+// Host: the B slab of one target of modulus r: rows b (slice b of the
+// folded constant, W bits; rows past the slices zero), columns k = 7i + a
+// (source i, byte a of y): slice b of c_i * 2^(8a) * 2^-32 mod r (c_i carries
+// 2^64, the epilogue's reduction takes 2^32 off); the last column holds the bias.
 template <int KB>
-static void tc_slab_kb(const std::vector<u64> &c, u64 r, uint16_t *slab)
+static void tc_slab_kb(const std::vector<u64> &c, u64 r, int W, uint16_t *slab)
 {
     constexpr int K = TcK<KB>::K;
+    const int NSL = W == 8 ? 7 : 6;
+    const u64 inv32 = invmod_h((u64)(((unsigned __int128)1 << 32) % r), r);
     for (int k = 0; k < K; ++k) {
         const int i = k / 7, a = k % 7;
-        const u64 cf = (k < K - 1 && i < (int)c.size()) ? mulmod_h(c[i] % r, powmod_h(2, 8 * (u64)a, r), r) : 0;
+        const u64 cf = (k < K - 1 && i < (int)c.size())
+                           ? mulmod_h(mulmod_h(c[i] % r, inv32, r), powmod_h(2, 8 * (u64)a, r), r) : 0;
         for (int b = 0; b < 8; ++b) {
-            const uint32_t byte = b < 7 ? (uint32_t)((cf >> (8 * b)) & 0xFF) : 0u;
-            // f16 of an integer below 256
+            const uint32_t sl = b < NSL ? (uint32_t)((cf >> (W * b)) & ((1u << W) - 1)) : 0u;
+            // f16 of an integer below 2048
             uint16_t bits = 0;
-            if (byte) {
-                int e = 31 - __builtin_clz(byte);                 // exponent
-                uint32_t mant = (byte << (10 - e)) & 0x3FF;        // 10 fraction bits
+            if (sl) {
+                int e = 31 - __builtin_clz(sl);                   // exponent
+                uint32_t mant = (sl << (10 - e)) & 0x3FF;          // 10 fraction bits
                 bits = (uint16_t)(((15 + e) << 10) | mant);
             }
             slab[tc_off<KB>(b, k) / 2] = bits;
         }
     }
     // the last column (never a slice: 9*KB sources use the columns before it)
-    // holds 4096 in the 7 used byte rows; times the A tile's 2048 there it
+    // holds 4096 in the used slice rows; times the A tile's 2048 there it
     // adds 2^23, so the fp32 accumulator of P (< 2^23) reads 2^23 + P: its
     // bits are 0x4B000000 + P
-    for (int b = 0; b < 7; ++b) slab[tc_off<KB>(b, K - 1) / 2] = (uint16_t)((15 + 12) << 10);
+    for (int b = 0; b < NSL; ++b) slab[tc_off<KB>(b, K - 1) / 2] = (uint16_t)((15 + 12) << 10);
 }
 
-void tc_slab(const std::vector<u64> &c, u64 r, int kblocks, uint16_t *slab)
+void tc_slab(const std::vector<u64> &c, u64 r, int kblocks, int bits, uint16_t *slab)
 {
     if (kblocks == 1)
-        tc_slab_kb<1>(c, r, slab);
+        tc_slab_kb<1>(c, r, bits, slab);
     else
-        tc_slab_kb<2>(c, r, slab);
+        tc_slab_kb<2>(c, r, 8, slab);
 }
 
 }  // namespace ks

@@ -255,6 +255,10 @@ int build_tables(ks_params *P)
     std::vector<uint16_t> up_tc, dn_tc;
     std::vector<int> up_tc_lvl((size_t)P->nq * P->ndig, 0);
     const int kb_up = tc_kblocks(A), kb_dn = tc_kblocks(P->kp);
+    int below54 = 1;
+    for (u64 q : P->q) below54 = below54 && q < (1ull << 54);
+    for (u64 p : P->p) below54 = below54 && p < (1ull << 54);
+    const int bits_up = tc_slice_bits(kb_up, below54), bits_dn = tc_slice_bits(kb_dn, below54);
     const size_t SLAB = (size_t)kTcSlabHalves * kb_up, DSLAB = (size_t)kTcSlabHalves * kb_dn;
     if (A <= 18) {
         std::vector<int> off((size_t)P->ndig * (A + 1), -1);
@@ -273,7 +277,7 @@ int build_tables(ks_params *P)
                         c[i] = to_mont(hat, r);
                     }
                     up_tc.resize(up_tc.size() + SLAB);
-                    tc_slab(c, r, kb_up, up_tc.data() + up_tc.size() - SLAB);
+                    tc_slab(c, r, kb_up, bits_up, up_tc.data() + up_tc.size() - SLAB);
                 }
             }
         }
@@ -286,7 +290,7 @@ int build_tables(ks_params *P)
         for (int i = 0; i < P->nq; ++i) {
             std::vector<u64> c(P->kp);
             for (int k = 0; k < P->kp; ++k) c[k] = to_mont(invmod_h(P->p[k] % P->q[i], P->q[i]), P->q[i]);
-            tc_slab(c, P->q[i], kb_dn, dn_tc.data() + (size_t)i * DSLAB);
+            tc_slab(c, P->q[i], kb_dn, bits_dn, dn_tc.data() + (size_t)i * DSLAB);
         }
     }
 
@@ -349,6 +353,9 @@ int build_tables(ks_params *P)
     T.dn_tc = P->bconv_tensor ? P->d_dn_tc : nullptr;
     T.ntt_cluster = P->ntt_cluster;
     T.row_stage = P->row_stage;
+    T.tc_below54 = 1;
+    for (u64 q : P->q) T.tc_below54 = T.tc_below54 && q < (1ull << 54);
+    for (u64 p : P->p) T.tc_below54 = T.tc_below54 && p < (1ull << 54);
     T.spq = 1;
     for (u64 q : P->q) T.spq = T.spq && (q & 0xFFFFFFFFull) == 1;
     for (u64 p : P->p) T.spq = T.spq && (p & 0xFFFFFFFFull) == 1;

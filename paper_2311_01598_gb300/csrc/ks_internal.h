@@ -79,6 +79,7 @@ struct Tables {
     int ntt_cluster;  // host side: NTTs as one cluster launch where supported
     int row_stage;    // host side: forward row passes staged by bulk copies (k_fwd_row_st)
     int spq;          // every modulus is q1*2^32 + 1: two-pass NTTs use shoup_est_sp
+    int tc_below54;   // every modulus is below 2^54: 9-bit constant slices (tensor-core BConv)
     int logN;
     int nq, kp, alpha, ndig;
 };

@@ -129,11 +129,15 @@ int launch_bconv_up_tc(const Tables &T, const BUpJobs &b, const uint4 *slabs, co
 int launch_bconv_down_tc(const Tables &T, const BDnJobs &b, const uint4 *slabs, cudaStream_t st);
 // K blocks of 64 slice columns for nsrc sources: one up to 9, two up to 18.
 inline int tc_kblocks(int nsrc) { return nsrc <= 9 ? 1 : 2; }
-// Host: one B slab of kblocks KB (8 byte rows x 64*kblocks slice columns,
-// f16, canonical layout) for the constants c[0..nsrc) of one target of
-// modulus r: row b, column 7i + a holds byte b of c_i * 2^(8a) mod r.
+// Bits of the constants' slices: 9 (6 slices, partial sums below 9*7*255*511
+// < 2^23) with one K block when every modulus is below 2^54, else 8 (7).
+inline int tc_slice_bits(int kblocks, int below54) { return kblocks == 1 && below54 ? 9 : 8; }
+// Host: one B slab of kblocks KB (8 slice rows x 64*kblocks slice columns,
+// f16, canonical layout) for the constants c[0..nsrc) (carrying 2^64) of one
+// target of modulus r: row b, column 7i + a holds bit slice b (of `bits`
+// bits) of c_i * 2^(8a) * 2^-32 mod r.
 constexpr int kTcSlabHalves = 8 * 64;  // f16 words of a slab per K block
-void tc_slab(const std::vector<u64> &c, u64 r, int kblocks, uint16_t *slab);
+void tc_slab(const std::vector<u64> &c, u64 r, int kblocks, int bits, uint16_t *slab);
 // Device flag set by a tensor-core kernel whose MMA wait gave up (-1: unreadable).
 int tc_error_flag(bool clear);
 // Device flag set by a staged row pass whose bulk-copy wait gave up (-1: unreadable).
