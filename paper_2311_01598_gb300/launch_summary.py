@@ -157,8 +157,6 @@ def to_markdown(table, total, n):
 # library launch names (KS_LAUNCH) of the key-switching kernels
 LIB_NAMES = {"k_fwd_row": "ntt_fwd_row", "k_fwd_col": "ntt_fwd_col", "k_inv_row": "ntt_inv_row",
              "k_inv_col": "ntt_inv_col", "k_bconv_up": "bconv_up", "k_bconv_down": "bconv_down",
-             "k_bconv_tc<0, 1>": "bconv_up", "k_bconv_tc<0, 2>": "bconv_up", "k_bconv_tc<1, 1>": "bconv_down",
-             "k_bconv_tc<1, 2>": "bconv_down",
              "k_oc_comb_qw": "oc_comb_q", "k_oc_comb_pw": "oc_comb_p", "k_oc_comb_q": "oc_comb_q",
              "k_oc_comb_p": "oc_comb_p", "k_oc_comb_qg": "oc_comb_q", "k_oc_comb_pg": "oc_comb_p",
              "k_fwd_cl": "ntt_fwd_cl", "k_inv_cl": "ntt_inv_cl", "k_oc_rowP": "oc_row_p", "k_oc_rowQ": "oc_row_q",
@@ -167,11 +165,17 @@ LIB_NAMES = {"k_fwd_row": "ntt_fwd_row", "k_fwd_col": "ntt_fwd_col", "k_inv_row"
              "k_shard_keyprod": "shard_keyprod", "k_shard_final": "shard_final"}
 
 
+# kernels named by their first template argument (the stage), whatever the rest
+LIB_BY_FIRST_ARG = {"k_bconv_tc": {"0": "bconv_up", "1": "bconv_down"}}
+
+
 def lib_name(kernel_name):
     """Library launch name of an ncu kernel name, or None."""
     m = re.search(r"\b(k_[A-Za-z0-9_]+)(<[^()]*>)?", kernel_name)
     if not m:
         return None
+    if m.group(1) in LIB_BY_FIRST_ARG and m.group(2):
+        return LIB_BY_FIRST_ARG[m.group(1)].get(m.group(2)[1:-1].split(",")[0].strip())
     full = m.group(1) + (m.group(2) or "")
     return LIB_NAMES.get(full, LIB_NAMES.get(m.group(1)))
 

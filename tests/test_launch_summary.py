@@ -40,6 +40,7 @@ def test_summarise_window_and_shares(tmp_path):
 def test_library_names():
     assert L.lib_name("void ks::(anonymous namespace)::k_bconv_tc<1, 1>(ks::Tables)") == "bconv_down"
     assert L.lib_name("void ks::(anonymous namespace)::k_bconv_tc<0, 2>(ks::Tables)") == "bconv_up"
+    assert L.lib_name("void ks::(anonymous namespace)::k_bconv_tc<1, 1, 9>(ks::Tables)") == "bconv_down"
     assert L.lib_name("void ks::k_fwd_row<ks::Shape<8, 8>, true>(ks::Tables, ks::LimbMaps)") == "ntt_fwd_row"
     assert L.lib_name("void ks::k_oc_comb_qg<false, true, 2>(ks::Tables)") == "oc_comb_q"
     assert L.lib_name("void at::native::vectorized_elementwise_kernel<4>(int)") is None
