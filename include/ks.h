@@ -104,7 +104,7 @@ int ks_params_info(const ks_params *params, uint64_t *h_q, uint64_t *h_p,
 
 /* Implementation options of a parameter set (none changes any result).
  *   KS_OPT_BCONV_TENSOR (default 1): run the fast base conversions (ModUp P2,
- *     ModDown P2) on the tensor cores (tcgen05, exact f16 byte slices)
+ *     ModDown P2) on the tensor cores (tcgen05, exact f16 slices)
  *     wherever at most 18 source towers meet N >= 2^7; 0 selects the CUDA-core
  *     kernels everywhere.
  *   KS_OPT_BATCH_LANES (default 2, 1..4): an Output-Centric batch of at least
