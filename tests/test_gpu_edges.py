@@ -174,20 +174,24 @@ def test_extreme_inputs_56bit(kind, key_kind):
         check_all_paths(ks, P, C, key, nact, d, w0, w1, engines=(True, False), what=(kind, key_kind))
 
 
-# (logN, nq, kp, dnum, levels): one K block of the tensor-core base conversion
-# (8 sources), and two at their limit (18 sources: partial sums up to
-# 7*18*255^2, just below the 2^23 of the accumulator's fixed read-out)
-EXTREME_SHAPES = [(16, 24, 8, 3, (24, 9)), (13, 36, 18, 2, (36, 19))]
+# (logN, nq, kp, dnum, levels, bits): one K block of the tensor-core base
+# conversion (8 sources) with byte slices of the constants (56-bit moduli) and
+# with 9-bit slices (54-bit moduli: partial sums up to 8*7*255*511), and two K
+# blocks at their limit (18 sources: partial sums up to 7*18*255^2, just below
+# the 2^23 of the accumulator's fixed read-out)
+EXTREME_SHAPES = [(16, 24, 8, 3, (24, 9), 56), (16, 24, 8, 3, (24, 9), 54), (13, 36, 18, 2, (36, 19), 56)]
+EXTREME_IDS = ["8src", "8src_9bit", "18src"]
 
 
-@pytest.mark.parametrize("shape", EXTREME_SHAPES, ids=["8src", "18src"])
+@pytest.mark.parametrize("shape", EXTREME_SHAPES, ids=EXTREME_IDS)
 @pytest.mark.parametrize("kind", ["all_q_minus_1", "max_y"])
 def test_modup_extreme_56bit(kind, shape):
-    """ModUp P1-P3 stage (Sec. III-B) with the largest inputs, 56-bit primes."""
+    """ModUp P1-P3 stage (Sec. III-B) with the largest inputs, 56-bit primes
+    (and 54-bit ones for the 9-bit constant slices)."""
     need_gpu()
     ks = built_lib()
-    logN, nq, kp, dnum, levels = shape
-    P, C = pair(logN, nq, kp, dnum, 56)
+    logN, nq, kp, dnum, levels, bits = shape
+    P, C = pair(logN, nq, kp, dnum, bits)
     for nact in levels:
         if kind == "all_q_minus_1":
             d = np.ones((nact, C.N), dtype=np.uint64) * (np.array(C.q[:nact], dtype=np.uint64) - 1)[:, None]
@@ -202,15 +206,16 @@ def test_modup_extreme_56bit(kind, shape):
     P.set_bconv_tensor(True)
 
 
-@pytest.mark.parametrize("shape", EXTREME_SHAPES, ids=["8src", "18src"])
+@pytest.mark.parametrize("shape", EXTREME_SHAPES, ids=EXTREME_IDS)
 @pytest.mark.parametrize("kind", ["all_r_minus_1", "max_w"])
 def test_moddown_extreme_56bit(kind, shape):
     """ModDown P1-P4 stage (Sec. III-C) with c' of all r-1, or with every
-    pre-scaled special-tower coefficient p_k - 1, 56-bit primes."""
+    pre-scaled special-tower coefficient p_k - 1, 56-bit primes (and 54-bit
+    ones for the 9-bit constant slices)."""
     need_gpu()
     ks = built_lib()
-    logN, nq, kp, dnum, levels = shape
-    P, C = pair(logN, nq, kp, dnum, 56)
+    logN, nq, kp, dnum, levels, bits = shape
+    P, C = pair(logN, nq, kp, dnum, bits)
     for nact in levels:
         if kind == "all_r_minus_1":
             towers = np.array(C.towers(nact), dtype=np.uint64)
