@@ -46,3 +46,18 @@ def test_impl_pairs_match_the_library_order():
     hdr = open(os.path.join(os.path.dirname(tune.HERE), "include", "ks.h")).read()
     assert "{(0,1), (1,1), (0,0), (1,0)}" in hdr
     assert tune.IMPL_PAIRS == ((0, 1), (1, 1), (0, 0), (1, 0))
+
+
+def test_implementation_flags_follow_the_kernels_limits():
+    """The last three inputs flag which implementations exist for a shape:
+    the tensor-core base conversion up to 18 sources (two K blocks) for
+    ModUp (the parameter set's alpha) and ModDown (K), the cluster NTT at
+    ring degrees other than 2^13 and 2^17."""
+    def flags(logN, nq, dnum, kp, alpha_params=None):
+        return tuple(float(x) for x in tune.features(logN, nq, dnum, kp, 16, alpha_params)[-3:])
+    assert flags(16, 24, 3, 8) == (1.0, 1.0, 1.0)              # alpha 8, K 8
+    assert flags(17, 36, 3, 12) == (1.0, 1.0, -1.0)            # alpha 12, K 12: two K blocks; no 2^17 cluster
+    assert flags(16, 36, 2, 18) == (1.0, 1.0, 1.0)             # alpha 18, K 18: the limit
+    assert flags(16, 38, 2, 19) == (-1.0, -1.0, 1.0)           # alpha 19, K 19: CUDA cores only
+    assert flags(13, 24, 1, 8, alpha_params=12) == (1.0, 1.0, -1.0)  # the parameter set's alpha decides
+    assert flags(14, 40, 2, 20) == (-1.0, -1.0, 1.0)
